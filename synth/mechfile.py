@@ -1,0 +1,128 @@
+"""Binary mechanism file: the one format every reader in this project parses.
+
+The layout is little-endian:
+
+    char[8]  magic "DLBMECH1"
+    int32    nsp, nrx, nelem, n_eff
+    f64[nsp] W        molar mass, g/mol
+    f64[nsp] cp_a     cp = cp_a + cp_b*T, J/(mol K)
+    f64[nsp] cp_b     J/(mol K^2)
+    f64[nsp] hf       formation enthalpy at T0 = 298.15 K, J/mol
+    f64[nsp] s0       standard entropy at T0 and p0 = 1 atm, J/(mol K)
+    i32[nsp*nelem] atoms (species-major; elements C, H, O, N)
+    nrx reaction records, each:
+        f64 lnA   (A in mol, cm^3, s units of the reaction's order)
+        f64 beta  (temperature exponent)
+        f64 Ea    (J/mol)
+        i32 nr, np, reversible, thirdbody
+        i32 ridx[3], rnu[3], pidx[3], pnu[3]   (unused slots are -1 / 0)
+    n_eff records of (i32 reaction, i32 species, f64 efficiency): third-body
+        efficiencies that differ from 1; every other species counts with 1.
+
+Each species appears at most once per side; its integer coefficient is in
+rnu / pnu.
+"""
+from __future__ import annotations
+
+import dataclasses
+import struct
+
+import numpy as np
+
+MAGIC = b"DLBMECH1"
+ELEMENTS = ("C", "H", "O", "N")
+ATOMIC_MASS = np.array([12.011, 1.008, 15.999, 14.007])
+
+
+@dataclasses.dataclass
+class Mechanism:
+    W: np.ndarray
+    cp_a: np.ndarray
+    cp_b: np.ndarray
+    hf: np.ndarray
+    s0: np.ndarray
+    atoms: np.ndarray            # [nsp, 4] int
+    lnA: np.ndarray              # [nrx]
+    beta: np.ndarray
+    Ea: np.ndarray
+    reac: list                   # per reaction: list of (species, nu)
+    prod: list
+    reversible: np.ndarray       # [nrx] int
+    thirdbody: np.ndarray        # [nrx] int
+    eff: list = dataclasses.field(default_factory=list)  # (rxn, species, eff)
+
+    @property
+    def nsp(self) -> int:
+        return len(self.W)
+
+    @property
+    def nrx(self) -> int:
+        return len(self.lnA)
+
+    def nu_matrix(self) -> tuple[np.ndarray, np.ndarray]:
+        """Reactant and product coefficient matrices, each [nsp, nrx]."""
+        nr = np.zeros((self.nsp, self.nrx), dtype=np.int64)
+        npd = np.zeros((self.nsp, self.nrx), dtype=np.int64)
+        for j, (r, p) in enumerate(zip(self.reac, self.prod)):
+            for k, nu in r:
+                nr[k, j] += nu
+            for k, nu in p:
+                npd[k, j] += nu
+        return nr, npd
+
+
+def write_mech(path: str, m: Mechanism) -> None:
+    nsp, nrx = m.nsp, m.nrx
+    with open(path, "wb") as f:
+        f.write(MAGIC)
+        f.write(struct.pack("<4i", nsp, nrx, 4, len(m.eff)))
+        for arr in (m.W, m.cp_a, m.cp_b, m.hf, m.s0):
+            f.write(np.asarray(arr, dtype="<f8").tobytes())
+        f.write(np.asarray(m.atoms, dtype="<i4").reshape(-1).tobytes())
+        for j in range(nrx):
+            r, p = m.reac[j], m.prod[j]
+            if not (1 <= len(r) <= 3 and 1 <= len(p) <= 3):
+                raise ValueError(f"reaction {j}: 1..3 species per side")
+            ridx = [k for k, _ in r] + [-1] * (3 - len(r))
+            rnu = [nu for _, nu in r] + [0] * (3 - len(r))
+            pidx = [k for k, _ in p] + [-1] * (3 - len(p))
+            pnu = [nu for _, nu in p] + [0] * (3 - len(p))
+            f.write(struct.pack("<3d", float(m.lnA[j]), float(m.beta[j]), float(m.Ea[j])))
+            f.write(struct.pack("<16i", len(r), len(p), int(m.reversible[j]), int(m.thirdbody[j]),
+                                *ridx, *rnu, *pidx, *pnu))
+        for (j, k, e) in m.eff:
+            f.write(struct.pack("<2id", int(j), int(k), float(e)))
+
+
+def read_mech(path: str) -> Mechanism:
+    with open(path, "rb") as f:
+        buf = f.read()
+    if buf[:8] != MAGIC:
+        raise ValueError(f"{path}: not a DLBMECH1 file")
+    nsp, nrx, nelem, neff = struct.unpack_from("<4i", buf, 8)
+    off = 24
+    arrs = []
+    for _ in range(5):
+        arrs.append(np.frombuffer(buf, dtype="<f8", count=nsp, offset=off).copy())
+        off += 8 * nsp
+    atoms = np.frombuffer(buf, dtype="<i4", count=nsp * nelem, offset=off).reshape(nsp, nelem).copy()
+    off += 4 * nsp * nelem
+    lnA, beta, Ea, reac, prod, rev, tb = [], [], [], [], [], [], []
+    for _ in range(nrx):
+        a, b, e = struct.unpack_from("<3d", buf, off)
+        off += 24
+        v = struct.unpack_from("<16i", buf, off)
+        off += 64
+        nr, npd = v[0], v[1]
+        lnA.append(a); beta.append(b); Ea.append(e)
+        rev.append(v[2]); tb.append(v[3])
+        reac.append([(v[4 + i], v[7 + i]) for i in range(nr)])
+        prod.append([(v[10 + i], v[13 + i]) for i in range(npd)])
+    eff = []
+    for _ in range(neff):
+        j, k, e = struct.unpack_from("<2id", buf, off)
+        off += 16
+        eff.append((j, k, e))
+    return Mechanism(W=arrs[0], cp_a=arrs[1], cp_b=arrs[2], hf=arrs[3], s0=arrs[4], atoms=atoms,
+                     lnA=np.array(lnA), beta=np.array(beta), Ea=np.array(Ea), reac=reac, prod=prod,
+                     reversible=np.array(rev), thirdbody=np.array(tb), eff=eff)

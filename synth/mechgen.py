@@ -1,0 +1,150 @@
+"""Seeded synthetic element-balanced mechanisms.
+
+Recipe (the paper names a 54-species n-dodecane mechanism that is not
+available here; these mechanisms stand in for its size and structure):
+
+* Species are atom vectors over (C, H, O, N) with counts 0..3. The set is
+  grown greedily from two single-atom species: each new species is the
+  candidate vector that adds the most new element-balanced pairs of
+  1- or 2-species multisets, ties broken by the seeded generator. This gives
+  the small-lattice structure of real mechanisms (H, O, OH, H2O, HO2, ...)
+  so that even 10 species carry 20+ balanced reactions.
+* Thermo per species: cp = a + b*T with a ~ U[25, 45] J/(mol K),
+  b ~ U[0, 0.01] J/(mol K^2); h_f ~ U[-150, 50] kJ/mol; s0 = 100 + 40*n_atoms
+  + U[-15, 15] J/(mol K). Tying s0 to the atom count (as for real species:
+  H 115, OH 184, H2O 189, H2O2 233) keeps reaction entropies physical: about
+  +100 J/(mol K) for A <=> B + C and about 0 for A + B <=> C + D. Entropies
+  drawn independently per species give |dS| up to 40 R, equilibrium
+  constants off by e^40 and reverse rate constants above 1e20 per second.
+* Reactions are drawn uniformly without replacement from all pairs of
+  distinct multisets with equal element sums (types A <=> B + C and
+  A + B <=> C + D). round(0.1*R) of them are third-body reactions
+  A + B (+M) <=> C (+M), efficiency 1 for every species.
+* Each reaction is oriented so that its forward direction is exothermic at
+  298.15 K (sum of nu*h_f <= 0); then A is log-uniform on [1e6, 1e14]
+  (mol, cm^3, s units), beta ~ U[-1, 1], Ea ~ U[0, 200] kJ/mol.
+* Every species must take part in at least one reaction; the reaction draw
+  is repeated (same stream) until it does.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+from .mechfile import ATOMIC_MASS, Mechanism
+
+_CANDIDATES = np.array([v for v in itertools.product(range(4), repeat=4) if sum(v) > 0], dtype=np.int64)
+
+
+def _key(v) -> tuple:
+    return tuple(int(x) for x in v)
+
+
+def _grow_species(nsp: int, rng: np.random.Generator) -> np.ndarray:
+    els = rng.permutation(4)[:2]
+    species = [np.eye(4, dtype=np.int64)[e] for e in els]
+    # count[sum] = number of 1- and 2-species multisets with that element sum
+    count: dict = {}
+
+    def add_counts(vs):
+        for v in vs:
+            count[_key(v)] = count.get(_key(v), 0) + 1
+
+    add_counts([species[0], species[1], 2 * species[0], 2 * species[1], species[0] + species[1]])
+    while len(species) < nsp:
+        have = {_key(s) for s in species}
+        best, best_gain = [], -1
+        for v in _CANDIDATES:
+            if _key(v) in have:
+                continue
+            # new multisets {v}, {v,v}, {v,s}: each pairs with every existing
+            # multiset of the same sum (they cannot collide with each other)
+            gain = count.get(_key(v), 0) + count.get(_key(2 * v), 0)
+            for s in species:
+                gain += count.get(_key(v + s), 0)
+            if gain > best_gain:
+                best, best_gain = [v], gain
+            elif gain == best_gain:
+                best.append(v)
+        v = best[int(rng.integers(len(best)))]
+        add_counts([v, 2 * v] + [v + s for s in species])
+        species.append(v)
+    return np.array(species)
+
+
+def _candidate_pairs(atoms: np.ndarray):
+    """All unordered pairs of distinct multisets (size 1 or 2) with equal sums."""
+    nsp = len(atoms)
+    groups: dict = {}
+    for i in range(nsp):
+        groups.setdefault(_key(atoms[i]), []).append((i,))
+        for j in range(i, nsp):
+            groups.setdefault(_key(atoms[i] + atoms[j]), []).append((i, j))
+    pairs = []
+    for key in sorted(groups):
+        ms = groups[key]
+        for a, b in itertools.combinations(ms, 2):
+            pairs.append((a, b))
+    return pairs
+
+
+def _side(ms) -> list:
+    out: dict = {}
+    for k in ms:
+        out[k] = out.get(k, 0) + 1
+    return sorted(out.items())
+
+
+def generate_mechanism(nsp: int, nrx: int, seed: int, tb_fraction: float = 0.1) -> Mechanism:
+    rng = np.random.default_rng(seed)
+    atoms = _grow_species(nsp, rng)
+    W = atoms @ ATOMIC_MASS
+    cp_a = rng.uniform(25.0, 45.0, nsp)
+    cp_b = rng.uniform(0.0, 0.01, nsp)
+    hf = rng.uniform(-150e3, 50e3, nsp)
+    s0 = 100.0 + 40.0 * atoms.sum(axis=1) + rng.uniform(-15.0, 15.0, nsp)
+
+    pairs = _candidate_pairs(atoms)
+    if len(pairs) < nrx:
+        raise ValueError(f"only {len(pairs)} balanced reactions exist for {nsp} species")
+    one_two = [i for i, (a, b) in enumerate(pairs) if len(a) != len(b)]
+    ntb = int(round(tb_fraction * nrx))
+    if len(one_two) < ntb:
+        raise ValueError("too few A <=> B + C candidates for the third-body share")
+    for _attempt in range(1000):
+        tb_sel = [one_two[i] for i in rng.choice(len(one_two), size=ntb, replace=False)]
+        rest = np.setdiff1d(np.arange(len(pairs)), tb_sel)
+        other = list(rng.choice(rest, size=nrx - ntb, replace=False))
+        chosen = tb_sel + [int(i) for i in other]
+        used = set()
+        for i in chosen:
+            a, b = pairs[i]
+            used.update(a)
+            used.update(b)
+        if len(used) == nsp:
+            break
+    else:
+        raise ValueError("could not cover every species with reactions")
+
+    reac, prod, tb = [], [], []
+    for n, i in enumerate(chosen):
+        a, b = pairs[i]
+        if n < ntb and len(a) == 2:     # third-body: write as A + B (+M) <=> C (+M)
+            a, b = b, a
+        ra, pb = _side(a), _side(b)
+        dh = sum(nu * hf[k] for k, nu in pb) - sum(nu * hf[k] for k, nu in ra)
+        if dh > 0.0:
+            ra, pb = pb, ra
+        reac.append(ra)
+        prod.append(pb)
+        tb.append(1 if n < ntb else 0)
+    lnA = rng.uniform(np.log(1e6), np.log(1e14), nrx)
+    beta = rng.uniform(-1.0, 1.0, nrx)
+    Ea = rng.uniform(0.0, 200e3, nrx)
+    perm = rng.permutation(nrx)   # interleave third-body and plain reactions
+    return Mechanism(W=W, cp_a=cp_a, cp_b=cp_b, hf=hf, s0=s0, atoms=atoms,
+                     lnA=lnA[perm], beta=beta[perm], Ea=Ea[perm],
+                     reac=[reac[i] for i in perm], prod=[prod[i] for i in perm],
+                     reversible=np.ones(nrx, dtype=np.int64),
+                     thirdbody=np.array([tb[i] for i in perm], dtype=np.int64), eff=[])

@@ -1,0 +1,26 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+
+
+@pytest.fixture(scope="session")
+def orc_c1():
+    import oracle
+    from synth import states
+    return oracle.Oracle(states.mech_path(10, 20, 0))
+
+
+@pytest.fixture(scope="session")
+def orc_c2():
+    import oracle
+    from synth import states
+    return oracle.Oracle(states.mech_path(53, 325, 0))

@@ -1,0 +1,162 @@
+/*
+ * dlbchem: batched stiff chemistry for the operator-split reacting-flow step,
+ * GB300 (sm_103a) CUDA library with a plain C ABI.
+ *
+ * The problem (DLBFoam paper, arXiv 2011.07978, Sec. 1 and Sec. 2.1): after
+ * operator splitting, every CFD cell n carries an independent stiff ODE
+ * dPhi/dt = f(Phi) for its thermochemical state Phi = (T, p, Y) over one flow
+ * step dt, and the cost of each cell depends on its initial state. Here p is
+ * held constant and the mixture is an adiabatic ideal gas, so each cell
+ * integrates y = (T, Y_1..Y_nsp) with mass-action Arrhenius kinetics, reverse
+ * rates from equilibrium constants built on species Gibbs energies, and
+ * third-body reactions. The integrator is the L-stable 4-stage Rosenbrock
+ * method of Hairer and Wanner (Solving ODEs II, Sec. IV.7) with embedded
+ * error estimate and adaptive steps, run by one warp (or one 4-warp team)
+ * per cell.
+ *
+ * The paper's two speed-ups become on-device scheduling here:
+ *  - load balancing (Sec. 2.2, Algorithm 1): cells are ordered by a cost key
+ *    (the per-cell step count of the previous call, the analogue of the
+ *    per-cell CPU time t_cpu^n) and pulled by a persistent kernel from a
+ *    device work queue, longest first;
+ *  - reference mapping (Sec. 2.3): cells close to a reference state reuse
+ *    the solution of the first such cell instead of being integrated.
+ *
+ * Conventions for every entry point:
+ *  - Arrays are species-major structure-of-arrays: Y[k * ncells + i] is the
+ *    mass fraction of species k in cell i. T in K, p in Pa.
+ *  - Unless a function says otherwise, pointers are DEVICE pointers owned by
+ *    the caller, and the work is enqueued asynchronously on the CUDA stream
+ *    passed as `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+ *  - Return codes cover argument validation and launch errors only; per-cell
+ *    outcomes are in status[] (device memory) once the stream has reached
+ *    the end of the call.
+ *  - A context is not thread-safe: calls on one context must not overlap on
+ *    the host. Calls on different contexts are independent.
+ */
+#ifndef DLBCHEM_H
+#define DLBCHEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define DLBCHEM_OK 0
+#define DLBCHEM_BAD_ARG 1   /* an argument is out of range or a pointer is NULL */
+#define DLBCHEM_BAD_MECH 2  /* mechanism file missing, truncated or inconsistent */
+#define DLBCHEM_CUDA 3      /* a CUDA runtime call or kernel launch failed */
+#define DLBCHEM_OOM 4       /* device workspace allocation failed */
+
+/* Per-cell status[] values. */
+#define DLBCHEM_CELL_OK 0
+#define DLBCHEM_CELL_MAPPED 1          /* copied the reference cell's increment */
+#define DLBCHEM_CELL_MAX_STEPS (-1)    /* max_steps attempted steps reached */
+#define DLBCHEM_CELL_H_UNDERFLOW (-2)  /* step size fell below hmin_frac*dt */
+#define DLBCHEM_CELL_NONFINITE (-3)    /* input not finite, T <= 0 or p <= 0 */
+/* A failed cell returns its last accepted state in T_out / Y_out. */
+
+/* Scheduling modes (dlbchem_options.schedule). */
+#define DLBCHEM_SCHED_PLAIN 0   /* one team per cell, cells in index order */
+#define DLBCHEM_SCHED_QUEUE 1   /* persistent teams pull cells longest-first */
+
+typedef struct dlbchem_ctx dlbchem_ctx;
+
+/*
+ * Integration and scheduling options. Sec. 4.1 of the paper gives the ODE
+ * tolerances rtol/atol; Sec. 2.3 the mapping tolerances (read here as a
+ * composition tolerance on max_k |Y_k - Yref_k| and a relative temperature
+ * tolerance |T - T_ref| < map_Ttol * T_ref).
+ */
+typedef struct dlbchem_options {
+  double rtol;          /* relative tolerance of the error norm (default 1e-6) */
+  double atol;          /* absolute tolerance (default 1e-10) */
+  int32_t max_steps;    /* attempted steps per cell before MAX_STEPS (100000) */
+  int32_t isothermal;   /* 1: freeze T (f_T = 0) */
+  double hmin_frac;     /* H_UNDERFLOW when h < hmin_frac * dt (1e-20) */
+  int32_t schedule;     /* DLBCHEM_SCHED_PLAIN or DLBCHEM_SCHED_QUEUE */
+  int32_t chunk;        /* cells per queue pull (1) */
+  int32_t mapping;      /* 1: reference mapping on */
+  int32_t reserved0;
+  double map_Ttol;      /* relative temperature tolerance (1e-4) */
+  double map_Ytol;      /* absolute composition tolerance (1e-4) */
+  double map_Tmax;      /* > 0: only cells below this T qualify (0 = off) */
+} dlbchem_options;
+
+/* Fill *opt with the defaults listed above. Returns DLBCHEM_OK or BAD_ARG. */
+int dlbchem_options_default(dlbchem_options* opt);
+
+/*
+ * Load a mechanism file (the DLBMECH1 binary format written by the seeded
+ * generator) on the current CUDA device and create a context. opt may be
+ * NULL (defaults). On success *out owns device copies of the mechanism
+ * tables; release it with dlbchem_destroy. On failure *out is NULL and the
+ * message is available from dlbchem_last_error(NULL).
+ * Returns DLBCHEM_OK, BAD_ARG, BAD_MECH, CUDA or OOM.
+ */
+int dlbchem_create(const char* mech_path, const dlbchem_options* opt, dlbchem_ctx** out);
+
+/* Replace the context's options (validated; BAD_ARG leaves them unchanged). */
+int dlbchem_set_options(dlbchem_ctx* ctx, const dlbchem_options* opt);
+
+/*
+ * Integrate ncells independent cells over one flow step dt (paper Sec. 2.2,
+ * stage 3, with stages 1 and 4 fused around it).
+ *   T, p   [ncells] inputs; Y [nsp][ncells] input mass fractions.
+ *   T_out  [ncells], Y_out [nsp][ncells] results; may alias T / Y.
+ *   steps  [ncells] int32, nullable. If non-NULL it is read first as the
+ *          per-cell cost key of the queue (the previous call's counts, the
+ *          analogue of t_cpu^n in Algorithm 1; all-zero keys give index
+ *          order) and then overwritten with the attempted steps of this call
+ *          (accepted + rejected; 0 for mapped cells).
+ *   status [ncells] int32, nullable: per-cell DLBCHEM_CELL_* codes.
+ *   Yref   [nsp] device pointer, nullable: the reference composition of the
+ *          mapping criterion; NULL uses cell 0's composition.
+ * ncells == 0 is a no-op. Mapping and the queue follow ctx's options.
+ * Returns DLBCHEM_OK, BAD_ARG (NULL pointer, dt <= 0 or not finite, ncells
+ * < 0), CUDA or OOM (workspace growth failed).
+ */
+int dlbchem_integrate(dlbchem_ctx* ctx, int64_t ncells, double dt, const double* T, const double* p,
+                      const double* Y, double* T_out, double* Y_out, int32_t* steps, int32_t* status,
+                      const double* Yref, void* cuda_stream);
+
+/*
+ * Same as dlbchem_integrate, but every array is a HOST pointer (pageable or
+ * pinned). The call copies the inputs into a device staging area owned by
+ * the context, integrates, copies the results back and synchronises the
+ * stream before returning. steps may be NULL (no cost key); status may be
+ * NULL. Returns as dlbchem_integrate.
+ */
+int dlbchem_integrate_host(dlbchem_ctx* ctx, int64_t ncells, double dt, const double* T, const double* p,
+                           const double* Y, double* T_out, double* Y_out, int32_t* steps, int32_t* status,
+                           const double* Yref, void* cuda_stream);
+
+/* Number of species / reactions of the loaded mechanism (-1 if ctx NULL). */
+int dlbchem_nspecies(const dlbchem_ctx* ctx);
+int dlbchem_nreactions(const dlbchem_ctx* ctx);
+
+/*
+ * Statistics of the last completed call on ctx (synchronises its stream).
+ *   out[0] cells integrated, out[1] cells mapped, out[2] reference cell
+ *   index (-1 if none), out[3] team size in threads, out[4] teams per CTA,
+ *   out[5] CTAs launched by the integrator, out[6] dynamic shared memory
+ *   bytes per CTA, out[7] integrator kernel launches in the call.
+ * Returns DLBCHEM_OK, BAD_ARG or CUDA.
+ */
+int dlbchem_last_stats(dlbchem_ctx* ctx, int64_t out[8]);
+
+/* Message of the last failed call on ctx, or of the last failed create when
+ * ctx is NULL. Never NULL; "" when there was no error. Owned by the library. */
+const char* dlbchem_last_error(const dlbchem_ctx* ctx);
+
+/* Release ctx and its device memory (synchronises its last stream). NULL ok. */
+void dlbchem_destroy(dlbchem_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DLBCHEM_H */

@@ -1,0 +1,538 @@
+// C-ABI of libdlbchem: mechanism loading, device tables, launch logic.
+// Declarations and contracts: include/dlbchem.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/dlbchem.h"
+#include "dlb_common.cuh"
+
+namespace {
+
+using namespace dlb;
+
+thread_local std::string g_create_err;
+
+// ---- host mechanism model (this library's own reader of DLBMECH1) ----------
+struct HostRxn {
+  double lnA, beta, Ea;
+  int rev, tb;
+  std::vector<int> r, p;       // species per slot, expanded by coefficient
+  std::vector<std::pair<int, double>> eff;   // listed efficiencies (species, eff)
+};
+
+struct HostMech {
+  int nsp = 0, nrx = 0;
+  std::vector<double> W, a, b, hf, s0;
+  std::vector<HostRxn> rx;
+};
+
+bool read_file(const char* path, std::vector<unsigned char>& buf) {
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return false;
+  std::fseek(f, 0, SEEK_END);
+  long sz = std::ftell(f);
+  std::fseek(f, 0, SEEK_SET);
+  if (sz < 0) { std::fclose(f); return false; }
+  buf.resize(size_t(sz));
+  size_t got = sz ? std::fread(buf.data(), 1, size_t(sz), f) : 0;
+  std::fclose(f);
+  return got == size_t(sz);
+}
+
+struct Reader {
+  const std::vector<unsigned char>& b;
+  size_t pos = 0;
+  bool ok = true;
+  template <class T>
+  T get() {
+    T v{};
+    if (pos + sizeof(T) > b.size()) { ok = false; return v; }
+    std::memcpy(&v, b.data() + pos, sizeof(T));
+    pos += sizeof(T);
+    return v;
+  }
+};
+
+bool parse_mech(const char* path, HostMech& m, std::string& err) {
+  std::vector<unsigned char> buf;
+  if (!read_file(path, buf)) { err = std::string("cannot read mechanism file ") + path; return false; }
+  if (buf.size() < 24 || std::memcmp(buf.data(), "DLBMECH1", 8) != 0) { err = "not a DLBMECH1 file"; return false; }
+  Reader rd{buf, 8};
+  m.nsp = rd.get<int32_t>();
+  m.nrx = rd.get<int32_t>();
+  const int nelem = rd.get<int32_t>();
+  const int neff = rd.get<int32_t>();
+  if (m.nsp < 1 || m.nsp > 4000 || m.nrx < 0 || m.nrx > 65535 || nelem < 1 || neff < 0) {
+    err = "mechanism sizes out of range (1..4000 species, 0..65535 reactions)";
+    return false;
+  }
+  for (auto* v : {&m.W, &m.a, &m.b, &m.hf, &m.s0}) {
+    v->resize(m.nsp);
+    for (auto& x : *v) x = rd.get<double>();
+  }
+  for (int i = 0; i < m.nsp * nelem; ++i) (void)rd.get<int32_t>();
+  m.rx.resize(m.nrx);
+  for (auto& r : m.rx) {
+    r.lnA = rd.get<double>(); r.beta = rd.get<double>(); r.Ea = rd.get<double>();
+    int32_t v[16];
+    for (auto& x : v) x = rd.get<int32_t>();
+    if (!rd.ok) break;
+    r.rev = v[2] != 0; r.tb = v[3] != 0;
+    if (v[0] < 1 || v[0] > 3 || v[1] < 1 || v[1] > 3) { err = "reaction arity out of range"; return false; }
+    for (int i = 0; i < v[0]; ++i) {
+      if (v[4 + i] < 0 || v[4 + i] >= m.nsp || v[7 + i] < 1) { err = "bad reactant"; return false; }
+      for (int c = 0; c < v[7 + i]; ++c) r.r.push_back(v[4 + i]);
+    }
+    for (int i = 0; i < v[1]; ++i) {
+      if (v[10 + i] < 0 || v[10 + i] >= m.nsp || v[13 + i] < 1) { err = "bad product"; return false; }
+      for (int c = 0; c < v[13 + i]; ++c) r.p.push_back(v[10 + i]);
+    }
+    if (r.r.size() > 3 || r.p.size() > 3) { err = "more than 3 molecules on one side"; return false; }
+  }
+  for (int i = 0; i < neff && rd.ok; ++i) {
+    int j = rd.get<int32_t>(), k = rd.get<int32_t>();
+    double e = rd.get<double>();
+    if (!rd.ok) break;
+    if (j < 0 || j >= m.nrx || k < 0 || k >= m.nsp || !m.rx[j].tb) { err = "bad efficiency record"; return false; }
+    m.rx[j].eff.push_back({k, e});
+  }
+  if (!rd.ok) { err = "truncated mechanism file"; return false; }
+  for (int k = 0; k < m.nsp; ++k)
+    if (!(m.W[k] > 0.0)) { err = "non-positive molar mass"; return false; }
+  return true;
+}
+
+// Rounds of 32 entries, no target twice in a round. Entries are placed first
+// fit in order of decreasing target multiplicity; per target the entries keep
+// their input order, which fixes every accumulation order.
+struct Entry {
+  int target;
+  uint32_t word;
+  double coef;
+};
+
+void build_rounds(const std::vector<Entry>& ents, uint32_t pad_word, std::vector<uint32_t>& words,
+                  std::vector<double>& coefs) {
+  std::map<int, std::vector<int>> by_t;
+  for (int i = 0; i < int(ents.size()); ++i) by_t[ents[i].target].push_back(i);
+  std::vector<std::pair<int, int>> order;   // (-multiplicity, target)
+  for (auto& kv : by_t) order.push_back({-int(kv.second.size()), kv.first});
+  std::sort(order.begin(), order.end());
+  std::vector<std::vector<int>> rounds;
+  std::vector<std::vector<int>> tgts;
+  for (auto& o : order) {
+    int start = 0;
+    for (int idx : by_t[o.second]) {
+      int rr = start;
+      for (;; ++rr) {
+        if (rr == int(rounds.size())) { rounds.emplace_back(); tgts.emplace_back(); }
+        if (rounds[rr].size() < 32 && std::find(tgts[rr].begin(), tgts[rr].end(), o.second) == tgts[rr].end()) break;
+      }
+      rounds[rr].push_back(idx);
+      tgts[rr].push_back(o.second);
+      start = rr + 1;
+    }
+  }
+  for (auto& rd : rounds) {
+    for (int l = 0; l < 32; ++l) {
+      if (l < int(rd.size())) { words.push_back(ents[rd[l]].word); coefs.push_back(ents[rd[l]].coef); }
+      else { words.push_back(pad_word); coefs.push_back(0.0); }
+    }
+  }
+}
+
+}  // namespace
+
+struct dlbchem_ctx {
+  int device = 0;
+  HostMech hm;
+  DevMech dm{};
+  void* d_blob = nullptr;
+  dlbchem_options opt{};
+  WsLayout L{};
+  int wpc = 1, teams = 1, smem_bytes = 0, blocks_per_sm = 1, num_sms = 0;
+  // workspace
+  unsigned long long* d_counter = nullptr;
+  int32_t* d_perm = nullptr;
+  int64_t perm_cap = 0;
+  // host-buffer staging
+  double* d_stage = nullptr;
+  int32_t* d_stage_i = nullptr;
+  int64_t stage_cap = 0;
+  cudaStream_t last_stream = nullptr;
+  int64_t stats[8] = {0, 0, -1, 0, 0, 0, 0, 0};
+  std::string err;
+};
+
+namespace {
+
+int fail(dlbchem_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg; else g_create_err = msg;
+  return code;
+}
+
+int cuda_fail(dlbchem_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, DLBCHEM_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool valid_opts(const dlbchem_options* o, std::string& why) {
+  if (!(o->rtol > 0) || !(o->atol > 0) || !std::isfinite(o->rtol) || !std::isfinite(o->atol)) { why = "rtol/atol must be positive"; return false; }
+  if (o->max_steps < 1) { why = "max_steps must be >= 1"; return false; }
+  if (!(o->hmin_frac > 0) || !(o->hmin_frac < 1)) { why = "hmin_frac must be in (0, 1)"; return false; }
+  if (o->schedule != DLBCHEM_SCHED_PLAIN && o->schedule != DLBCHEM_SCHED_QUEUE) { why = "unknown schedule"; return false; }
+  if (o->chunk < 1) { why = "chunk must be >= 1"; return false; }
+  if (!(o->map_Ttol >= 0) || !(o->map_Ytol >= 0) || !(o->map_Tmax >= 0)) { why = "mapping tolerances must be >= 0"; return false; }
+  return true;
+}
+
+// Build all device tables of one mechanism into one contiguous blob.
+bool build_tables(const HostMech& hm, int wpc, std::vector<unsigned char>& blob, DevMech& dm, std::string& err) {
+  const int nsp = hm.nsp, nrx = hm.nrx, N = nsp + 1, ld = N + 1;
+  dm.nsp = nsp; dm.nrx = nrx; dm.N = N; dm.ld = ld; dm.wpc = wpc;
+  if (N * ld + 2 >= 65536) { err = "mechanism too large for 16-bit matrix indices (max 254 species)"; return false; }
+  // species
+  std::vector<double> W(nsp), iW(nsp), H0(nsp), cpa(nsp), hcpb(nsp), cpb(nsp), G0(nsp), G1(nsp), G2(nsp), G3(nsp), bW(nsp);
+  for (int k = 0; k < nsp; ++k) {
+    const double a = hm.a[k], b = hm.b[k];
+    W[k] = hm.W[k]; iW[k] = 1.0 / hm.W[k];
+    H0[k] = hm.hf[k] - a * kT0 - 0.5 * b * kT0 * kT0;          // h = H0 + a T + b/2 T^2
+    const double S0 = hm.s0[k] - a * std::log(kT0) - b * kT0;   // s = S0 + a ln T + b T
+    cpa[k] = a; cpb[k] = b; hcpb[k] = 0.5 * b;
+    G0[k] = H0[k] / kR; G1[k] = (a - S0) / kR; G2[k] = a / kR; G3[k] = b / (2.0 * kR);
+    bW[k] = b / hm.W[k];
+  }
+  // reactions
+  std::vector<double> lnA(nrx), beta(nrx), EaR(nrx);
+  std::vector<RxnMeta> meta(nrx);
+  std::vector<int32_t> eff_sp;
+  std::vector<double> eff_dm1;
+  std::vector<std::vector<int>> distinct(nrx);
+  int DS = 1;
+  for (int r = 0; r < nrx; ++r) {
+    const HostRxn& x = hm.rx[r];
+    lnA[r] = x.lnA; beta[r] = x.beta; EaR[r] = x.Ea / kR;
+    RxnMeta& mt = meta[r];
+    std::memset(&mt, 0, sizeof(mt));
+    for (int i = 0; i < 6; ++i) mt.sp[i] = -1;
+    auto& dl = distinct[r];
+    auto slot_of = [&](int k) {
+      for (int s = 0; s < int(dl.size()); ++s) if (dl[s] == k) return s;
+      dl.push_back(k);
+      return int(dl.size()) - 1;
+    };
+    mt.nr = uint8_t(x.r.size()); mt.np = uint8_t(x.p.size());
+    for (int i = 0; i < int(x.r.size()); ++i) { mt.sp[i] = int16_t(x.r[i]); mt.ds[i] = uint8_t(slot_of(x.r[i])); }
+    for (int i = 0; i < int(x.p.size()); ++i) { mt.sp[3 + i] = int16_t(x.p[i]); mt.ds[3 + i] = uint8_t(slot_of(x.p[i])); }
+    mt.dnu = int8_t(int(x.p.size()) - int(x.r.size()));
+    mt.flags = (x.rev ? RX_REV : 0) | (x.tb ? RX_TB : 0);
+    mt.nds = uint8_t(dl.size());
+    mt.eff_begin = int32_t(eff_sp.size());
+    if (x.tb && !x.eff.empty()) {
+      mt.flags |= RX_EFF;
+      mt.dslot_eff = mt.nds;
+      mt.nds += 1;
+      for (auto& e : x.eff) { eff_sp.push_back(e.first); eff_dm1.push_back(e.second - 1.0); }
+    }
+    mt.eff_end = int32_t(eff_sp.size());
+    DS = std::max(DS, int(mt.nds));
+  }
+  dm.DS = DS;
+  if (int64_t(nrx) * DS >= 65536) { err = "too many reactions for 16-bit D indices"; return false; }
+  // incidence and triple entries, partitioned by target species over the team's warps
+  std::vector<std::vector<Entry>> inc_w(wpc), tri_w(wpc);
+  for (int r = 0; r < nrx; ++r) {
+    const HostRxn& x = hm.rx[r];
+    std::map<int, int> nu;
+    for (int k : x.r) nu[k] -= 1;
+    for (int k : x.p) nu[k] += 1;
+    for (auto& kv : nu) {
+      const int k = kv.first, v = kv.second;
+      if (v == 0) continue;
+      if (v < -7 || v > 7) { err = "stoichiometric coefficient out of range"; return false; }
+      inc_w[k % wpc].push_back({k, pack_inc(k, r, v), double(v)});
+      const auto& dl = distinct[r];
+      for (int s = 0; s < int(dl.size()); ++s) {
+        const int j = dl[s];
+        tri_w[k % wpc].push_back({(1 + k) * ld + 1 + j, pack_tri((1 + k) * ld + 1 + j, r * DS + s),
+                                  v * W[k] / W[j]});
+      }
+      if (meta[r].flags & RX_EFF)
+        for (auto& e : x.eff) {
+          const int j = e.first;
+          tri_w[k % wpc].push_back({(1 + k) * ld + 1 + j,
+                                    pack_tri((1 + k) * ld + 1 + j, r * DS + meta[r].dslot_eff),
+                                    v * (e.second - 1.0) * W[k] / W[j]});
+        }
+    }
+  }
+  std::vector<uint32_t> inc, tri;
+  std::vector<double> incc, tric;
+  for (int w = 0; w < wpc; ++w) {
+    dm.inc_ptr[w] = int(inc.size() / 32);
+    build_rounds(inc_w[w], pack_inc(nsp, 0, 0), inc, incc);
+    dm.tri_ptr[w] = int(tri.size() / 32);
+    build_rounds(tri_w[w], pack_tri(N * ld, 0), tri, tric);
+  }
+  dm.inc_ptr[wpc] = int(inc.size() / 32);
+  dm.tri_ptr[wpc] = int(tri.size() / 32);
+  for (int w = wpc + 1; w < 5; ++w) { dm.inc_ptr[w] = dm.inc_ptr[wpc]; dm.tri_ptr[w] = dm.tri_ptr[wpc]; }
+  // blob
+  blob.clear();
+  auto put = [&](const void* p, size_t bytes) {
+    size_t o = (blob.size() + 255) & ~size_t(255);
+    blob.resize(o + bytes);
+    if (bytes) std::memcpy(blob.data() + o, p, bytes);
+    return o;
+  };
+  std::vector<size_t> offs;
+  for (auto* v : {&W, &iW, &H0, &cpa, &hcpb, &cpb, &G0, &G1, &G2, &G3, &bW}) offs.push_back(put(v->data(), v->size() * 8));
+  for (auto* v : {&lnA, &beta, &EaR}) offs.push_back(put(v->data(), v->size() * 8));
+  offs.push_back(put(meta.data(), meta.size() * sizeof(RxnMeta)));
+  offs.push_back(put(eff_sp.data(), eff_sp.size() * 4));
+  offs.push_back(put(eff_dm1.data(), eff_dm1.size() * 8));
+  offs.push_back(put(inc.data(), inc.size() * 4));
+  offs.push_back(put(tri.data(), tri.size() * 4));
+  offs.push_back(put(tric.data(), tric.size() * 8));
+  // store offsets as fake pointers; relocated after upload
+  auto P = [&](int i) { return reinterpret_cast<const double*>(offs[i]); };
+  dm.W = P(0); dm.iW = P(1); dm.H0 = P(2); dm.cpa = P(3); dm.hcpb = P(4); dm.cpb = P(5);
+  dm.G0 = P(6); dm.G1 = P(7); dm.G2 = P(8); dm.G3 = P(9); dm.bW = P(10);
+  dm.lnA = P(11); dm.beta = P(12); dm.EaR = P(13);
+  dm.meta = reinterpret_cast<const RxnMeta*>(offs[14]);
+  dm.eff_sp = reinterpret_cast<const int32_t*>(offs[15]);
+  dm.eff_dm1 = P(16);
+  dm.inc = reinterpret_cast<const uint32_t*>(offs[17]);
+  dm.tri = reinterpret_cast<const uint32_t*>(offs[18]);
+  dm.tri_coef = P(19);
+  return true;
+}
+
+template <class T>
+T* reloc(T* off, void* base) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + reinterpret_cast<size_t>(off));
+}
+
+void relocate(DevMech& dm, void* base) {
+  dm.W = reloc(dm.W, base); dm.iW = reloc(dm.iW, base); dm.H0 = reloc(dm.H0, base);
+  dm.cpa = reloc(dm.cpa, base); dm.hcpb = reloc(dm.hcpb, base); dm.cpb = reloc(dm.cpb, base);
+  dm.G0 = reloc(dm.G0, base); dm.G1 = reloc(dm.G1, base); dm.G2 = reloc(dm.G2, base); dm.G3 = reloc(dm.G3, base);
+  dm.bW = reloc(dm.bW, base); dm.lnA = reloc(dm.lnA, base); dm.beta = reloc(dm.beta, base);
+  dm.EaR = reloc(dm.EaR, base); dm.meta = reloc(dm.meta, base); dm.eff_sp = reloc(dm.eff_sp, base);
+  dm.eff_dm1 = reloc(dm.eff_dm1, base); dm.inc = reloc(dm.inc, base); dm.tri = reloc(dm.tri, base);
+  dm.tri_coef = reloc(dm.tri_coef, base);
+}
+
+int configure_launch(dlbchem_ctx* c) {
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetDeviceProperties");
+  c->num_sms = prop.multiProcessorCount;
+  const size_t team_bytes = size_t(c->L.total) * 8;
+  const size_t max_block = prop.sharedMemPerBlockOptin;
+  const int max_teams = c->wpc == 1 ? 4 : 1;
+  int teams = int(std::min<size_t>(max_teams, max_block / team_bytes));
+  if (teams < 1) return fail(c, DLBCHEM_BAD_MECH, "mechanism too large: one cell's workspace exceeds shared memory");
+  c->teams = teams;
+  c->smem_bytes = int(team_bytes * teams);
+  e = cudaFuncSetAttribute(dlb::rosenbrock_kernel_ptr(c->wpc), cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaFuncSetAttribute");
+  int bps = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, dlb::rosenbrock_kernel_ptr(c->wpc), 32 * c->wpc * teams, c->smem_bytes);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (bps < 1) return fail(c, DLBCHEM_BAD_MECH, "integrator kernel cannot be resident with this workspace");
+  c->blocks_per_sm = bps;
+  return DLBCHEM_OK;
+}
+
+int ensure_perm(dlbchem_ctx* c, int64_t n) {
+  if (n <= c->perm_cap) return DLBCHEM_OK;
+  if (c->d_perm) cudaFree(c->d_perm);
+  c->d_perm = nullptr;
+  c->perm_cap = 0;
+  if (cudaMalloc(&c->d_perm, size_t(n) * 4) != cudaSuccess) return fail(c, DLBCHEM_OOM, "workspace allocation failed");
+  c->perm_cap = n;
+  return DLBCHEM_OK;
+}
+
+__global__ void iota_kernel(int32_t* perm, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    perm[i] = int32_t(i);
+}
+
+}  // namespace
+
+extern "C" {
+
+int dlbchem_options_default(dlbchem_options* o) {
+  if (!o) return DLBCHEM_BAD_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->rtol = 1e-6; o->atol = 1e-10; o->max_steps = 100000; o->isothermal = 0; o->hmin_frac = 1e-20;
+  o->schedule = DLBCHEM_SCHED_PLAIN; o->chunk = 1; o->mapping = 0;
+  o->map_Ttol = 1e-4; o->map_Ytol = 1e-4; o->map_Tmax = 0.0;
+  return DLBCHEM_OK;
+}
+
+int dlbchem_create(const char* mech_path, const dlbchem_options* opt, dlbchem_ctx** out) {
+  g_create_err.clear();
+  if (!out) return fail(nullptr, DLBCHEM_BAD_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mech_path) return fail(nullptr, DLBCHEM_BAD_ARG, "mech_path is NULL");
+  dlbchem_options o;
+  dlbchem_options_default(&o);
+  if (opt) o = *opt;
+  std::string why;
+  if (!valid_opts(&o, why)) return fail(nullptr, DLBCHEM_BAD_ARG, why);
+  auto* c = new dlbchem_ctx;
+  c->opt = o;
+  if (!parse_mech(mech_path, c->hm, why)) { delete c; return fail(nullptr, DLBCHEM_BAD_MECH, why); }
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) { delete c; return fail(nullptr, DLBCHEM_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e)); }
+  c->wpc = (c->hm.nsp + 1 <= 64) ? 1 : 4;
+  std::vector<unsigned char> blob;
+  if (!build_tables(c->hm, c->wpc, blob, c->dm, why)) { delete c; return fail(nullptr, DLBCHEM_BAD_MECH, why); }
+  c->L = make_layout(c->hm.nsp, c->hm.nrx, c->dm.N, c->dm.ld, c->dm.DS);
+  if (cudaMalloc(&c->d_blob, blob.size()) != cudaSuccess || cudaMalloc(&c->d_counter, 64) != cudaSuccess) {
+    dlbchem_destroy(c);
+    return fail(nullptr, DLBCHEM_OOM, "device allocation of mechanism tables failed");
+  }
+  e = cudaMemcpy(c->d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { dlbchem_destroy(c); return fail(nullptr, DLBCHEM_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e)); }
+  relocate(c->dm, c->d_blob);
+  int rc = configure_launch(c);
+  if (rc != DLBCHEM_OK) { std::string m = c->err; dlbchem_destroy(c); return fail(nullptr, rc, m); }
+  *out = c;
+  return DLBCHEM_OK;
+}
+
+int dlbchem_set_options(dlbchem_ctx* c, const dlbchem_options* opt) {
+  if (!c || !opt) return DLBCHEM_BAD_ARG;
+  std::string why;
+  if (!valid_opts(opt, why)) return fail(c, DLBCHEM_BAD_ARG, why);
+  c->opt = *opt;
+  return DLBCHEM_OK;
+}
+
+int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, const double* p, const double* Y,
+                      double* T_out, double* Y_out, int32_t* steps, int32_t* status, const double* Yref,
+                      void* stream) {
+  if (!c) return DLBCHEM_BAD_ARG;
+  c->err.clear();
+  (void)Yref;
+  if (n < 0 || n > (int64_t(1) << 31) - 1) return fail(c, DLBCHEM_BAD_ARG, "ncells out of range");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(c, DLBCHEM_BAD_ARG, "dt must be positive and finite");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  c->last_stream = s;
+  for (int i = 0; i < 8; ++i) c->stats[i] = 0;
+  c->stats[2] = -1;
+  if (n == 0) return DLBCHEM_OK;
+  if (!T || !p || !Y || !T_out || !Y_out) return fail(c, DLBCHEM_BAD_ARG, "NULL array pointer");
+  KernelArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.m = c->dm;
+  a.P.rtol = c->opt.rtol; a.P.atol = c->opt.atol; a.P.hmin_frac = c->opt.hmin_frac; a.P.dt = dt;
+  a.P.max_steps = c->opt.max_steps; a.P.isothermal = c->opt.isothermal;
+  a.L = c->L;
+  a.n = n; a.T = T; a.p = p; a.Y = Y; a.Tout = T_out; a.Yout = Y_out; a.steps = steps; a.status = status;
+  const int threads = 32 * c->wpc * c->teams;
+  int64_t grid;
+  if (c->opt.schedule == DLBCHEM_SCHED_QUEUE) {
+    int rc = ensure_perm(c, n);
+    if (rc != DLBCHEM_OK) return rc;
+    iota_kernel<<<std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(c->d_perm, n);
+    cudaError_t e = cudaMemsetAsync(c->d_counter, 0, 8, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+    a.queue = 1; a.perm = c->d_perm; a.nqueue = n; a.counter = c->d_counter; a.chunk = c->opt.chunk;
+    grid = int64_t(c->num_sms) * c->blocks_per_sm;
+    grid = std::min<int64_t>(grid, (n + c->teams - 1) / c->teams);
+  } else {
+    grid = (n + c->teams - 1) / c->teams;
+  }
+  cudaError_t e = dlb::launch_rosenbrock(c->wpc, unsigned(grid), threads, c->smem_bytes, s, a);
+  if (e != cudaSuccess) return cuda_fail(c, e, "integrator launch");
+  c->stats[0] = n; c->stats[1] = 0; c->stats[2] = -1; c->stats[3] = 32 * c->wpc; c->stats[4] = c->teams;
+  c->stats[5] = grid; c->stats[6] = c->smem_bytes; c->stats[7] = 1;
+  return DLBCHEM_OK;
+}
+
+int dlbchem_integrate_host(dlbchem_ctx* c, int64_t n, double dt, const double* T, const double* p, const double* Y,
+                           double* T_out, double* Y_out, int32_t* steps, int32_t* status, const double* Yref,
+                           void* stream) {
+  if (!c) return DLBCHEM_BAD_ARG;
+  c->err.clear();
+  if (n < 0 || n > (int64_t(1) << 31) - 1) return fail(c, DLBCHEM_BAD_ARG, "ncells out of range");
+  if (n == 0) return DLBCHEM_OK;
+  if (!T || !p || !Y || !T_out || !Y_out) return fail(c, DLBCHEM_BAD_ARG, "NULL array pointer");
+  const int nsp = c->hm.nsp;
+  const int64_t nd = int64_t(2 * nsp + 3) * n + nsp;   // T, p, Y, Tout, Yout, Yref
+  if (n > c->stage_cap) {
+    if (c->d_stage) cudaFree(c->d_stage);
+    if (c->d_stage_i) cudaFree(c->d_stage_i);
+    c->d_stage = nullptr; c->d_stage_i = nullptr; c->stage_cap = 0;
+    if (cudaMalloc(&c->d_stage, size_t(nd) * 8) != cudaSuccess || cudaMalloc(&c->d_stage_i, size_t(2 * n) * 4) != cudaSuccess)
+      return fail(c, DLBCHEM_OOM, "staging allocation failed");
+    c->stage_cap = n;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* dT = c->d_stage;
+  double* dp = dT + n;
+  double* dY = dp + n;
+  double* dTo = dY + int64_t(nsp) * n;
+  double* dYo = dTo + n;
+  double* dYr = dYo + int64_t(nsp) * n;
+  int32_t* dsteps = c->d_stage_i;
+  int32_t* dstat = dsteps + n;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(dT, T, size_t(n) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(dp, p, size_t(n) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(dY, Y, size_t(nsp) * n * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(c, e, "host to device copy");
+  if (steps && (e = cudaMemcpyAsync(dsteps, steps, size_t(n) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(c, e, "host to device copy");
+  if (Yref && (e = cudaMemcpyAsync(dYr, Yref, size_t(nsp) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(c, e, "host to device copy");
+  int rc = dlbchem_integrate(c, n, dt, dT, dp, dY, dTo, dYo, steps ? dsteps : nullptr, dstat, Yref ? dYr : nullptr, s);
+  if (rc != DLBCHEM_OK) return rc;
+  if ((e = cudaMemcpyAsync(T_out, dTo, size_t(n) * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(Y_out, dYo, size_t(nsp) * n * 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(c, e, "device to host copy");
+  if (steps && (e = cudaMemcpyAsync(steps, dsteps, size_t(n) * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(c, e, "device to host copy");
+  if (status && (e = cudaMemcpyAsync(status, dstat, size_t(n) * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(c, e, "device to host copy");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  return DLBCHEM_OK;
+}
+
+int dlbchem_nspecies(const dlbchem_ctx* c) { return c ? c->hm.nsp : -1; }
+int dlbchem_nreactions(const dlbchem_ctx* c) { return c ? c->hm.nrx : -1; }
+
+int dlbchem_last_stats(dlbchem_ctx* c, int64_t out[8]) {
+  if (!c || !out) return DLBCHEM_BAD_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->last_stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  for (int i = 0; i < 8; ++i) out[i] = c->stats[i];
+  return DLBCHEM_OK;
+}
+
+const char* dlbchem_last_error(const dlbchem_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+void dlbchem_destroy(dlbchem_ctx* c) {
+  if (!c) return;
+  if (c->d_blob || c->d_perm || c->d_stage) cudaStreamSynchronize(c->last_stream);
+  if (c->d_blob) cudaFree(c->d_blob);
+  if (c->d_counter) cudaFree(c->d_counter);
+  if (c->d_perm) cudaFree(c->d_perm);
+  if (c->d_stage) cudaFree(c->d_stage);
+  if (c->d_stage_i) cudaFree(c->d_stage_i);
+  delete c;
+}
+
+}  // extern "C"

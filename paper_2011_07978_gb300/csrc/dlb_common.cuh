@@ -1,0 +1,138 @@
+// Device-side mechanism tables, per-team workspace layout and team primitives
+// of the batched Rosenbrock integrator (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dlb {
+
+constexpr double kR = 8.314462618;   // J/(mol K)
+constexpr double kRc = 82.05736;     // cm^3 atm/(mol K)
+constexpr double kT0 = 298.15;       // K
+
+// Rosenbrock coefficients: the L-stable 4-stage order-4(3) set of Hairer and
+// Wanner, Solving ODEs II, Sec. IV.7, Table 7.2, in the transformed variables
+// u_i (stage matrix 1/(h gamma) I - J, stage 4 reuses stage 3's f value).
+constexpr double kGamma = 0.57282;
+constexpr double kA21 = 2.0;
+constexpr double kA31 = 1.867943637803922, kA32 = 0.2344449711399156;
+constexpr double kC21 = -7.137615036412310;
+constexpr double kC31 = 2.580708087951457, kC32 = 0.6515950076447975;
+constexpr double kC41 = -2.137148994382534, kC42 = -0.3214669691237626, kC43 = -0.6949742501781779;
+constexpr double kM1 = 2.255570073418735, kM2 = 0.2870493262186792, kM3 = 0.4353179431840180,
+                 kM4 = 1.093502252409163;
+constexpr double kE1 = -0.2815431932141155, kE2 = -0.07276199124938920, kE3 = -0.1082196201495311,
+                 kE4 = -1.093502252409163;
+
+enum : int { CELL_OK = 0, CELL_MAPPED = 1, CELL_MAX_STEPS = -1, CELL_H_UNDERFLOW = -2, CELL_NONFINITE = -3 };
+
+// Per reaction, 32 bytes. Species slots are expanded by multiplicity
+// (2A -> slots A, A); sp[0..2] reactants, sp[3..5] products, -1 unused.
+struct RxnMeta {
+  int16_t sp[6];
+  uint8_t ds[6];        // distinct-participant (D) slot of each expanded slot
+  uint8_t nr, np;       // expanded reactant / product counts
+  int8_t dnu;           // np - nr
+  uint8_t flags;        // bit0 reversible, bit1 third-body, bit2 listed efficiencies
+  uint8_t nds;          // D slots in use (participants + 1 if listed efficiencies)
+  uint8_t dslot_eff;    // D slot holding (fwd - rev) for listed efficiencies
+  int32_t eff_begin;    // listed-efficiency range [eff_begin, eff_end)
+  int32_t eff_end;
+};
+static_assert(sizeof(RxnMeta) == 32, "RxnMeta layout");
+
+enum : uint8_t { RX_REV = 1, RX_TB = 2, RX_EFF = 4 };
+
+// Incidence entry (species k, reaction r, coefficient nu), packed:
+//   k in bits 20..31, r in bits 4..19, nu + 8 in bits 0..3.
+__host__ __device__ inline uint32_t pack_inc(int k, int r, int nu) {
+  return (uint32_t(k) << 20) | (uint32_t(r) << 4) | uint32_t(nu + 8);
+}
+// Jacobian triple: target index into M (bits 16..31) and D index (bits 0..15).
+__host__ __device__ inline uint32_t pack_tri(int e, int d) { return (uint32_t(e) << 16) | uint32_t(d); }
+
+struct DevMech {
+  int nsp, nrx, N, ld, DS, wpc;
+  // species
+  const double *W, *iW, *H0, *cpa, *hcpb, *cpb, *G0, *G1, *G2, *G3, *bW;
+  // reactions
+  const double *lnA, *beta, *EaR;
+  const RxnMeta* meta;
+  const int32_t* eff_sp;
+  const double* eff_dm1;
+  // incidence rounds: warp w of a team processes rounds [inc_ptr[w], inc_ptr[w+1]) of 32 entries
+  const uint32_t* inc;
+  int inc_ptr[5];
+  // Jacobian triple rounds, same partition
+  const uint32_t* tri;
+  const double* tri_coef;
+  int tri_ptr[5];
+};
+
+struct IntegParams {
+  double rtol, atol, hmin_frac, dt;
+  int32_t max_steps, isothermal;
+};
+
+// Offsets (in doubles) of one team's workspace inside dynamic shared memory.
+struct WsLayout {
+  int M, y0, f0, ys, fs, u, c, E, Einv, hk, wdot, vv, dwdT, uu, invd, q, sig, dqdT, dlt, D, scal, perm;
+  int total;  // doubles per team (perm is int32 at the end, counted in doubles)
+};
+
+__host__ inline WsLayout make_layout(int nsp, int nrx, int N, int ld, int DS) {
+  WsLayout L;
+  int o = 0;
+  auto take = [&](int n) { int r = o; o += (n + 1) & ~1; return r; };  // keep 16-byte alignment
+  L.M = take(N * ld + 2);
+  L.y0 = take(N);
+  L.f0 = take(N);
+  L.ys = take(N);
+  L.fs = take(N);
+  L.u = take(4 * N);
+  L.c = take(nsp + 1);
+  L.E = take(nsp + 1);
+  L.Einv = take(nsp + 1);
+  L.hk = take(nsp + 1);
+  L.wdot = take(nsp + 1);
+  L.vv = take(nsp + 1);
+  L.dwdT = take(nsp + 1);
+  L.uu = take(nsp + 1);
+  L.invd = take(N);
+  L.q = take(nrx);
+  L.sig = take(nrx);
+  L.dqdT = take(nrx);
+  L.dlt = take(nrx);
+  L.D = take(nrx * DS);
+  L.scal = take(32);
+  L.perm = take((N + 1) / 2 + 1);
+  L.total = o;
+  return L;
+}
+
+// Arguments of the integrator kernel (one struct, passed by value).
+struct KernelArgs {
+  DevMech m;
+  IntegParams P;
+  WsLayout L;
+  int64_t n;
+  const double* T;
+  const double* p;
+  const double* Y;
+  double* Tout;
+  double* Yout;
+  int32_t* steps;
+  int32_t* status;
+  // queue mode: cells perm[0..nqueue) are pulled in chunks through *counter
+  const int32_t* perm;
+  int64_t nqueue;
+  unsigned long long* counter;
+  int chunk;
+  int queue;
+};
+
+// Host-side launchers defined next to the kernels (integrator.cu).
+cudaError_t launch_rosenbrock(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
+const void* rosenbrock_kernel_ptr(int wpc);
+
+}  // namespace dlb

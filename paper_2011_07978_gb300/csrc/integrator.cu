@@ -1,0 +1,581 @@
+// Batched adaptive Rosenbrock integration of the per-cell chemistry ODE.
+//
+// Paper (arXiv 2011.07978) Sec. 1 / Sec. 2.1: every cell integrates its own
+// stiff ODE dPhi/dt = f(Phi) over the flow step dt; Sec. 2.2 stage 3 is this
+// solve. One team of threads (one warp, or four warps for mechanisms with
+// more than 64 unknowns) owns one cell at a time and keeps the whole cell in
+// shared memory: the dense iteration matrix M = I/(h gamma) - J, the stage
+// vectors and the per-species and per-reaction work arrays. Lanes split
+// species, reactions, matrix entries and rows; FP64 is the bottleneck on
+// GB300 (two FP64 FMA lanes per clock per SM, a warp instruction costs the
+// same whatever its active lanes), so every phase is laid out to keep all 32
+// lanes of a warp busy: flattened trailing updates in the LU, conflict-free
+// rounds of 32 for the sparse scatters.
+//
+// Every reduction runs in a fixed order, so a cell's result does not depend
+// on which team, CTA or launch integrates it (plain and queued schedules
+// agree bit for bit).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "dlb_common.cuh"
+
+namespace dlb {
+
+template <int WPC>
+struct Team {
+  static constexpr int TS = 32 * WPC;
+  int tid, warp, lane, bar_id;
+  double* red;          // 2*WPC doubles of cross-warp reduction scratch
+  mutable int parity;
+
+  __device__ __forceinline__ void sync() const {
+    if (WPC == 1) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(TS) : "memory");
+    }
+  }
+  // Sum over the team; every thread receives the bitwise-identical result.
+  __device__ __forceinline__ double sum(double x) const {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (WPC == 1) return x;
+    double* buf = red + parity * WPC;
+    parity ^= 1;
+    if (lane == 0) buf[warp] = x;
+    sync();
+    double s = buf[0];
+#pragma unroll
+    for (int w = 1; w < WPC; ++w) s += buf[w];
+    return s;
+  }
+  __device__ __forceinline__ int any(int x) const {
+    x = __any_sync(0xffffffffu, x);
+    if (WPC == 1) return x;
+    double* buf = red + parity * WPC;
+    parity ^= 1;
+    if (lane == 0) buf[warp] = x ? 1.0 : 0.0;
+    sync();
+    int r = 0;
+#pragma unroll
+    for (int w = 0; w < WPC; ++w) r |= buf[w] != 0.0;
+    return r;
+  }
+};
+
+struct WS {
+  double *M, *y0, *f0, *ys, *fs, *u, *c, *E, *Einv, *hk, *wdot, *vv, *dwdT, *uu, *invd, *q, *sig, *dqdT, *dlt,
+      *D, *scal;
+  int* perm;
+};
+
+__device__ __forceinline__ WS carve(double* base, const WsLayout& L) {
+  WS w;
+  w.M = base + L.M; w.y0 = base + L.y0; w.f0 = base + L.f0; w.ys = base + L.ys; w.fs = base + L.fs;
+  w.u = base + L.u; w.c = base + L.c; w.E = base + L.E; w.Einv = base + L.Einv; w.hk = base + L.hk;
+  w.wdot = base + L.wdot; w.vv = base + L.vv; w.dwdT = base + L.dwdT; w.uu = base + L.uu;
+  w.invd = base + L.invd; w.q = base + L.q; w.sig = base + L.sig; w.dqdT = base + L.dqdT; w.dlt = base + L.dlt;
+  w.D = base + L.D; w.scal = base + L.scal; w.perm = reinterpret_cast<int*>(base + L.perm);
+  return w;
+}
+
+// Mixture scalars shared by one rate evaluation.
+struct Mix {
+  double T, iT, lnT, S, rho, irho;
+};
+
+// ---------------------------------------------------------------------------
+// Rates. Species pass: concentrations c_k = rho Y_k / W_k, E_k = exp(-g_k/RT)
+// and 1/E_k (equilibrium constants as products of per-species factors:
+// 1/K_c = prod_reac E^nu' prod_prod (1/E)^nu'' (R_c T / p0)^dnu), molar h_k.
+// Reaction pass: k_f = exp(ln A + b ln T - Ea/(R T)), q = [M](fwd - rev).
+// With JAC, also d q / d c for each distinct participant (D slots), the
+// homogeneity sum sigma = sum_j c_j dq/dc_j, dq/dT at fixed c, and the
+// third-body difference fwd - rev. Then the incidence rounds gather
+// wdot_k = sum_r nu_kr q_r (and v, dwdT, u).
+// ---------------------------------------------------------------------------
+template <int WPC, bool JAC>
+__device__ __noinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm, const WS& w, const double* yv,
+                                        double P1, Mix& mx) {
+  constexpr int TS = 32 * WPC;
+  const int nsp = m.nsp, nrx = m.nrx;
+  const double T = yv[0];
+  const double iT = 1.0 / T;
+  const double lnT = log(T);
+  double s = 0.0;
+  for (int k = tm.tid; k < nsp; k += TS) s = fma(yv[1 + k], m.iW[k], s);
+  const double S = tm.sum(s);
+  const double rho = P1 * iT / S;
+  mx.T = T; mx.iT = iT; mx.lnT = lnT; mx.S = S; mx.rho = rho; mx.irho = (T * S) / P1;
+  for (int k = tm.tid; k < nsp; k += TS) {
+    w.c[k] = rho * yv[1 + k] * m.iW[k];
+    const double e = exp(fma(m.G2[k], lnT, fma(m.G3[k], T, -fma(m.G0[k], iT, m.G1[k]))));
+    w.E[k] = e;
+    w.Einv[k] = 1.0 / e;
+    w.hk[k] = fma(T, fma(m.hcpb[k], T, m.cpa[k]), m.H0[k]);
+  }
+  if (tm.tid == 0) w.c[nsp] = 0.0;
+  tm.sync();
+  const double Ctot = P1 * iT;          // sum_k c_k (unit efficiencies)
+  const double C0inv = (kRc / 1.0) * T; // R_c T / p0, p0 = 1 atm
+  const double C0 = 1.0 / C0inv;
+  for (int r = tm.tid; r < nrx; r += TS) {
+    const RxnMeta mt = m.meta[r];
+    const double kf = exp(m.lnA[r] + m.beta[r] * lnT - m.EaR[r] * iT);
+    double cr[3], cq[3];
+    double pf = kf;
+    for (int i = 0; i < mt.nr; ++i) { cr[i] = w.c[mt.sp[i]]; pf *= cr[i]; }
+    double pr = 0.0, kr = 0.0;
+    if (mt.flags & RX_REV) {
+      kr = kf;
+      for (int i = 0; i < mt.nr; ++i) kr *= w.E[mt.sp[i]];
+      for (int i = 0; i < mt.np; ++i) kr *= w.Einv[mt.sp[3 + i]];
+      for (int i = 0; i < mt.dnu; ++i) kr *= C0inv;
+      for (int i = 0; i < -mt.dnu; ++i) kr *= C0;
+      pr = kr;
+      for (int i = 0; i < mt.np; ++i) { cq[i] = w.c[mt.sp[3 + i]]; pr *= cq[i]; }
+    }
+    double Mf = 1.0;
+    if (mt.flags & RX_TB) {
+      Mf = Ctot;
+      for (int e = mt.eff_begin; e < mt.eff_end; ++e) Mf = fma(m.eff_dm1[e], w.c[m.eff_sp[e]], Mf);
+    }
+    w.q[r] = Mf * (pf - pr);
+    if (JAC) {
+      double* D = w.D + r * m.DS;
+      for (int s2 = 0; s2 < mt.nds; ++s2) D[s2] = 0.0;
+      // d/dc of prod over the expanded slots: product of the other slots
+      for (int i = 0; i < mt.nr; ++i) {
+        double t = kf * Mf;
+        for (int l = 0; l < mt.nr; ++l)
+          if (l != i) t *= cr[l];
+        D[mt.ds[i]] += t;
+      }
+      if (mt.flags & RX_REV) {
+        for (int i = 0; i < mt.np; ++i) {
+          double t = kr * Mf;
+          for (int l = 0; l < mt.np; ++l)
+            if (l != i) t *= cq[l];
+          D[mt.ds[3 + i]] -= t;
+        }
+      }
+      const int tb = (mt.flags & RX_TB) ? 1 : 0;
+      if (mt.flags & RX_EFF) D[mt.dslot_eff] = pf - pr;
+      w.sig[r] = Mf * ((mt.nr + tb) * pf - (mt.np + tb) * pr);
+      const double dlnkf = fma(m.EaR[r], iT * iT, m.beta[r] * iT);
+      double dq = pf * dlnkf;
+      if (mt.flags & RX_REV) {
+        double dH = 0.0;
+        for (int i = 0; i < mt.np; ++i) dH += w.hk[mt.sp[3 + i]];
+        for (int i = 0; i < mt.nr; ++i) dH -= w.hk[mt.sp[i]];
+        const double dlnKc = dH * iT * iT * (1.0 / kR) - mt.dnu * iT;
+        dq -= pr * (dlnkf - dlnKc);
+      }
+      w.dqdT[r] = Mf * dq;
+      w.dlt[r] = tb ? (pf - pr) : 0.0;
+    }
+  }
+  for (int k = tm.tid; k <= nsp; k += TS) {
+    w.wdot[k] = 0.0;
+    if (JAC) { w.vv[k] = 0.0; w.dwdT[k] = 0.0; w.uu[k] = 0.0; }
+  }
+  tm.sync();
+  // incidence rounds: within a round every lane owns a distinct species
+  const int r0 = m.inc_ptr[tm.warp], r1 = m.inc_ptr[tm.warp + 1];
+  for (int rd = r0; rd < r1; ++rd) {
+    const uint32_t e = m.inc[rd * 32 + tm.lane];
+    const int k = int(e >> 20), r = int((e >> 4) & 0xffffu);
+    const double nu = double(int(e & 15u) - 8);
+    w.wdot[k] = fma(nu, w.q[r], w.wdot[k]);
+    if (JAC) {
+      w.vv[k] = fma(nu, w.sig[r], w.vv[k]);
+      w.dwdT[k] = fma(nu, w.dqdT[r], w.dwdT[k]);
+      w.uu[k] = fma(nu, w.dlt[r], w.uu[k]);
+    }
+    __syncwarp();
+  }
+  tm.sync();
+}
+
+// f = (f_T, f_Y): f_Y_k = W_k wdot_k / rho, f_T = -sum h_k wdot_k / (rho cp_mass).
+// Returns Q = sum h_k wdot_k and cp_mass through the references.
+template <int WPC>
+__device__ __forceinline__ void finish_f(const DevMech& m, const Team<WPC>& tm, const WS& w, const double* yv,
+                                         const Mix& mx, bool iso, double* f, double& Q, double& cpm) {
+  constexpr int TS = 32 * WPC;
+  double q = 0.0, cp = 0.0;
+  for (int k = tm.tid; k < m.nsp; k += TS) {
+    f[1 + k] = m.W[k] * w.wdot[k] * mx.irho;
+    q = fma(w.hk[k], w.wdot[k], q);
+    cp = fma(yv[1 + k] * m.iW[k], fma(m.cpb[k], mx.T, m.cpa[k]), cp);
+  }
+  Q = tm.sum(q);
+  cpm = tm.sum(cp);
+  if (tm.tid == 0) f[0] = iso ? 0.0 : -Q * mx.irho / cpm;
+  tm.sync();
+}
+
+template <int WPC>
+__device__ __forceinline__ void eval_f(const DevMech& m, const Team<WPC>& tm, const WS& w, const double* yv,
+                                       double P1, bool iso, double* f) {
+  Mix mx;
+  eval_rates<WPC, false>(m, tm, w, yv, P1, mx);
+  double Q, cpm;
+  finish_f<WPC>(m, tm, w, yv, mx, iso, f, Q, cpm);
+}
+
+// ---------------------------------------------------------------------------
+// Jacobian and iteration matrix M = I/(h gamma) - J at y0 (also f0 = f(y0)).
+// Rows/columns: 0 = T, 1 + k = Y_k. Species block:
+//   J_kj = (W_k / W_j) dwdot_k/dc_j + r_k / W_j,
+//   r_k = W_k (u_k + (wdot_k - v_k) / (rho S)),
+// where the sparse part comes from the triple rounds (coefficients
+// nu_kr W_k / W_j applied to the D slots), u is the unit-efficiency
+// third-body term and v_k = sum_j c_j dwdot_k/dc_j the chain rule through
+// rho(T, Y).
+// ---------------------------------------------------------------------------
+template <int WPC>
+__device__ __noinline__ void assemble(const DevMech& m, const Team<WPC>& tm, const WS& w, double P1, bool iso,
+                                      double ihg) {
+  constexpr int TS = 32 * WPC;
+  const int nsp = m.nsp, N = m.N, ld = m.ld;
+  Mix mx;
+  eval_rates<WPC, true>(m, tm, w, w.y0, P1, mx);
+  double Q, cpm;
+  finish_f<WPC>(m, tm, w, w.y0, mx, iso, w.f0, Q, cpm);
+  const int ntot = N * ld + 2;
+  for (int i = tm.tid; i < ntot; i += TS) w.M[i] = 0.0;
+  tm.sync();
+  const int t0 = m.tri_ptr[tm.warp], t1 = m.tri_ptr[tm.warp + 1];
+  for (int rd = t0; rd < t1; ++rd) {
+    const uint32_t e = m.tri[rd * 32 + tm.lane];
+    const double cf = m.tri_coef[rd * 32 + tm.lane];
+    const int tgt = int(e >> 16), d = int(e & 0xffffu);
+    w.M[tgt] = fma(cf, w.D[d], w.M[tgt]);
+    __syncwarp();
+  }
+  tm.sync();
+  // scalars for the T row / column
+  double hv = 0.0, hu = 0.0, dc = 0.0, tt = 0.0;
+  for (int k = tm.tid; k < nsp; k += TS) {
+    hv = fma(w.hk[k], w.vv[k], hv);
+    hu = fma(w.hk[k], w.uu[k], hu);
+    dc = fma(w.y0[1 + k], m.bW[k], dc);
+    const double cpk = fma(m.cpb[k], mx.T, m.cpa[k]);
+    tt = fma(cpk, w.wdot[k], fma(w.hk[k], fma(-w.vv[k], mx.iT, w.dwdT[k]), tt));
+  }
+  const double Hv = tm.sum(hv), Hu = tm.sum(hu), dcpm = tm.sum(dc), Tsum = tm.sum(tt);
+  const double irS = mx.irho / mx.S;
+  const double icpm = 1.0 / cpm;
+  // r_k into E, h_k/W_k into Einv (both free after the rate pass); T column
+  // M[1+k][0] = -J_kT, J_kT = W_k/rho (dwdT_k + (wdot_k - v_k)/T)
+  for (int k = tm.tid; k < nsp; k += TS) {
+    w.E[k] = m.W[k] * fma(w.wdot[k] - w.vv[k], irS, w.uu[k]);
+    w.Einv[k] = w.hk[k] * m.iW[k];
+    w.M[(1 + k) * ld] = -m.W[k] * mx.irho * fma(w.wdot[k] - w.vv[k], mx.iT, w.dwdT[k]);
+  }
+  tm.sync();
+  // T row: J_Tj = (1/cp) [ -sum_k (h_k/W_k) Shat_kj + (1/W_j)(-Hu + (Hv - Q)/(rho S) + Q cp_j/(rho cp)) ]
+  for (int j = tm.tid; j < nsp; j += TS) {
+    double hs = 0.0;
+    for (int k = 0; k < nsp; ++k) hs = fma(w.Einv[k], w.M[(1 + k) * ld + 1 + j], hs);
+    const double cpj = fma(m.cpb[j], mx.T, m.cpa[j]);
+    const double bracket = fma(Q * cpj, mx.irho * icpm, fma(Hv - Q, irS, -Hu));
+    const double JT = icpm * fma(m.iW[j], bracket, -hs);
+    w.M[1 + j] = iso ? 0.0 : -JT;
+  }
+  if (tm.tid == 0) {
+    // J_TT = -(1/(rho cp)) sum_k (cp_k wdot_k + h_k dwdot_k/dT) - Q (1/(rho cp T) - dcp/dT/(rho cp^2))
+    const double JTT = -mx.irho * icpm * Tsum - Q * mx.irho * icpm * (mx.iT - dcpm * icpm);
+    w.M[0] = iso ? ihg : ihg - JTT;
+  }
+  tm.sync();
+  // species block: M = delta/(h gamma) - (Shat_kj + r_k / W_j)
+  const int nn = nsp * nsp;
+  for (int e = tm.tid; e < nn; e += TS) {
+    const int k = e / nsp, j = e - k * nsp;
+    const int idx = (1 + k) * ld + 1 + j;
+    double v = -fma(w.E[k], m.iW[j], w.M[idx]);
+    if (k == j) v += ihg;
+    w.M[idx] = v;
+  }
+  tm.sync();
+}
+
+// ---------------------------------------------------------------------------
+// Dense LU with partial pivoting, in place, row-major with leading dim ld.
+// P M = L D U~ with L unit lower (multipliers below the diagonal), D the
+// pivots (their inverses kept in invd) and U~ = D^-1 U unit upper: each row
+// of U is scaled by its inverse pivot one step after it is used, so the
+// triangular solves need no division. The pivot is the first row of largest
+// |M_ik| (compared through the IEEE bit pattern, which orders |x| exactly).
+// Returns false if a pivot is zero.
+// ---------------------------------------------------------------------------
+template <int WPC>
+__device__ __noinline__ bool lu_factor(const Team<WPC>& tm, double* M, int N, int ld, double* invd, int* perm) {
+  constexpr int TS = 32 * WPC;
+  for (int i = tm.tid; i < N; i += TS) perm[i] = i;
+  bool singular = false;
+  tm.sync();
+  for (int k = 0; k < N; ++k) {
+    if (k > 0) {
+      const double iv = invd[k - 1];
+      for (int j = k + tm.tid; j < N; j += TS) M[(k - 1) * ld + j] *= iv;
+    }
+    unsigned long long best = 0ull;
+    int bi = k;
+    for (int i = k + tm.tid; i < N; i += TS) {
+      const unsigned long long key = __double_as_longlong(M[i * ld + k]) & 0x7fffffffffffffffull;
+      if (key > best) { best = key; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (WPC > 1) {
+      double* buf = tm.red + tm.parity * WPC;
+      tm.parity ^= 1;
+      int* ibuf = reinterpret_cast<int*>(buf);
+      unsigned long long* kbuf = reinterpret_cast<unsigned long long*>(tm.red + 2 * WPC);
+      if (tm.lane == 0) { kbuf[tm.warp] = best; ibuf[2 * tm.warp] = bi; }
+      tm.sync();
+      best = kbuf[0]; bi = ibuf[0];
+      for (int wv = 1; wv < WPC; ++wv) {
+        const unsigned long long ob = kbuf[wv];
+        const int oi = ibuf[2 * wv];
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      tm.sync();
+    }
+    if (bi != k) {
+      for (int j = tm.tid; j < N; j += TS) {
+        const double a = M[k * ld + j];
+        M[k * ld + j] = M[bi * ld + j];
+        M[bi * ld + j] = a;
+      }
+      if (tm.tid == 0) { const int t = perm[k]; perm[k] = perm[bi]; perm[bi] = t; }
+    }
+    tm.sync();
+    const double d = M[k * ld + k];
+    if (d == 0.0) singular = true;
+    const double inv = 1.0 / d;
+    if (tm.tid == 0) invd[k] = inv;
+    for (int i = k + 1 + tm.tid; i < N; i += TS) M[i * ld + k] *= inv;
+    tm.sync();
+    const int wd = N - 1 - k;
+    const int tot = wd * wd;
+    for (int e = tm.tid; e < tot; e += TS) {
+      const int ii = e / wd, jj = e - ii * wd;
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      M[i * ld + j] = fma(-M[i * ld + k], M[k * ld + j], M[i * ld + j]);
+    }
+    tm.sync();
+  }
+  return !singular;
+}
+
+// x = M^-1 b with the factors above; b and x are distinct team vectors.
+template <int WPC>
+__device__ __noinline__ void lu_solve(const Team<WPC>& tm, const double* M, int N, int ld, const double* invd,
+                                      const int* perm, const double* b, double* x) {
+  constexpr int TS = 32 * WPC;
+  for (int i = tm.tid; i < N; i += TS) x[i] = b[perm[i]];
+  tm.sync();
+  for (int j = 0; j < N - 1; ++j) {
+    const double xj = x[j];
+    for (int i = j + 1 + tm.tid; i < N; i += TS) x[i] = fma(-M[i * ld + j], xj, x[i]);
+    tm.sync();
+  }
+  for (int i = tm.tid; i < N; i += TS) x[i] *= invd[i];
+  tm.sync();
+  for (int j = N - 1; j > 0; --j) {
+    const double xj = x[j];
+    for (int i = tm.tid; i < j; i += TS) x[i] = fma(-M[i * ld + j], xj, x[i]);
+    tm.sync();
+  }
+}
+
+// weighted RMS norm sqrt(sum (v/sc)^2 / N) over a team vector
+template <int WPC>
+__device__ __forceinline__ double wrms(const Team<WPC>& tm, const double* v, const double* sc, int N) {
+  double s = 0.0;
+  for (int i = tm.tid; i < N; i += 32 * WPC) { const double r = v[i] / sc[i]; s = fma(r, r, s); }
+  return sqrt(tm.sum(s) / N);
+}
+
+// Starting step (Hairer, Norsett, Wanner, Solving ODEs I, Sec. II.4) with the
+// order-3 error exponent 1/4 and fallbacks scaled by dt. Uses ys, fs, u.
+template <int WPC>
+__device__ double initial_step(const DevMech& m, const Team<WPC>& tm, const WS& w, const IntegParams& P,
+                               double P1, bool iso) {
+  constexpr int TS = 32 * WPC;
+  const int N = m.N;
+  double* sc = w.u;
+  for (int i = tm.tid; i < N; i += TS) sc[i] = fma(P.rtol, fabs(w.y0[i]), P.atol);
+  tm.sync();
+  const double d0 = wrms(tm, w.y0, sc, N), d1 = wrms(tm, w.f0, sc, N);
+  double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 * P.dt : 0.01 * d0 / d1;
+  h0 = fmin(h0, P.dt);
+  for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(h0, w.f0[i], w.y0[i]);
+  tm.sync();
+  eval_f<WPC>(m, tm, w, w.ys, P1, iso, w.fs);
+  double* df = w.u + N;
+  for (int i = tm.tid; i < N; i += TS) df[i] = w.fs[i] - w.f0[i];
+  tm.sync();
+  const double d2 = wrms(tm, df, sc, N) / h0;
+  if (!isfinite(d2)) return h0;
+  const double dm = fmax(d1, d2);
+  const double h1 = (dm <= 1e-15) ? fmax(1e-6 * P.dt, h0 * 1e-3) : pow(0.01 / dm, 0.25);
+  return fmin(fmin(100.0 * h0, h1), P.dt);
+}
+
+// Integrate one cell over [0, dt] (the oracle's algorithm step for step).
+template <int WPC>
+__device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Team<WPC>& tm, const WS& w,
+                               int64_t cell, int64_t n, const double* __restrict__ Tin,
+                               const double* __restrict__ pin, const double* __restrict__ Yin,
+                               double* __restrict__ Tout, double* __restrict__ Yout, int32_t* __restrict__ steps_out,
+                               int32_t* __restrict__ status_out) {
+  constexpr int TS = 32 * WPC;
+  const int N = m.N;
+  const bool iso = P.isothermal != 0;
+  for (int i = tm.tid; i < N; i += TS) w.y0[i] = (i == 0) ? Tin[cell] : Yin[int64_t(i - 1) * n + cell];
+  const double p = pin[cell];
+  tm.sync();
+  int bad = 0;
+  for (int i = tm.tid; i < N; i += TS) bad |= !isfinite(w.y0[i]);
+  bad |= !(w.y0[0] > 0.0) || !(p > 0.0) || !isfinite(p);
+  bad = tm.any(bad);
+  int status = CELL_OK, steps = 0;
+  if (!bad) {
+    const double P1 = 1e-6 * p / kR;
+    eval_f<WPC>(m, tm, w, w.y0, P1, iso, w.f0);
+    double h = initial_step<WPC>(m, tm, w, P, P1, iso);
+    const double dt = P.dt;
+    double t = 0.0;
+    bool rejected_last = false;
+    double* u1 = w.u;
+    double* u2 = w.u + N;
+    double* u3 = w.u + 2 * N;
+    double* u4 = w.u + 3 * N;
+    while (t < dt) {
+      if (steps >= P.max_steps) { status = CELL_MAX_STEPS; break; }
+      if ((dt - t) - h <= 1e-12 * dt) h = dt - t;
+      if (h < P.hmin_frac * dt) { status = CELL_H_UNDERFLOW; break; }
+      ++steps;
+      const double ih = 1.0 / h;
+      assemble<WPC>(m, tm, w, P1, iso, ih * (1.0 / kGamma));
+      const bool ok = lu_factor<WPC>(tm, w.M, N, m.ld, w.invd, w.perm);
+      // stage 1
+      lu_solve<WPC>(tm, w.M, N, m.ld, w.invd, w.perm, w.f0, u1);
+      // stage 2
+      for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(kA21, u1[i], w.y0[i]);
+      tm.sync();
+      eval_f<WPC>(m, tm, w, w.ys, P1, iso, w.fs);
+      for (int i = tm.tid; i < N; i += TS) w.fs[i] = fma(kC21 * ih, u1[i], w.fs[i]);
+      tm.sync();
+      lu_solve<WPC>(tm, w.M, N, m.ld, w.invd, w.perm, w.fs, u2);
+      // stage 3
+      for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(kA31, u1[i], fma(kA32, u2[i], w.y0[i]));
+      tm.sync();
+      eval_f<WPC>(m, tm, w, w.ys, P1, iso, w.fs);
+      for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(ih, fma(kC31, u1[i], kC32 * u2[i]), w.fs[i]);
+      tm.sync();
+      lu_solve<WPC>(tm, w.M, N, m.ld, w.invd, w.perm, w.ys, u3);
+      // stage 4 (same f as stage 3)
+      for (int i = tm.tid; i < N; i += TS)
+        w.ys[i] = fma(ih, fma(kC41, u1[i], fma(kC42, u2[i], kC43 * u3[i])), w.fs[i]);
+      tm.sync();
+      lu_solve<WPC>(tm, w.M, N, m.ld, w.invd, w.perm, w.ys, u4);
+      // new state (ys) and error estimate
+      double acc = 0.0;
+      for (int i = tm.tid; i < N; i += TS) {
+        const double yn = fma(kM1, u1[i], fma(kM2, u2[i], fma(kM3, u3[i], fma(kM4, u4[i], w.y0[i]))));
+        const double er = fma(kE1, u1[i], fma(kE2, u2[i], fma(kE3, u3[i], kE4 * u4[i])));
+        const double sc = fma(P.rtol, fmax(fabs(w.y0[i]), fabs(yn)), P.atol);
+        const double r = er / sc;
+        acc = fma(r, r, acc);
+        w.ys[i] = yn;
+      }
+      double errn = sqrt(tm.sum(acc) / N);
+      if (!ok) errn = nan("");
+      if (errn <= 1.0) {
+        double fac = fmin(5.0, fmax(0.2, 0.9 * pow(errn, -0.25)));
+        if (rejected_last) fac = fmin(fac, 1.0);
+        t = (t + h >= dt) ? dt : t + h;
+        for (int i = tm.tid; i < N; i += TS) w.y0[i] = w.ys[i];
+        tm.sync();
+        rejected_last = false;
+        h *= fac;
+      } else {
+        const double fac = isfinite(errn) ? fmax(0.2, 0.9 * pow(errn, -0.25)) : 0.2;
+        rejected_last = true;
+        h *= fac;
+      }
+    }
+  }
+  for (int i = tm.tid; i < N; i += TS) {
+    if (i == 0) Tout[cell] = w.y0[0];
+    else Yout[int64_t(i - 1) * n + cell] = w.y0[i];
+  }
+  if (tm.tid == 0) {
+    if (steps_out) steps_out[cell] = steps;
+    if (status_out) status_out[cell] = bad ? CELL_NONFINITE : status;
+  }
+  tm.sync();
+}
+
+
+template <int WPC>
+__global__ void __launch_bounds__(128) rosenbrock_kernel(const KernelArgs a) {
+  extern __shared__ __align__(16) double smem[];
+  constexpr int TS = 32 * WPC;
+  const int teams = blockDim.x / TS;
+  const int team = threadIdx.x / TS;
+  Team<WPC> tm;
+  tm.tid = threadIdx.x % TS;
+  tm.warp = tm.tid >> 5;
+  tm.lane = threadIdx.x & 31;
+  tm.bar_id = 1 + team;
+  tm.parity = 0;
+  double* base = smem + size_t(team) * a.L.total;
+  WS w = carve(base, a.L);
+  tm.red = w.scal;
+  if (!a.queue) {
+    const int64_t cell = int64_t(blockIdx.x) * teams + team;
+    if (cell < a.n)
+      integrate_cell<WPC>(a.m, a.P, tm, w, cell, a.n, a.T, a.p, a.Y, a.Tout, a.Yout, a.steps, a.status);
+    return;
+  }
+  volatile int64_t* slot = reinterpret_cast<volatile int64_t*>(w.scal + 24);
+  for (;;) {
+    if (tm.tid == 0) *slot = int64_t(atomicAdd(a.counter, (unsigned long long)a.chunk));
+    tm.sync();
+    const int64_t first = *slot;
+    tm.sync();
+    if (first >= a.nqueue) break;
+    const int64_t last = min(first + int64_t(a.chunk), a.nqueue);
+    for (int64_t qi = first; qi < last; ++qi) {
+      const int64_t cell = a.perm[qi];
+      integrate_cell<WPC>(a.m, a.P, tm, w, cell, a.n, a.T, a.p, a.Y, a.Tout, a.Yout, a.steps, a.status);
+    }
+  }
+}
+
+cudaError_t launch_rosenbrock(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a) {
+  if (wpc == 1) rosenbrock_kernel<1><<<grid, threads, smem, s>>>(a);
+  else rosenbrock_kernel<4><<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+const void* rosenbrock_kernel_ptr(int wpc) {
+  return wpc == 1 ? reinterpret_cast<const void*>(&rosenbrock_kernel<1>)
+                  : reinterpret_cast<const void*>(&rosenbrock_kernel<4>);
+}
+
+}  // namespace dlb

@@ -1,0 +1,155 @@
+"""Thin ctypes binding of libdlbchem (include/dlbchem.h), same entry-point names.
+
+Only argument marshalling lives here: every step of the chemistry runs in the
+library's CUDA kernels. PyTorch supplies device memory and streams. If the
+library is missing the import fails; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdlbchem.so")
+
+OK, BAD_ARG, BAD_MECH, CUDA, OOM = 0, 1, 2, 3, 4
+CELL_OK, CELL_MAPPED, CELL_MAX_STEPS, CELL_H_UNDERFLOW, CELL_NONFINITE = 0, 1, -1, -2, -3
+SCHED_PLAIN, SCHED_QUEUE = 0, 1
+
+
+class dlbchem_options(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("max_steps", ctypes.c_int32),
+                ("isothermal", ctypes.c_int32), ("hmin_frac", ctypes.c_double), ("schedule", ctypes.c_int32),
+                ("chunk", ctypes.c_int32), ("mapping", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("map_Ttol", ctypes.c_double), ("map_Ytol", ctypes.c_double), ("map_Tmax", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libdlbchem.so (built by paper_2011_07978_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    lib.dlbchem_options_default.argtypes = [ctypes.POINTER(dlbchem_options)]
+    lib.dlbchem_create.argtypes = [ctypes.c_char_p, ctypes.POINTER(dlbchem_options), ctypes.POINTER(_vp)]
+    lib.dlbchem_set_options.argtypes = [_vp, ctypes.POINTER(dlbchem_options)]
+    sig = [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    lib.dlbchem_integrate.argtypes = sig
+    lib.dlbchem_integrate_host.argtypes = sig
+    lib.dlbchem_nspecies.argtypes = [_vp]
+    lib.dlbchem_nreactions.argtypes = [_vp]
+    lib.dlbchem_last_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.dlbchem_last_error.argtypes = [_vp]
+    lib.dlbchem_last_error.restype = ctypes.c_char_p
+    lib.dlbchem_destroy.argtypes = [_vp]
+    _lib = lib
+    return lib
+
+
+def options_default() -> dlbchem_options:
+    o = dlbchem_options()
+    load().dlbchem_options_default(ctypes.byref(o))
+    return o
+
+
+class DlbchemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dlbchem error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One loaded mechanism on the current CUDA device (dlbchem_create)."""
+
+    def __init__(self, mech_path: str, **opts):
+        lib = load()
+        o = options_default()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        h = _vp()
+        rc = lib.dlbchem_create(mech_path.encode(), ctypes.byref(o), ctypes.byref(h))
+        if rc != OK:
+            raise DlbchemError(rc, lib.dlbchem_last_error(None).decode())
+        self._h = h
+        self.opts = o
+        self.nsp = lib.dlbchem_nspecies(h)
+        self.nrx = lib.dlbchem_nreactions(h)
+
+    def set_options(self, **opts):
+        o = dlbchem_options.from_buffer_copy(self.opts)
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        self._check(load().dlbchem_set_options(self._h, ctypes.byref(o)))
+        self.opts = o
+
+    def _check(self, rc):
+        if rc != OK:
+            raise DlbchemError(rc, load().dlbchem_last_error(self._h).decode())
+
+    def integrate(self, T, p, Y, dt, T_out=None, Y_out=None, steps=None, status=None, Yref=None, stream=None):
+        """dlbchem_integrate on CUDA tensors (float64 T[n], p[n], Y[nsp, n] species-major;
+        int32 steps/status). Asynchronous on `stream` (default: torch's current stream)."""
+        import torch
+        n = T.numel()
+        for t in (T, p, Y):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("T, p, Y must be contiguous float64 CUDA tensors")
+        if Y.shape != (self.nsp, n) or p.numel() != n:
+            raise ValueError("shape mismatch")
+        if T_out is None:
+            T_out = torch.empty_like(T)
+        if Y_out is None:
+            Y_out = torch.empty_like(Y)
+        if stream is None:
+            stream = torch.cuda.current_stream(T.device)
+        sh = ctypes.c_void_p(stream.cuda_stream)
+        self._check(load().dlbchem_integrate(self._h, n, float(dt), _ptr(T), _ptr(p), _ptr(Y), _ptr(T_out),
+                                             _ptr(Y_out), _ptr(steps), _ptr(status), _ptr(Yref), sh))
+        return T_out, Y_out
+
+    def integrate_host(self, T, p, Y, dt, T_out, Y_out, steps=None, status=None, Yref=None, stream=None):
+        """dlbchem_integrate_host on host numpy arrays or CPU tensors (copies inside)."""
+        import numpy as np
+
+        def hp(a):
+            if a is None:
+                return None
+            if isinstance(a, np.ndarray):
+                assert a.flags.c_contiguous
+                return ctypes.c_void_p(a.ctypes.data)
+            return ctypes.c_void_p(a.data_ptr())
+        n = int(T.shape[0]) if hasattr(T, "shape") else len(T)
+        sh = ctypes.c_void_p(0 if stream is None else stream.cuda_stream)
+        self._check(load().dlbchem_integrate_host(self._h, n, float(dt), hp(T), hp(p), hp(Y), hp(T_out), hp(Y_out),
+                                                  hp(steps), hp(status), hp(Yref), sh))
+
+    def last_stats(self) -> dict:
+        out = (ctypes.c_int64 * 8)()
+        self._check(load().dlbchem_last_stats(self._h, out))
+        keys = ["integrated", "mapped", "ref", "team_threads", "teams_per_cta", "ctas", "smem_bytes", "launches"]
+        return dict(zip(keys, list(out)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dlbchem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

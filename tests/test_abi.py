@@ -1,0 +1,63 @@
+"""The C-ABI library loads and exports every function include/dlbchem.h declares
+(CPU only: no compute call is made)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dlbchem.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b(dlbchem_[a-z_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2011_07978_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("dlbchem_create", "dlbchem_integrate", "dlbchem_integrate_host", "dlbchem_destroy",
+                 "dlbchem_last_error", "dlbchem_nspecies", "dlbchem_options_default"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (dlbchem_[a-z_]+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_options_default_and_binding_layout(lib_path):
+    from paper_2011_07978_gb300 import dlbchem
+    o = dlbchem.options_default()
+    assert o.rtol == 1e-6 and o.atol == 1e-10 and o.max_steps == 100000 and o.schedule == dlbchem.SCHED_PLAIN
+    assert o.map_Ttol == 1e-4 and o.map_Ytol == 1e-4 and o.chunk == 1
+    # the ctypes struct must match the C layout (sizeof checked against the header's field list)
+    assert ctypes.sizeof(dlbchem.dlbchem_options) == 8 * 2 + 4 * 2 + 8 + 4 * 4 + 8 * 3
+
+
+def test_create_rejects_bad_arguments_without_gpu(lib_path):
+    from paper_2011_07978_gb300 import dlbchem
+    lib = dlbchem.load()
+    h = ctypes.c_void_p()
+    assert lib.dlbchem_create(b"/nonexistent/mech.bin", None, ctypes.byref(h)) == dlbchem.BAD_MECH
+    assert h.value is None
+    assert b"cannot read" in lib.dlbchem_last_error(None)
+    o = dlbchem.options_default()
+    o.rtol = -1.0
+    assert lib.dlbchem_create(b"x", ctypes.byref(o), ctypes.byref(h)) == dlbchem.BAD_ARG
+    assert lib.dlbchem_nspecies(None) == -1
+    lib.dlbchem_destroy(None)

@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark: chemistry cells/s per flow step dt on one GB300 (per GPU under torchrun).
+
+Workload (the one the metric is quoted on): 262,144 cells of a 53-species /
+325-reaction synthetic mechanism, bimodal field (45 % cold ambient, 45 %
+burnt near-equilibrium, 10 % flame front), p = 20 bar, dt = 1e-5 s, rtol
+1e-5, atol 1e-8 (the paper's ODE tolerances, Sec. 4.1), FP64. One step is
+one call of the whole hot path: mapping classification, cost-key sort, the
+persistent Rosenbrock integrator pulling cells longest-first, mapping
+scatter. Cost keys are the previous call's step counts.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the launching stream; L2 is flushed (256 MB write) between timed steps.
+value = cells / (device ms per step). e2e repeats the same step through the
+host-buffer entry point (dlbchem_integrate_host) with the host<->device
+copies inside the timed region. The CPU baseline and the reference arm time
+the FP64 oracle on a bounded random sample of the same field.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import read_mech, states  # noqa: E402
+
+NSP, NRX, SEED = 53, 325, 0
+NCELLS = 262144
+DT, RTOL, ATOL = 1e-5, 1e-5, 1e-8
+MAP_TOL = 1e-4
+METRIC = "chemistry cells/s per dt at stated T/Y error vs FP64 oracle; frac of FP64 roofline"
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2.07 GHz x 2 FP64
+# FMA lanes per clock per SM x 2 flop (= the 1.25 TFLOP/s nominal figure).
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
+# dram__bytes_read.sum + dram__bytes_write.sum of one integrator launch from
+# ncu, scaled to the full field; None until taken on the current kernel.
+INTEGRATOR_TRAFFIC_BYTES = None
+
+
+def flops_per_step(m) -> float:
+    """Algorithmic FP64 flops of one attempted Rosenbrock step (FMA = 2,
+    exp/log = 20, division = 8); the terms are listed in the design doc."""
+    nsp, nrx = m.nsp, m.nrx
+    N = nsp + 1
+    nr, npd = m.nu_matrix()
+    nu = npd - nr
+    n_inc = int((nu != 0).sum())
+    distinct = ((nr + npd) > 0).sum(axis=0)
+    n_tri = int(((nu != 0).sum(axis=0) * distinct).sum())
+    lu_solve = (2.0 / 3.0) * N**3 + 8.0 * N**2
+    rates = 3 * (nsp * 48 + nrx * 40 + 2 * n_inc)
+    jac = nrx * 28 + 6 * n_inc + 2 * n_tri + 4 * nsp * nsp
+    vec = 40 * N
+    return lu_solve + rates + jac + vec
+
+
+class ClockSampler:
+    """nvidia-smi clocks sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(T, p, Y, n_sample, seed, mapping=True):
+    """Time the FP64 oracle on a random sample of cells, all host cores."""
+    import oracle
+    idx = np.sort(np.random.default_rng(seed + 99).choice(T.size, size=n_sample, replace=False))
+    orc = oracle.Oracle(states.mech_path(NSP, NRX, SEED))
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    res = orc.integrate(T[idx], p[idx], np.ascontiguousarray(Y[:, idx]), DT, rtol=RTOL, atol=ATOL,
+                        nthreads=cores, mapping=mapping, map_Ttol=MAP_TOL, map_Ytol=MAP_TOL)
+    wall = time.perf_counter() - t0
+    return idx, res, wall, cores
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reference_arm(args):
+    """--impl reference: the FP64 oracle on the host cores (rank 0 only)."""
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    T, p, Y, cls = states.bimodal_states(NSP, NRX, NCELLS, SEED)
+    n_sample = 384
+    for w in range(args.warmup):
+        cpu_oracle_sample(T, p, Y, n_sample, 1000 + w)
+    walls = []
+    cores = os.cpu_count() or 1
+    for k in range(args.steps):
+        _, _, wall, cores = cpu_oracle_sample(T, p, Y, n_sample, k)
+        walls.append(wall)
+    v = n_sample / (sum(walls) / len(walls))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cells/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_sample / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "bimodal 262144 cells, 53 species / 325 reactions, p 20 bar, dt 1e-5 s, "
+                                   "rtol 1e-5, atol 1e-8, mapping tol 1e-4", "sample_cells_per_step": n_sample},
+            "cpu_baseline": {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n_sample} random cells of the 262144-cell field per step"},
+            "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dlbchem", choices=["dlbchem", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", default="queue", choices=["queue", "plain"])
+    ap.add_argument("--mapping", type=int, default=1)
+    ap.add_argument("--ncells", type=int, default=NCELLS)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_07978_gb300 import dlbchem
+
+    n = args.ncells
+    T, p, Y, cls = states.bimodal_states(NSP, NRX, n, SEED + rank)
+    mech = read_mech(states.mech_path(NSP, NRX, SEED))
+    sched = dlbchem.SCHED_QUEUE if args.schedule == "queue" else dlbchem.SCHED_PLAIN
+    ctx = dlbchem.Context(states.mech_path(NSP, NRX, SEED), rtol=RTOL, atol=ATOL, schedule=sched,
+                          mapping=args.mapping, map_Ttol=MAP_TOL, map_Ytol=MAP_TOL, timing=1)
+    d = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    Td, pd, Yd = d(T), d(p), d(Y)
+    To, Yo = torch.empty_like(Td), torch.empty_like(Yd)
+    steps = torch.zeros(n, dtype=torch.int32, device=dev)
+    status = torch.zeros(n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        ctx.integrate(Td, pd, Yd, DT, T_out=To, Y_out=Yo, steps=steps, status=status, stream=stream)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    integ_ms, launches, total_steps = [], 0, 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            ctx.integrate(Td, pd, Yd, DT, T_out=To, Y_out=Yo, steps=steps, status=status, stream=stream)
+            ev[k][1].record(stream)
+            integ_ms.append(ctx.last_timing()["integrator_ms"])
+            st = ctx.last_stats()
+            launches += st["launches"]
+            total_steps += int(steps.sum().item())
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        wall = time.perf_counter() - t0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_ms = float(np.sum(step_ms))
+    if world > 1:
+        tmax = torch.tensor([dev_ms], device=dev)
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        dev_ms = float(tmax.item())
+    ms_per_step = dev_ms / args.steps
+    value = world * n / (ms_per_step / 1e3)
+
+    # roofline of the integrator kernel (algorithmic flops / its event-timed duration)
+    fstep = flops_per_step(mech)
+    flops_launch = fstep * total_steps / args.steps
+    integ_avg_ms = float(np.mean(integ_ms))
+    achieved = flops_launch / (integ_avg_ms / 1e3) / 1e12
+    stats = ctx.last_stats()
+    status_h = status.cpu().numpy()
+
+    # e2e: same step through the host-buffer entry point, copies inside the timed region
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    Th, ph, Yh = pin(T), pin(p), pin(Y)
+    Toh, Yoh = pin(np.zeros(n)), pin(np.zeros_like(Y))
+    sth = pin(steps.cpu().numpy())
+    stath = pin(np.zeros(n, dtype=np.int32))
+    ctx.set_options(timing=0)
+    ctx.integrate_host(Th, ph, Yh, DT, Toh, Yoh, steps=sth, status=stath, stream=stream)   # warm
+    e2e_walls = []
+    for k in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ctx.integrate_host(Th, ph, Yh, DT, Toh, Yoh, steps=sth, status=stath, stream=stream)
+        e2e_walls.append(time.perf_counter() - t1)
+    e2e_value = world * n / float(np.mean(e2e_walls))
+    h2d = Th.nbytes + ph.nbytes + Yh.nbytes + sth.nbytes
+    d2h = Toh.nbytes + Yoh.nbytes + sth.nbytes + stath.nbytes
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"bimodal {n} cells, 53 species / 325 reactions (seeded synthetic), p 20 bar, "
+                               f"dt 1e-5 s, rtol 1e-5, atol 1e-8, FP64", "schedule": args.schedule,
+                   "mapping": bool(args.mapping), "mapping_tol": MAP_TOL, "cells_per_gpu": n,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": INTEGRATOR_TRAFFIC_BYTES,
+                     "kernel": "rosenbrock_kernel", "flops_per_step": fstep,
+                     "steps_per_launch": total_steps / args.steps, "launch_ms": integ_avg_ms,
+                     "peak_source": "derived: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM x 2"},
+        "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "clocks": clk.summary(),
+        "gpu_launches": int(launches),
+        "cells": {"integrated": stats["integrated"], "mapped": stats["mapped"],
+                  "failed": int((status_h < 0).sum())},
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        idx, res, cwall, cores = cpu_oracle_sample(T, p, Y, 1024, 0, mapping=False)
+        # error of this field's GPU result on the sampled cells vs the oracle (unmapped cells)
+        To_h, Yo_h = To.cpu().numpy(), Yo.cpu().numpy()
+        integrated = status_h[idx] == 0
+        dT = np.abs(To_h[idx] - res[0]) / res[0]
+        dY = np.abs(Yo_h[:, idx] - res[1]).max(axis=0)
+        err = {}
+        for c, name in ((0, "cold"), (1, "burnt"), (2, "front")):
+            sel = (cls[idx] == c) & integrated
+            if sel.any():
+                err[name] = {"max_rel_T": float(dT[sel].max()), "p99_rel_T": float(np.percentile(dT[sel], 99)),
+                             "max_abs_Y": float(dY[sel].max()), "p99_abs_Y": float(np.percentile(dY[sel], 99)),
+                             "cells": int(sel.sum())}
+        line["error_vs_oracle"] = err
+        line["cpu_baseline"] = {"value": idx.size / cwall, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{idx.size} random cells of the field, no mapping, {cwall:.1f} s wall"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -80,10 +80,12 @@ typedef struct dlbchem_options {
   int32_t schedule;     /* DLBCHEM_SCHED_PLAIN or DLBCHEM_SCHED_QUEUE */
   int32_t chunk;        /* cells per queue pull (1) */
   int32_t mapping;      /* 1: reference mapping on */
-  int32_t reserved0;
+  int32_t timing;       /* 1: record CUDA events around each kernel (see dlbchem_last_timing) */
   double map_Ttol;      /* relative temperature tolerance (1e-4) */
   double map_Ytol;      /* absolute composition tolerance (1e-4) */
   double map_Tmax;      /* > 0: only cells below this T qualify (0 = off) */
+  int32_t team_warps;   /* warps per cell: 0 = automatic, or 1, 2, 4 */
+  int32_t reserved1;
 } dlbchem_options;
 
 /* Fill *opt with the defaults listed above. Returns DLBCHEM_OK or BAD_ARG. */
@@ -147,6 +149,27 @@ int dlbchem_nreactions(const dlbchem_ctx* ctx);
  * Returns DLBCHEM_OK, BAD_ARG or CUDA.
  */
 int dlbchem_last_stats(dlbchem_ctx* ctx, int64_t out[8]);
+
+/*
+ * Device time of the kernels of the last call, in milliseconds, measured with
+ * CUDA events recorded on the call's stream around each launch when the
+ * context was created (or set) with options.timing = 1; 0 otherwise.
+ *   out[0] integrator (Rosenbrock) kernel, out[1] mapping classification,
+ *   out[2] cost-key sort, out[3] mapping scatter, out[4..7] reserved.
+ * Synchronises the stream of the last call. Returns DLBCHEM_OK or BAD_ARG.
+ */
+int dlbchem_last_timing(dlbchem_ctx* ctx, double out[8]);
+
+/*
+ * Diagnostic: copy the work list of the last call (the cells handed to the
+ * integrator, in the order the queue hands them out: unmapped cells sorted
+ * by descending cost key, ties in index order) into list_out, a DEVICE
+ * array of at least ncells int32, and its length into *m_out (host).
+ * Only valid after a call with mapping or the queue schedule; otherwise
+ * *m_out = -1. Synchronises the stream of the last call.
+ * Returns DLBCHEM_OK, BAD_ARG or CUDA.
+ */
+int dlbchem_last_worklist(dlbchem_ctx* ctx, int32_t* list_out, int64_t* m_out);
 
 /* Message of the last failed call on ctx, or of the last failed create when
  * ctx is NULL. Never NULL; "" when there was no error. Owned by the library. */

@@ -159,10 +159,20 @@ struct dlbchem_ctx {
   dlbchem_options opt{};
   WsLayout L{};
   int wpc = 1, teams = 1, smem_bytes = 0, blocks_per_sm = 1, num_sms = 0;
-  // workspace
-  unsigned long long* d_counter = nullptr;
-  int32_t* d_perm = nullptr;
-  int64_t perm_cap = 0;
+  // workspace (grown on demand to the largest ncells seen)
+  unsigned long long* d_counter = nullptr;   // queue counter (8 B) + reference index (8 B)
+  void* d_ws = nullptr;
+  int64_t ws_cap = 0;
+  uint8_t* w_flag = nullptr;
+  double* w_ref_state = nullptr;
+  int32_t *w_bcount = nullptr, *w_boff = nullptr, *w_list = nullptr, *w_list_alt = nullptr, *w_hist = nullptr;
+  uint32_t *w_keys = nullptr, *w_keys_alt = nullptr;
+  int64_t* w_total = nullptr;
+  cudaEvent_t ev[8] = {};
+  bool timed_last = false;
+  int64_t last_n = 0;
+  int last_mapping = 0;
+  int last_listed = 0;
   // host-buffer staging
   double* d_stage = nullptr;
   int32_t* d_stage_i = nullptr;
@@ -190,6 +200,7 @@ bool valid_opts(const dlbchem_options* o, std::string& why) {
   if (o->schedule != DLBCHEM_SCHED_PLAIN && o->schedule != DLBCHEM_SCHED_QUEUE) { why = "unknown schedule"; return false; }
   if (o->chunk < 1) { why = "chunk must be >= 1"; return false; }
   if (!(o->map_Ttol >= 0) || !(o->map_Ytol >= 0) || !(o->map_Tmax >= 0)) { why = "mapping tolerances must be >= 0"; return false; }
+  if (o->team_warps != 0 && o->team_warps != 1 && o->team_warps != 2 && o->team_warps != 4) { why = "team_warps must be 0, 1, 2 or 4"; return false; }
   return true;
 }
 
@@ -197,7 +208,7 @@ bool valid_opts(const dlbchem_options* o, std::string& why) {
 bool build_tables(const HostMech& hm, int wpc, std::vector<unsigned char>& blob, DevMech& dm, std::string& err) {
   const int nsp = hm.nsp, nrx = hm.nrx, N = nsp + 1, ld = N + 1;
   dm.nsp = nsp; dm.nrx = nrx; dm.N = N; dm.ld = ld; dm.wpc = wpc;
-  if (N * ld + 2 >= 65536) { err = "mechanism too large for 16-bit matrix indices (max 254 species)"; return false; }
+  if (N * ld + 2 >= 65536 || N > 256) { err = "mechanism too large (max 254 species)"; return false; }
   // species
   std::vector<double> W(nsp), iW(nsp), H0(nsp), cpa(nsp), hcpb(nsp), cpb(nsp), G0(nsp), G1(nsp), G2(nsp), G3(nsp), bW(nsp);
   for (int k = 0; k < nsp; ++k) {
@@ -337,7 +348,7 @@ int configure_launch(dlbchem_ctx* c) {
   c->num_sms = prop.multiProcessorCount;
   const size_t team_bytes = size_t(c->L.total) * 8;
   const size_t max_block = prop.sharedMemPerBlockOptin;
-  const int max_teams = c->wpc == 1 ? 4 : 1;
+  const int max_teams = 4 / c->wpc;
   int teams = int(std::min<size_t>(max_teams, max_block / team_bytes));
   if (teams < 1) return fail(c, DLBCHEM_BAD_MECH, "mechanism too large: one cell's workspace exceeds shared memory");
   c->teams = teams;
@@ -352,19 +363,40 @@ int configure_launch(dlbchem_ctx* c) {
   return DLBCHEM_OK;
 }
 
-int ensure_perm(dlbchem_ctx* c, int64_t n) {
-  if (n <= c->perm_cap) return DLBCHEM_OK;
-  if (c->d_perm) cudaFree(c->d_perm);
-  c->d_perm = nullptr;
-  c->perm_cap = 0;
-  if (cudaMalloc(&c->d_perm, size_t(n) * 4) != cudaSuccess) return fail(c, DLBCHEM_OOM, "workspace allocation failed");
-  c->perm_cap = n;
-  return DLBCHEM_OK;
-}
+int64_t tiles256(int64_t n) { return (n + 255) / 256; }
 
-__global__ void iota_kernel(int32_t* perm, int64_t n) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    perm[i] = int32_t(i);
+int ensure_ws(dlbchem_ctx* c, int64_t n) {
+  if (n <= c->ws_cap) return DLBCHEM_OK;
+  if (c->d_ws) cudaFree(c->d_ws);
+  c->d_ws = nullptr;
+  c->ws_cap = 0;
+  const int64_t nb = tiles256(n);
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off = 0;
+  const size_t o_flag = off; off += al(size_t(n));
+  const size_t o_ref = off; off += al(size_t(c->hm.nsp + 1) * 8);
+  const size_t o_bc = off; off += al(size_t(nb) * 4);
+  const size_t o_bo = off; off += al(size_t(nb) * 4);
+  const size_t o_tot = off; off += al(8);
+  const size_t o_l = off; off += al(size_t(n) * 4);
+  const size_t o_la = off; off += al(size_t(n) * 4);
+  const size_t o_k = off; off += al(size_t(n) * 4);
+  const size_t o_ka = off; off += al(size_t(n) * 4);
+  const size_t o_h = off; off += al(size_t(nb) * 256 * 4);
+  if (cudaMalloc(&c->d_ws, off) != cudaSuccess) { c->d_ws = nullptr; return fail(c, DLBCHEM_OOM, "workspace allocation failed"); }
+  char* b = static_cast<char*>(c->d_ws);
+  c->w_flag = reinterpret_cast<uint8_t*>(b + o_flag);
+  c->w_ref_state = reinterpret_cast<double*>(b + o_ref);
+  c->w_bcount = reinterpret_cast<int32_t*>(b + o_bc);
+  c->w_boff = reinterpret_cast<int32_t*>(b + o_bo);
+  c->w_total = reinterpret_cast<int64_t*>(b + o_tot);
+  c->w_list = reinterpret_cast<int32_t*>(b + o_l);
+  c->w_list_alt = reinterpret_cast<int32_t*>(b + o_la);
+  c->w_keys = reinterpret_cast<uint32_t*>(b + o_k);
+  c->w_keys_alt = reinterpret_cast<uint32_t*>(b + o_ka);
+  c->w_hist = reinterpret_cast<int32_t*>(b + o_h);
+  c->ws_cap = n;
+  return DLBCHEM_OK;
 }
 
 }  // namespace
@@ -375,7 +407,7 @@ int dlbchem_options_default(dlbchem_options* o) {
   if (!o) return DLBCHEM_BAD_ARG;
   std::memset(o, 0, sizeof(*o));
   o->rtol = 1e-6; o->atol = 1e-10; o->max_steps = 100000; o->isothermal = 0; o->hmin_frac = 1e-20;
-  o->schedule = DLBCHEM_SCHED_PLAIN; o->chunk = 1; o->mapping = 0;
+  o->schedule = DLBCHEM_SCHED_PLAIN; o->chunk = 1; o->mapping = 0; o->timing = 0;
   o->map_Ttol = 1e-4; o->map_Ytol = 1e-4; o->map_Tmax = 0.0;
   return DLBCHEM_OK;
 }
@@ -395,10 +427,12 @@ int dlbchem_create(const char* mech_path, const dlbchem_options* opt, dlbchem_ct
   if (!parse_mech(mech_path, c->hm, why)) { delete c; return fail(nullptr, DLBCHEM_BAD_MECH, why); }
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) { delete c; return fail(nullptr, DLBCHEM_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e)); }
-  c->wpc = (c->hm.nsp + 1 <= 64) ? 1 : 4;
+  c->wpc = o.team_warps ? o.team_warps : ((c->hm.nsp + 1 <= 64) ? 1 : 4);
   std::vector<unsigned char> blob;
   if (!build_tables(c->hm, c->wpc, blob, c->dm, why)) { delete c; return fail(nullptr, DLBCHEM_BAD_MECH, why); }
   c->L = make_layout(c->hm.nsp, c->hm.nrx, c->dm.N, c->dm.ld, c->dm.DS);
+  for (auto& ev : c->ev)
+    if (cudaEventCreate(&ev) != cudaSuccess) { ev = nullptr; dlbchem_destroy(c); return fail(nullptr, DLBCHEM_CUDA, "cudaEventCreate failed"); }
   if (cudaMalloc(&c->d_blob, blob.size()) != cudaSuccess || cudaMalloc(&c->d_counter, 64) != cudaSuccess) {
     dlbchem_destroy(c);
     return fail(nullptr, DLBCHEM_OOM, "device allocation of mechanism tables failed");
@@ -416,6 +450,7 @@ int dlbchem_set_options(dlbchem_ctx* c, const dlbchem_options* opt) {
   if (!c || !opt) return DLBCHEM_BAD_ARG;
   std::string why;
   if (!valid_opts(opt, why)) return fail(c, DLBCHEM_BAD_ARG, why);
+  if (opt->team_warps != c->opt.team_warps) return fail(c, DLBCHEM_BAD_ARG, "team_warps is fixed at creation");
   c->opt = *opt;
   return DLBCHEM_OK;
 }
@@ -425,7 +460,6 @@ int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, con
                       void* stream) {
   if (!c) return DLBCHEM_BAD_ARG;
   c->err.clear();
-  (void)Yref;
   if (n < 0 || n > (int64_t(1) << 31) - 1) return fail(c, DLBCHEM_BAD_ARG, "ncells out of range");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(c, DLBCHEM_BAD_ARG, "dt must be positive and finite");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -434,6 +468,31 @@ int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, con
   c->stats[2] = -1;
   if (n == 0) return DLBCHEM_OK;
   if (!T || !p || !Y || !T_out || !Y_out) return fail(c, DLBCHEM_BAD_ARG, "NULL array pointer");
+  int rc = ensure_ws(c, n);
+  if (rc != DLBCHEM_OK) return rc;
+  const bool timing = c->opt.timing != 0;
+  const bool mapping = c->opt.mapping != 0;
+  const bool queue = c->opt.schedule == DLBCHEM_SCHED_QUEUE;
+  cudaError_t e = cudaSuccess;
+  auto rec = [&](int i) { if (timing && e == cudaSuccess) e = cudaEventRecord(c->ev[i], s); };
+  unsigned long long* d_ref = c->d_counter + 1;
+  // stage 1: mapping classification and the work list (paper Sec. 2.3 filter)
+  rec(2);
+  if (mapping) {
+    if (e == cudaSuccess)
+      e = dlb::launch_map_classify(n, c->hm.nsp, T, Y, Yref, c->opt.map_Ttol, c->opt.map_Ytol, c->opt.map_Tmax,
+                                   c->w_flag, d_ref, c->w_ref_state, c->w_bcount, c->w_boff, c->w_total, s);
+    if (e == cudaSuccess) e = dlb::launch_compact(n, c->w_flag, c->w_boff, steps, c->w_list, c->w_keys, s);
+  } else if (queue) {
+    if (e == cudaSuccess) e = dlb::launch_init_list(n, steps, c->w_list, c->w_keys, c->w_total, s);
+  }
+  rec(3);
+  // stage 2: longest-first order of the work list by the previous call's cost
+  if (queue && steps && e == cudaSuccess)
+    e = dlb::launch_sort(n, c->w_total, c->w_keys, c->w_list, c->w_keys_alt, c->w_list_alt, c->w_hist, s);
+  rec(4);
+  if (e != cudaSuccess) return cuda_fail(c, e, "scheduling kernels");
+  // stage 3: the integrator
   KernelArgs a;
   std::memset(&a, 0, sizeof(a));
   a.m = c->dm;
@@ -441,24 +500,36 @@ int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, con
   a.P.max_steps = c->opt.max_steps; a.P.isothermal = c->opt.isothermal;
   a.L = c->L;
   a.n = n; a.T = T; a.p = p; a.Y = Y; a.Tout = T_out; a.Yout = Y_out; a.steps = steps; a.status = status;
+  const bool listed = mapping || queue;
+  a.perm = listed ? c->w_list : nullptr;
+  a.nqueue = listed ? c->w_total : nullptr;
   const int threads = 32 * c->wpc * c->teams;
-  int64_t grid;
-  if (c->opt.schedule == DLBCHEM_SCHED_QUEUE) {
-    int rc = ensure_perm(c, n);
-    if (rc != DLBCHEM_OK) return rc;
-    iota_kernel<<<std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(c->d_perm, n);
-    cudaError_t e = cudaMemsetAsync(c->d_counter, 0, 8, s);
+  int64_t grid = (n + c->teams - 1) / c->teams;
+  if (queue) {
+    e = cudaMemsetAsync(c->d_counter, 0, 8, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
-    a.queue = 1; a.perm = c->d_perm; a.nqueue = n; a.counter = c->d_counter; a.chunk = c->opt.chunk;
-    grid = int64_t(c->num_sms) * c->blocks_per_sm;
-    grid = std::min<int64_t>(grid, (n + c->teams - 1) / c->teams);
-  } else {
-    grid = (n + c->teams - 1) / c->teams;
+    a.queue = 1; a.counter = c->d_counter; a.chunk = c->opt.chunk;
+    grid = std::min<int64_t>(int64_t(c->num_sms) * c->blocks_per_sm, grid);
   }
-  cudaError_t e = dlb::launch_rosenbrock(c->wpc, unsigned(grid), threads, c->smem_bytes, s, a);
+  rec(0);
+  if (e == cudaSuccess) e = dlb::launch_rosenbrock(c->wpc, unsigned(grid), threads, c->smem_bytes, s, a);
+  rec(1);
   if (e != cudaSuccess) return cuda_fail(c, e, "integrator launch");
+  // stage 4: mapped cells take the reference cell's increment
+  rec(5);
+  if (mapping && e == cudaSuccess)
+    e = dlb::launch_map_scatter(n, c->hm.nsp, c->w_flag, d_ref, c->w_ref_state, T, Y, T_out, Y_out, steps, status, s);
+  rec(6);
+  if (e != cudaSuccess) return cuda_fail(c, e, "mapping scatter");
+  c->timed_last = timing;
+  c->last_n = n;
+  c->last_mapping = mapping;
+  c->last_listed = listed;
   c->stats[0] = n; c->stats[1] = 0; c->stats[2] = -1; c->stats[3] = 32 * c->wpc; c->stats[4] = c->teams;
-  c->stats[5] = grid; c->stats[6] = c->smem_bytes; c->stats[7] = 1;
+  // kernels launched by this call: classify (init, classify, flag, scan, compact) or the list init,
+  // four sort passes of three kernels, the integrator, the scatter
+  c->stats[5] = grid; c->stats[6] = c->smem_bytes;
+  c->stats[7] = (mapping ? 5 : (queue ? 1 : 0)) + ((queue && steps) ? 12 : 0) + 1 + (mapping ? 1 : 0);
   return DLBCHEM_OK;
 }
 
@@ -518,7 +589,45 @@ int dlbchem_last_stats(dlbchem_ctx* c, int64_t out[8]) {
   if (!c || !out) return DLBCHEM_BAD_ARG;
   cudaError_t e = cudaStreamSynchronize(c->last_stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  if (c->last_mapping && c->last_n > 0) {
+    int64_t m = 0;
+    unsigned long long r = 0;
+    if ((e = cudaMemcpy(&m, c->w_total, 8, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(&r, c->d_counter + 1, 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(c, e, "cudaMemcpy");
+    c->stats[0] = m;
+    c->stats[1] = c->last_n - m;
+    c->stats[2] = int64_t(r) < c->last_n ? int64_t(r) : -1;
+  }
   for (int i = 0; i < 8; ++i) out[i] = c->stats[i];
+  return DLBCHEM_OK;
+}
+
+int dlbchem_last_worklist(dlbchem_ctx* c, int32_t* list_out, int64_t* m_out) {
+  if (!c || !list_out || !m_out) return DLBCHEM_BAD_ARG;
+  *m_out = -1;
+  if (!c->last_listed || c->last_n <= 0) return DLBCHEM_OK;
+  cudaError_t e = cudaStreamSynchronize(c->last_stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  int64_t m = 0;
+  if ((e = cudaMemcpy(&m, c->w_total, 8, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
+  if (m > 0 && (e = cudaMemcpy(list_out, c->w_list, size_t(m) * 4, cudaMemcpyDeviceToDevice)) != cudaSuccess)
+    return cuda_fail(c, e, "cudaMemcpy");
+  *m_out = m;
+  return DLBCHEM_OK;
+}
+
+int dlbchem_last_timing(dlbchem_ctx* c, double out[8]) {
+  if (!c || !out) return DLBCHEM_BAD_ARG;
+  for (int i = 0; i < 8; ++i) out[i] = 0.0;
+  if (!c->timed_last) return DLBCHEM_OK;
+  cudaError_t e = cudaEventSynchronize(c->ev[6]);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) out[0] = ms;
+  if (cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]) == cudaSuccess) out[1] = ms;
+  if (cudaEventElapsedTime(&ms, c->ev[3], c->ev[4]) == cudaSuccess) out[2] = ms;
+  if (cudaEventElapsedTime(&ms, c->ev[5], c->ev[6]) == cudaSuccess) out[3] = ms;
   return DLBCHEM_OK;
 }
 
@@ -526,10 +635,12 @@ const char* dlbchem_last_error(const dlbchem_ctx* c) { return c ? c->err.c_str()
 
 void dlbchem_destroy(dlbchem_ctx* c) {
   if (!c) return;
-  if (c->d_blob || c->d_perm || c->d_stage) cudaStreamSynchronize(c->last_stream);
+  if (c->d_blob || c->d_ws || c->d_stage) cudaStreamSynchronize(c->last_stream);
   if (c->d_blob) cudaFree(c->d_blob);
   if (c->d_counter) cudaFree(c->d_counter);
-  if (c->d_perm) cudaFree(c->d_perm);
+  if (c->d_ws) cudaFree(c->d_ws);
+  for (auto& ev : c->ev)
+    if (ev) cudaEventDestroy(ev);
   if (c->d_stage) cudaFree(c->d_stage);
   if (c->d_stage_i) cudaFree(c->d_stage_i);
   delete c;

@@ -123,9 +123,11 @@ struct KernelArgs {
   double* Yout;
   int32_t* steps;
   int32_t* status;
-  // queue mode: cells perm[0..nqueue) are pulled in chunks through *counter
+  // work list perm[0..*nqueue) (NULL perm: cells 0..n-1; NULL nqueue: n).
+  // Plain mode: one team per list entry; queue mode: persistent teams pull
+  // chunks of the list through *counter.
   const int32_t* perm;
-  int64_t nqueue;
+  const int64_t* nqueue;
   unsigned long long* counter;
   int chunk;
   int queue;
@@ -134,5 +136,18 @@ struct KernelArgs {
 // Host-side launchers defined next to the kernels (integrator.cu).
 cudaError_t launch_rosenbrock(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
 const void* rosenbrock_kernel_ptr(int wpc);
+cudaError_t launch_map_classify(int64_t n, int nsp, const double* T, const double* Y, const double* Yref,
+                                double Ttol, double Ytol, double Tmax, uint8_t* qual, unsigned long long* ref,
+                                double* ref_state, int32_t* block_count, int32_t* block_off, int64_t* total,
+                                cudaStream_t s);
+cudaError_t launch_compact(int64_t n, const uint8_t* mapped, const int32_t* block_off, const int32_t* steps_in,
+                           int32_t* list, uint32_t* keys, cudaStream_t s);
+cudaError_t launch_init_list(int64_t n, const int32_t* steps_in, int32_t* list, uint32_t* keys, int64_t* total,
+                             cudaStream_t s);
+cudaError_t launch_sort(int64_t n, const int64_t* mdev, uint32_t* keys, int32_t* list, uint32_t* keys_alt,
+                        int32_t* list_alt, int32_t* hist, cudaStream_t s);
+cudaError_t launch_map_scatter(int64_t n, int nsp, const uint8_t* mapped, const unsigned long long* ref,
+                               const double* ref_state, const double* T, const double* Y, double* Tout,
+                               double* Yout, int32_t* steps, int32_t* status, cudaStream_t s);
 
 }  // namespace dlb

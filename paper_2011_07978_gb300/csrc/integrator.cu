@@ -293,14 +293,15 @@ __device__ __noinline__ void assemble(const DevMech& m, const Team<WPC>& tm, con
     w.M[0] = iso ? ihg : ihg - JTT;
   }
   tm.sync();
-  // species block: M = delta/(h gamma) - (Shat_kj + r_k / W_j)
-  const int nn = nsp * nsp;
-  for (int e = tm.tid; e < nn; e += TS) {
-    const int k = e / nsp, j = e - k * nsp;
-    const int idx = (1 + k) * ld + 1 + j;
-    double v = -fma(w.E[k], m.iW[j], w.M[idx]);
-    if (k == j) v += ihg;
-    w.M[idx] = v;
+  // species block: M = delta/(h gamma) - (Shat_kj + r_k / W_j); warps take rows, lanes columns
+  for (int k = tm.warp; k < nsp; k += WPC) {
+    const double rk = w.E[k];
+    double* row = w.M + (1 + k) * ld + 1;
+    for (int j = tm.lane; j < nsp; j += 32) {
+      double v = -fma(rk, m.iW[j], row[j]);
+      if (k == j) v += ihg;
+      row[j] = v;
+    }
   }
   tm.sync();
 }
@@ -312,8 +313,12 @@ __device__ __noinline__ void assemble(const DevMech& m, const Team<WPC>& tm, con
 // of U is scaled by its inverse pivot one step after it is used, so the
 // triangular solves need no division. The pivot is the first row of largest
 // |M_ik| (compared through the IEEE bit pattern, which orders |x| exactly).
-// Returns false if a pivot is zero.
+// Trailing update: lanes own columns and keep the pivot row in registers,
+// the team's warps split the rows; no index division on the hot loop.
+// Returns false if a pivot is zero. Supports N <= 32 * kMaxC.
 // ---------------------------------------------------------------------------
+constexpr int kMaxC = 8;
+
 template <int WPC>
 __device__ __noinline__ bool lu_factor(const Team<WPC>& tm, double* M, int N, int ld, double* invd, int* perm) {
   constexpr int TS = 32 * WPC;
@@ -366,13 +371,25 @@ __device__ __noinline__ bool lu_factor(const Team<WPC>& tm, double* M, int N, in
     const double inv = 1.0 / d;
     if (tm.tid == 0) invd[k] = inv;
     for (int i = k + 1 + tm.tid; i < N; i += TS) M[i * ld + k] *= inv;
-    tm.sync();
     const int wd = N - 1 - k;
-    const int tot = wd * wd;
-    for (int e = tm.tid; e < tot; e += TS) {
-      const int ii = e / wd, jj = e - ii * wd;
-      const int i = k + 1 + ii, j = k + 1 + jj;
-      M[i * ld + j] = fma(-M[i * ld + k], M[k * ld + j], M[i * ld + j]);
+    const int C = (wd + 31) >> 5;
+    double u[kMaxC];
+#pragma unroll
+    for (int c = 0; c < kMaxC; ++c) {
+      const int jj = tm.lane + 32 * c;
+      u[c] = (c < C && jj < wd) ? M[k * ld + k + 1 + jj] : 0.0;
+    }
+    tm.sync();
+    for (int i = k + 1 + tm.warp; i < N; i += WPC) {
+      double* row = M + i * ld + k + 1;
+      const double l = -M[i * ld + k];
+#pragma unroll
+      for (int c = 0; c < kMaxC; ++c) {
+        if (c < C) {
+          const int jj = tm.lane + 32 * c;
+          if (jj < wd) row[jj] = fma(l, u[c], row[jj]);
+        }
+      }
     }
     tm.sync();
   }
@@ -380,10 +397,39 @@ __device__ __noinline__ bool lu_factor(const Team<WPC>& tm, double* M, int N, in
 }
 
 // x = M^-1 b with the factors above; b and x are distinct team vectors.
+// One warp per cell and N <= 64: x lives in two registers per lane and the
+// solved entry is broadcast by a shuffle, so the column sweeps need neither
+// shared-memory round trips nor barriers.
 template <int WPC>
 __device__ __noinline__ void lu_solve(const Team<WPC>& tm, const double* M, int N, int ld, const double* invd,
                                       const int* perm, const double* b, double* x) {
   constexpr int TS = 32 * WPC;
+  if (WPC == 1 && N <= 64) {
+    const int l = tm.lane;
+    const bool r0 = l < N, r1 = l + 32 < N;
+    double x0 = r0 ? b[perm[l]] : 0.0;
+    double x1 = r1 ? b[perm[l + 32]] : 0.0;
+    for (int j = 0; j < N - 1; ++j) {
+      const double xj = __shfl_sync(0xffffffffu, j < 32 ? x0 : x1, j & 31);
+      if (j < 31) {
+        if (r0 && l > j) x0 = fma(-M[l * ld + j], xj, x0);
+      }
+      if (r1 && l + 32 > j) x1 = fma(-M[(l + 32) * ld + j], xj, x1);
+    }
+    if (r0) x0 *= invd[l];
+    if (r1) x1 *= invd[l + 32];
+    for (int j = N - 1; j > 0; --j) {
+      const double xj = __shfl_sync(0xffffffffu, j < 32 ? x0 : x1, j & 31);
+      if (r0 && l < j) x0 = fma(-M[l * ld + j], xj, x0);
+      if (j > 32) {
+        if (r1 && l + 32 < j) x1 = fma(-M[(l + 32) * ld + j], xj, x1);
+      }
+    }
+    if (r0) x[l] = x0;
+    if (r1) x[l + 32] = x1;
+    __syncwarp();
+    return;
+  }
   for (int i = tm.tid; i < N; i += TS) x[i] = b[perm[i]];
   tm.sync();
   for (int j = 0; j < N - 1; ++j) {
@@ -546,10 +592,13 @@ __global__ void __launch_bounds__(128) rosenbrock_kernel(const KernelArgs a) {
   double* base = smem + size_t(team) * a.L.total;
   WS w = carve(base, a.L);
   tm.red = w.scal;
+  const int64_t nq = a.nqueue ? *a.nqueue : a.n;
   if (!a.queue) {
-    const int64_t cell = int64_t(blockIdx.x) * teams + team;
-    if (cell < a.n)
+    const int64_t j = int64_t(blockIdx.x) * teams + team;
+    if (j < nq) {
+      const int64_t cell = a.perm ? int64_t(a.perm[j]) : j;
       integrate_cell<WPC>(a.m, a.P, tm, w, cell, a.n, a.T, a.p, a.Y, a.Tout, a.Yout, a.steps, a.status);
+    }
     return;
   }
   volatile int64_t* slot = reinterpret_cast<volatile int64_t*>(w.scal + 24);
@@ -558,8 +607,8 @@ __global__ void __launch_bounds__(128) rosenbrock_kernel(const KernelArgs a) {
     tm.sync();
     const int64_t first = *slot;
     tm.sync();
-    if (first >= a.nqueue) break;
-    const int64_t last = min(first + int64_t(a.chunk), a.nqueue);
+    if (first >= nq) break;
+    const int64_t last = min(first + int64_t(a.chunk), nq);
     for (int64_t qi = first; qi < last; ++qi) {
       const int64_t cell = a.perm[qi];
       integrate_cell<WPC>(a.m, a.P, tm, w, cell, a.n, a.T, a.p, a.Y, a.Tout, a.Yout, a.steps, a.status);
@@ -569,13 +618,15 @@ __global__ void __launch_bounds__(128) rosenbrock_kernel(const KernelArgs a) {
 
 cudaError_t launch_rosenbrock(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a) {
   if (wpc == 1) rosenbrock_kernel<1><<<grid, threads, smem, s>>>(a);
+  else if (wpc == 2) rosenbrock_kernel<2><<<grid, threads, smem, s>>>(a);
   else rosenbrock_kernel<4><<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 const void* rosenbrock_kernel_ptr(int wpc) {
   return wpc == 1 ? reinterpret_cast<const void*>(&rosenbrock_kernel<1>)
-                  : reinterpret_cast<const void*>(&rosenbrock_kernel<4>);
+         : wpc == 2 ? reinterpret_cast<const void*>(&rosenbrock_kernel<2>)
+                    : reinterpret_cast<const void*>(&rosenbrock_kernel<4>);
 }
 
 }  // namespace dlb

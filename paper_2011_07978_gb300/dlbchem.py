@@ -20,8 +20,9 @@ SCHED_PLAIN, SCHED_QUEUE = 0, 1
 class dlbchem_options(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("max_steps", ctypes.c_int32),
                 ("isothermal", ctypes.c_int32), ("hmin_frac", ctypes.c_double), ("schedule", ctypes.c_int32),
-                ("chunk", ctypes.c_int32), ("mapping", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("map_Ttol", ctypes.c_double), ("map_Ytol", ctypes.c_double), ("map_Tmax", ctypes.c_double)]
+                ("chunk", ctypes.c_int32), ("mapping", ctypes.c_int32), ("timing", ctypes.c_int32),
+                ("map_Ttol", ctypes.c_double), ("map_Ytol", ctypes.c_double), ("map_Tmax", ctypes.c_double),
+                ("team_warps", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p
@@ -45,6 +46,8 @@ def load() -> ctypes.CDLL:
     lib.dlbchem_nspecies.argtypes = [_vp]
     lib.dlbchem_nreactions.argtypes = [_vp]
     lib.dlbchem_last_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.dlbchem_last_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+    lib.dlbchem_last_worklist.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int64)]
     lib.dlbchem_last_error.argtypes = [_vp]
     lib.dlbchem_last_error.restype = ctypes.c_char_p
     lib.dlbchem_destroy.argtypes = [_vp]
@@ -142,6 +145,17 @@ class Context:
         self._check(load().dlbchem_last_stats(self._h, out))
         keys = ["integrated", "mapped", "ref", "team_threads", "teams_per_cta", "ctas", "smem_bytes", "launches"]
         return dict(zip(keys, list(out)))
+
+    def last_timing(self) -> dict:
+        out = (ctypes.c_double * 8)()
+        self._check(load().dlbchem_last_timing(self._h, out))
+        return dict(zip(["integrator_ms", "classify_ms", "sort_ms", "scatter_ms"], list(out)[:4]))
+
+    def last_worklist(self, out):
+        """Copy the last work list into the int32 CUDA tensor `out`; returns its length."""
+        m = ctypes.c_int64()
+        self._check(load().dlbchem_last_worklist(self._h, _ptr(out), ctypes.byref(m)))
+        return m.value
 
     def close(self):
         if getattr(self, "_h", None):

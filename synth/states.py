@@ -53,8 +53,11 @@ def burnt_seed_states(nsp: int, nbase: int, seed: int):
 
 
 def bimodal_states(nsp: int, nrx: int, n: int, seed: int, p: float = 20e5,
-                   n_ambient: int = 8, cold_noise: float = 2e-5, burnt_noise: float = 1e-6):
-    path = burnt_base_path(nsp, nrx, seed)
+                   n_ambient: int = 8, cold_noise: float = 2e-5, burnt_noise: float = 1e-6,
+                   mech_seed: int = 0):
+    """seed draws the field; mech_seed names the mechanism whose stored burnt
+    base states are used."""
+    path = burnt_base_path(nsp, nrx, mech_seed)
     if not os.path.exists(path):
         raise FileNotFoundError(f"{path} missing: it is written by oracle/make_burnt_base.py")
     base = np.load(path)

@@ -46,7 +46,7 @@ def test_options_default_and_binding_layout(lib_path):
     assert o.rtol == 1e-6 and o.atol == 1e-10 and o.max_steps == 100000 and o.schedule == dlbchem.SCHED_PLAIN
     assert o.map_Ttol == 1e-4 and o.map_Ytol == 1e-4 and o.chunk == 1
     # the ctypes struct must match the C layout (sizeof checked against the header's field list)
-    assert ctypes.sizeof(dlbchem.dlbchem_options) == 8 * 2 + 4 * 2 + 8 + 4 * 4 + 8 * 3
+    assert ctypes.sizeof(dlbchem.dlbchem_options) == 8 * 2 + 4 * 2 + 8 + 4 * 4 + 8 * 3 + 4 * 2
 
 
 def test_create_rejects_bad_arguments_without_gpu(lib_path):

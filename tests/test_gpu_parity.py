@@ -210,3 +210,85 @@ def test_bimodal_full_size_sampled_parity():
     # whole-field properties that hold at any size
     np.testing.assert_allclose(g[1].sum(0), 1.0, atol=1e-12)
     assert np.isfinite(g[0]).all() and (g[0] > 0).all()
+
+
+def _bimodal(n, seed=0):
+    return states.bimodal_states(53, 325, n, seed)
+
+
+def test_mapping_matches_oracle_and_zero_tolerance_is_identity():
+    """Reference mapping (Sec. 2.3 reading): same reference cell, same mapped
+    set (bit-exact), and mapped cells carry the reference increment; with
+    zero tolerances nothing is mapped and the result equals the unmapped run."""
+    d = dlb()
+    mech = states.mech_path(53, 325, 0)
+    T, p, Y, cls = _bimodal(3000, 3)
+    ctx = d.Context(mech, rtol=1e-5, atol=1e-8, mapping=1, map_Ttol=1e-4, map_Ytol=1e-4)
+    g = run_gpu(ctx, T, p, Y, 1e-5)
+    st = ctx.last_stats()
+    orc = oracle.Oracle(mech)
+    ref, flag = orc.map_classify(T, Y, Y[:, 0], 1e-4, 1e-4)
+    assert st["ref"] == ref and st["mapped"] == int(flag.sum()) > 0
+    np.testing.assert_array_equal(g[3] == d.CELL_MAPPED, flag.astype(bool))
+    o = orc.integrate(T, p, Y, 1e-5, rtol=1e-5, atol=1e-8, mapping=True, map_Ttol=1e-4, map_Ytol=1e-4)
+    assert_parity(g, o)
+    np.testing.assert_array_equal(g[2][flag.astype(bool)], 0)
+    # zero tolerances: identical to the plain unmapped run, bit for bit
+    ctx0 = d.Context(mech, rtol=1e-5, atol=1e-8, mapping=1, map_Ttol=0.0, map_Ytol=0.0)
+    g0 = run_gpu(ctx0, T, p, Y, 1e-5)
+    plain = run_gpu(d.Context(mech, rtol=1e-5, atol=1e-8), T, p, Y, 1e-5)
+    assert ctx0.last_stats()["mapped"] == 0
+    for a, b in zip(g0, plain):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_sorted_queue_with_mapping_is_bit_identical_to_plain():
+    """Queue order (descending previous-call steps) and chunking change only
+    who integrates a cell and when, never its result (the paper's appendix A:
+    balancing alone reproduces the standard model exactly)."""
+    d = dlb()
+    mech = states.mech_path(53, 325, 0)
+    T, p, Y, cls = _bimodal(2000, 4)
+    kw = dict(rtol=1e-5, atol=1e-8, mapping=1)
+    plain = run_gpu(d.Context(mech, **kw), T, p, Y, 1e-5)
+    keys = plain[2].copy()
+    for chunk in (1, 4):
+        q = run_gpu(d.Context(mech, schedule=d.SCHED_QUEUE, chunk=chunk, **kw), T, p, Y, 1e-5, steps_in=keys)
+        for a, b in zip(plain, q):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_work_list_is_stable_descending_cost_order():
+    """The queue hands out the unmapped cells by descending cost key (the
+    previous call's step counts), ties in index order: compared with a stable
+    argsort on the host. Keys include ties, zeros and large values."""
+    d = dlb()
+    mech = states.mech_path(53, 325, 0)
+    n = 5000
+    T, p, Y, cls = _bimodal(n, 5)
+    rng = np.random.default_rng(0)
+    keys = rng.integers(0, 40, n).astype(np.int32)
+    keys[::7] = rng.integers(0, 2**20, keys[::7].size)
+    ctx = d.Context(mech, rtol=1e-5, atol=1e-8, schedule=d.SCHED_QUEUE, mapping=1)
+    run_gpu(ctx, T, p, Y, 1e-5, steps_in=keys)
+    out = torch.zeros(n, dtype=torch.int32, device=DEV)
+    m = ctx.last_worklist(out)
+    ref, flag = oracle.Oracle(mech).map_classify(T, Y, Y[:, 0], 1e-4, 1e-4)
+    unm = np.flatnonzero(flag == 0)
+    expect = unm[np.argsort(-keys[unm].astype(np.int64), kind="stable")]
+    assert m == unm.size
+    np.testing.assert_array_equal(out.cpu().numpy()[:m], expect)
+
+
+@pytest.mark.parametrize("wpc", [1, 2, 4])
+def test_team_layouts_match_oracle(wpc):
+    """One, two or four warps per cell: same results within the bar (the
+    reduction order differs between layouts, the arithmetic does not)."""
+    d = dlb()
+    mech = states.mech_path(53, 325, 0)
+    T, p, Y, cls = _bimodal(600, 6)
+    ctx = d.Context(mech, rtol=1e-5, atol=1e-8, team_warps=wpc, schedule=d.SCHED_QUEUE)
+    g = run_gpu(ctx, T, p, Y, 1e-5)
+    assert ctx.last_stats()["team_threads"] == 32 * wpc
+    o = oracle.Oracle(mech).integrate(T, p, Y, 1e-5, rtol=1e-5, atol=1e-8)
+    assert_parity(g, o)

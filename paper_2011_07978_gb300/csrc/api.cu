@@ -13,26 +13,13 @@
 
 #include "../../include/dlbchem.h"
 #include "dlb_common.cuh"
+#include "dlb_ctx.h"
 
 namespace {
 
 using namespace dlb;
 
 thread_local std::string g_create_err;
-
-// ---- host mechanism model (this library's own reader of DLBMECH1) ----------
-struct HostRxn {
-  double lnA, beta, Ea;
-  int rev, tb;
-  std::vector<int> r, p;       // species per slot, expanded by coefficient
-  std::vector<std::pair<int, double>> eff;   // listed efficiencies (species, eff)
-};
-
-struct HostMech {
-  int nsp = 0, nrx = 0;
-  std::vector<double> W, a, b, hf, s0;
-  std::vector<HostRxn> rx;
-};
 
 bool read_file(const char* path, std::vector<unsigned char>& buf) {
   FILE* f = std::fopen(path, "rb");
@@ -61,7 +48,7 @@ struct Reader {
   }
 };
 
-bool parse_mech(const char* path, HostMech& m, std::string& err) {
+bool parse_mech(const char* path, dlb::HostMech& m, std::string& err) {
   std::vector<unsigned char> buf;
   if (!read_file(path, buf)) { err = std::string("cannot read mechanism file ") + path; return false; }
   if (buf.size() < 24 || std::memcmp(buf.data(), "DLBMECH1", 8) != 0) { err = "not a DLBMECH1 file"; return false; }
@@ -151,36 +138,6 @@ void build_rounds(const std::vector<Entry>& ents, uint32_t pad_word, std::vector
 
 }  // namespace
 
-struct dlbchem_ctx {
-  int device = 0;
-  HostMech hm;
-  DevMech dm{};
-  void* d_blob = nullptr;
-  dlbchem_options opt{};
-  WsLayout L{};
-  int wpc = 1, teams = 1, smem_bytes = 0, blocks_per_sm = 1, num_sms = 0;
-  // workspace (grown on demand to the largest ncells seen)
-  unsigned long long* d_counter = nullptr;   // queue counter (8 B) + reference index (8 B)
-  void* d_ws = nullptr;
-  int64_t ws_cap = 0;
-  uint8_t* w_flag = nullptr;
-  double* w_ref_state = nullptr;
-  int32_t *w_bcount = nullptr, *w_boff = nullptr, *w_list = nullptr, *w_list_alt = nullptr, *w_hist = nullptr;
-  uint32_t *w_keys = nullptr, *w_keys_alt = nullptr;
-  int64_t* w_total = nullptr;
-  cudaEvent_t ev[8] = {};
-  bool timed_last = false;
-  int64_t last_n = 0;
-  int last_mapping = 0;
-  int last_listed = 0;
-  // host-buffer staging
-  double* d_stage = nullptr;
-  int32_t* d_stage_i = nullptr;
-  int64_t stage_cap = 0;
-  cudaStream_t last_stream = nullptr;
-  int64_t stats[8] = {0, 0, -1, 0, 0, 0, 0, 0};
-  std::string err;
-};
 
 namespace {
 
@@ -205,7 +162,7 @@ bool valid_opts(const dlbchem_options* o, std::string& why) {
 }
 
 // Build all device tables of one mechanism into one contiguous blob.
-bool build_tables(const HostMech& hm, int wpc, std::vector<unsigned char>& blob, DevMech& dm, std::string& err) {
+bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& blob, DevMech& dm, std::string& err) {
   const int nsp = hm.nsp, nrx = hm.nrx, N = nsp + 1, ld = N + 1;
   dm.nsp = nsp; dm.nrx = nrx; dm.N = N; dm.ld = ld; dm.wpc = wpc;
   if (N * ld + 2 >= 65536 || N > 256) { err = "mechanism too large (max 254 species)"; return false; }

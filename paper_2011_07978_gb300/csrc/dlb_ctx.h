@@ -1,0 +1,61 @@
+// Internal: the context behind the opaque dlbchem_ctx handle (shared by the
+// C-ABI translation units of the library; not part of the public header).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/dlbchem.h"
+#include "dlb_common.cuh"
+
+namespace dlb {
+
+// Host mechanism model (this library's own reader of DLBMECH1).
+struct HostRxn {
+  double lnA, beta, Ea;
+  int rev, tb;
+  std::vector<int> r, p;       // species per slot, expanded by coefficient
+  std::vector<std::pair<int, double>> eff;   // listed efficiencies (species, eff)
+};
+
+struct HostMech {
+  int nsp = 0, nrx = 0;
+  std::vector<double> W, a, b, hf, s0;
+  std::vector<HostRxn> rx;
+};
+
+}  // namespace dlb
+
+struct dlbchem_ctx {
+  int device = 0;
+  dlb::HostMech hm;
+  dlb::DevMech dm{};
+  void* d_blob = nullptr;
+  dlbchem_options opt{};
+  dlb::WsLayout L{};
+  int wpc = 1, teams = 1, smem_bytes = 0, blocks_per_sm = 1, num_sms = 0;
+  // workspace (grown on demand to the largest ncells seen)
+  unsigned long long* d_counter = nullptr;   // queue counter (8 B) + reference index (8 B)
+  void* d_ws = nullptr;
+  int64_t ws_cap = 0;
+  uint8_t* w_flag = nullptr;
+  double* w_ref_state = nullptr;
+  int32_t *w_bcount = nullptr, *w_boff = nullptr, *w_list = nullptr, *w_list_alt = nullptr, *w_hist = nullptr;
+  uint32_t *w_keys = nullptr, *w_keys_alt = nullptr;
+  int64_t* w_total = nullptr;
+  cudaEvent_t ev[8] = {};
+  bool timed_last = false;
+  int64_t last_n = 0;
+  int last_mapping = 0;
+  int last_listed = 0;
+  // host-buffer staging
+  double* d_stage = nullptr;
+  int32_t* d_stage_i = nullptr;
+  int64_t stage_cap = 0;
+  cudaStream_t last_stream = nullptr;
+  int64_t stats[8] = {0, 0, -1, 0, 0, 0, 0, 0};
+  std::string err;
+};

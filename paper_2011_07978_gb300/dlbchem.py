@@ -13,6 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdlbchem.so")
 
 OK, BAD_ARG, BAD_MECH, CUDA, OOM = 0, 1, 2, 3, 4
+STATIC_MAX_CELLS = 262144
 CELL_OK, CELL_MAPPED, CELL_MAX_STEPS, CELL_H_UNDERFLOW, CELL_NONFINITE = 0, 1, -1, -2, -3
 SCHED_PLAIN, SCHED_QUEUE = 0, 1
 
@@ -43,6 +44,7 @@ def load() -> ctypes.CDLL:
     sig = [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     lib.dlbchem_integrate.argtypes = sig
     lib.dlbchem_integrate_host.argtypes = sig
+    lib.dlbchem_integrate_static.argtypes = sig[:-2] + [_vp]
     lib.dlbchem_nspecies.argtypes = [_vp]
     lib.dlbchem_nreactions.argtypes = [_vp]
     lib.dlbchem_last_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
@@ -122,6 +124,17 @@ class Context:
         sh = ctypes.c_void_p(stream.cuda_stream)
         self._check(load().dlbchem_integrate(self._h, n, float(dt), _ptr(T), _ptr(p), _ptr(Y), _ptr(T_out),
                                              _ptr(Y_out), _ptr(steps), _ptr(status), _ptr(Yref), sh))
+        return T_out, Y_out
+
+    def integrate_static(self, T, p, Y, dt, T_out, Y_out, steps=None, status=None, stream=None):
+        """dlbchem_integrate_static: queued integration with the library's fixed scratch
+        array (no device allocation); CUDA tensors as for integrate()."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(T.device)
+        self._check(load().dlbchem_integrate_static(self._h, T.numel(), float(dt), _ptr(T), _ptr(p), _ptr(Y),
+                                                    _ptr(T_out), _ptr(Y_out), _ptr(steps), _ptr(status),
+                                                    ctypes.c_void_p(stream.cuda_stream)))
         return T_out, Y_out
 
     def integrate_host(self, T, p, Y, dt, T_out, Y_out, steps=None, status=None, Yref=None, stream=None):

@@ -84,7 +84,7 @@ typedef struct dlbchem_options {
   double map_Ttol;      /* relative temperature tolerance (1e-4) */
   double map_Ytol;      /* absolute composition tolerance (1e-4) */
   double map_Tmax;      /* > 0: only cells below this T qualify (0 = off) */
-  int32_t team_warps;   /* warps per cell: 0 = automatic, or 1, 2, 4 */
+  int32_t team_warps;   /* warps per cell: 1, 2, 4, or 0 = automatic (1 up to 32 unknowns, 2 up to 64, else 4) */
   int32_t reserved1;
 } dlbchem_options;
 
@@ -195,6 +195,15 @@ int dlbchem_last_timing(dlbchem_ctx* ctx, double out[8]);
  * Returns DLBCHEM_OK, BAD_ARG or CUDA.
  */
 int dlbchem_last_worklist(dlbchem_ctx* ctx, int32_t* list_out, int64_t* m_out);
+
+/*
+ * Diagnostic: evaluate the integrator's own exponential (Tang's table-driven
+ * method) and reciprocal (Newton-Raphson from the hardware approximation)
+ * next to CUDA's exp and IEEE division. x [n] device input; out [4n] device
+ * output, per element: exp_own, exp_cuda, rcp_own, 1/x. Asynchronous on the
+ * stream. Returns DLBCHEM_OK, BAD_ARG or CUDA.
+ */
+int dlbchem_check_math(dlbchem_ctx* ctx, int64_t n, const double* x, double* out, void* cuda_stream);
 
 /* Message of the last failed call on ctx, or of the last failed create when
  * ctx is NULL. Never NULL; "" when there was no error. Owned by the library. */

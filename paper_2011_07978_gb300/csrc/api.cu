@@ -269,6 +269,9 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   offs.push_back(put(inc.data(), inc.size() * 4));
   offs.push_back(put(tri.data(), tri.size() * 4));
   offs.push_back(put(tric.data(), tric.size() * 8));
+  std::vector<double> exptab(64);
+  for (int j = 0; j < 64; ++j) exptab[j] = double(exp2l((long double)j / 64.0L));
+  offs.push_back(put(exptab.data(), exptab.size() * 8));
   // store offsets as fake pointers; relocated after upload
   auto P = [&](int i) { return reinterpret_cast<const double*>(offs[i]); };
   dm.W = P(0); dm.iW = P(1); dm.H0 = P(2); dm.cpa = P(3); dm.hcpb = P(4); dm.cpb = P(5);
@@ -280,6 +283,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   dm.inc = reinterpret_cast<const uint32_t*>(offs[17]);
   dm.tri = reinterpret_cast<const uint32_t*>(offs[18]);
   dm.tri_coef = P(19);
+  dm.exptab = P(20);
   return true;
 }
 
@@ -296,6 +300,7 @@ void relocate(DevMech& dm, void* base) {
   dm.EaR = reloc(dm.EaR, base); dm.meta = reloc(dm.meta, base); dm.eff_sp = reloc(dm.eff_sp, base);
   dm.eff_dm1 = reloc(dm.eff_dm1, base); dm.inc = reloc(dm.inc, base); dm.tri = reloc(dm.tri, base);
   dm.tri_coef = reloc(dm.tri_coef, base);
+  dm.exptab = reloc(dm.exptab, base);
 }
 
 int configure_launch(dlbchem_ctx* c) {
@@ -306,10 +311,10 @@ int configure_launch(dlbchem_ctx* c) {
   const size_t team_bytes = size_t(c->L.total) * 8;
   const size_t max_block = prop.sharedMemPerBlockOptin;
   const int max_teams = 4 / c->wpc;
-  int teams = int(std::min<size_t>(max_teams, max_block / team_bytes));
+  int teams = int(std::min<size_t>(max_teams, (max_block - 512) / team_bytes));
   if (teams < 1) return fail(c, DLBCHEM_BAD_MECH, "mechanism too large: one cell's workspace exceeds shared memory");
   c->teams = teams;
-  c->smem_bytes = int(team_bytes * teams);
+  c->smem_bytes = int(team_bytes * teams) + 64 * 8;   // + the CTA's exp table
   e = cudaFuncSetAttribute(dlb::rosenbrock_kernel_ptr(c->wpc), cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaFuncSetAttribute");
   int bps = 0;
@@ -384,7 +389,8 @@ int dlbchem_create(const char* mech_path, const dlbchem_options* opt, dlbchem_ct
   if (!parse_mech(mech_path, c->hm, why)) { delete c; return fail(nullptr, DLBCHEM_BAD_MECH, why); }
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) { delete c; return fail(nullptr, DLBCHEM_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e)); }
-  c->wpc = o.team_warps ? o.team_warps : ((c->hm.nsp + 1 <= 64) ? 1 : 4);
+  // automatic team size (measured on GB300): one warp up to 32 unknowns, two up to 64, four above
+  c->wpc = o.team_warps ? o.team_warps : (c->hm.nsp + 1 <= 32 ? 1 : (c->hm.nsp + 1 <= 64 ? 2 : 4));
   std::vector<unsigned char> blob;
   if (!build_tables(c->hm, c->wpc, blob, c->dm, why)) { delete c; return fail(nullptr, DLBCHEM_BAD_MECH, why); }
   c->L = make_layout(c->hm.nsp, c->hm.nrx, c->dm.N, c->dm.ld, c->dm.DS);
@@ -558,6 +564,13 @@ int dlbchem_last_stats(dlbchem_ctx* c, int64_t out[8]) {
   }
   for (int i = 0; i < 8; ++i) out[i] = c->stats[i];
   return DLBCHEM_OK;
+}
+
+int dlbchem_check_math(dlbchem_ctx* c, int64_t n, const double* x, double* out, void* stream) {
+  if (!c || n < 0 || (n > 0 && (!x || !out))) return DLBCHEM_BAD_ARG;
+  if (n == 0) return DLBCHEM_OK;
+  cudaError_t e = dlb::launch_check_math(n, x, c->dm.exptab, out, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? DLBCHEM_OK : cuda_fail(c, e, "check_math launch");
 }
 
 int dlbchem_last_worklist(dlbchem_ctx* c, int32_t* list_out, int64_t* m_out) {

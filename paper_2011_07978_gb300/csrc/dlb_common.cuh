@@ -67,6 +67,7 @@ struct DevMech {
   const uint32_t* tri;
   const double* tri_coef;
   int tri_ptr[5];
+  const double* exptab;   // 2^(j/64), j = 0..63 (staged into shared memory per CTA)
 };
 
 struct IntegParams {
@@ -136,6 +137,7 @@ struct KernelArgs {
 // Host-side launchers defined next to the kernels (integrator.cu).
 cudaError_t launch_rosenbrock(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
 const void* rosenbrock_kernel_ptr(int wpc);
+cudaError_t launch_check_math(int64_t n, const double* x, const double* tab, double* out, cudaStream_t s);
 cudaError_t launch_map_classify(int64_t n, int nsp, const double* T, const double* Y, const double* Yref,
                                 double Ttol, double Ytol, double Tmax, uint8_t* qual, unsigned long long* ref,
                                 double* ref_state, int32_t* block_count, int32_t* block_off, int64_t* total,

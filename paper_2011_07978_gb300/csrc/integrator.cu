@@ -70,6 +70,7 @@ struct WS {
   double *M, *y0, *f0, *ys, *fs, *u, *c, *E, *Einv, *hk, *wdot, *vv, *dwdT, *uu, *invd, *q, *sig, *dqdT, *dlt,
       *D, *scal;
   int* perm;
+  const double* exptab;   // 64 entries of 2^(j/64), shared by the CTA
 };
 
 __device__ __forceinline__ WS carve(double* base, const WsLayout& L) {
@@ -87,6 +88,42 @@ struct Mix {
   double T, iT, lnT, S, rho, irho;
 };
 
+// exp(x) by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989):
+// x = (64 m + j) ln2/64 + r with |r| <= ln2/128, exp(x) = 2^m 2^(j/64) e^r.
+// k = 64 m + j is rounded with the 1.5*2^52 shift, r is reduced with a
+// two-constant Cody-Waite split of ln2/64 (32-bit high part, so k*hi is
+// exact), e^r is its degree-5 Taylor polynomial (remainder < 3.5e-17), and
+// 2^m is added to the exponent field. tab[j] = 2^(j/64) rounded to double.
+// About 10 FP64 operations against ~19 for the library exp; |x| >= 700 and
+// NaN go to the library exp.
+__device__ __forceinline__ double exp_tab(double x, const double* __restrict__ tab) {
+  if (!(fabs(x) < 700.0)) return exp(x);
+  const double kShift = 6755399441055744.0;                 // 1.5 * 2^52
+  const double t = fma(x, 92.33248261689366, kShift);       // x * 64 / ln2, rounded to an integer
+  const int ki = __double2loint(t);
+  const double k = t - kShift;
+  double r = fma(-k, 0.010830424696905538, x);              // ln2/64, high 32 bits
+  r = fma(-k, -6.563929801064195e-13, r);                   // ln2/64, remainder
+  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  p = fma(r, p, 1.0 / 6.0);
+  p = fma(r, p, 0.5);
+  p = fma(r, p, 1.0);
+  p = fma(r, p, 1.0);
+  const double v = tab[ki & 63] * p;
+  return __hiloint2double(__double2hiint(v) + ((ki >> 6) << 20), __double2loint(v));
+}
+
+// 1/d by two Newton-Raphson steps r <- r + r(1 - d r) from the hardware
+// approximation rcp.approx.ftz.f64 (each step doubles the correct bits).
+__device__ __forceinline__ double rcp_nr(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
 // ---------------------------------------------------------------------------
 // Rates. Species pass: concentrations c_k = rho Y_k / W_k, E_k = exp(-g_k/RT)
 // and 1/E_k (equilibrium constants as products of per-species factors:
@@ -98,7 +135,7 @@ struct Mix {
 // wdot_k = sum_r nu_kr q_r (and v, dwdT, u).
 // ---------------------------------------------------------------------------
 template <int WPC, bool JAC>
-__device__ __noinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm, const WS& w, const double* yv,
+__device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm, const WS& w, const double* yv,
                                         double P1, Mix& mx) {
   constexpr int TS = 32 * WPC;
   const int nsp = m.nsp, nrx = m.nrx;
@@ -112,9 +149,9 @@ __device__ __noinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm, c
   mx.T = T; mx.iT = iT; mx.lnT = lnT; mx.S = S; mx.rho = rho; mx.irho = (T * S) / P1;
   for (int k = tm.tid; k < nsp; k += TS) {
     w.c[k] = rho * yv[1 + k] * m.iW[k];
-    const double e = exp(fma(m.G2[k], lnT, fma(m.G3[k], T, -fma(m.G0[k], iT, m.G1[k]))));
+    const double e = exp_tab(fma(m.G2[k], lnT, fma(m.G3[k], T, -fma(m.G0[k], iT, m.G1[k]))), w.exptab);
     w.E[k] = e;
-    w.Einv[k] = 1.0 / e;
+    w.Einv[k] = rcp_nr(e);
     w.hk[k] = fma(T, fma(m.hcpb[k], T, m.cpa[k]), m.H0[k]);
   }
   if (tm.tid == 0) w.c[nsp] = 0.0;
@@ -124,19 +161,30 @@ __device__ __noinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm, c
   const double C0 = 1.0 / C0inv;
   for (int r = tm.tid; r < nrx; r += TS) {
     const RxnMeta mt = m.meta[r];
-    const double kf = exp(m.lnA[r] + m.beta[r] * lnT - m.EaR[r] * iT);
-    double cr[3], cq[3];
-    double pf = kf;
-    for (int i = 0; i < mt.nr; ++i) { cr[i] = w.c[mt.sp[i]]; pf *= cr[i]; }
-    double pr = 0.0, kr = 0.0;
+    const double kf = exp_tab(fma(m.beta[r], lnT, fma(-m.EaR[r], iT, m.lnA[r])), w.exptab);
+    // expanded slots as fixed registers (unused slots hold 1)
+    const double a0 = w.c[mt.sp[0]];
+    const double a1 = mt.nr > 1 ? w.c[mt.sp[1]] : 1.0;
+    const double a2 = mt.nr > 2 ? w.c[mt.sp[2]] : 1.0;
+    double pf = kf * a0;
+    if (mt.nr > 1) pf *= a1;
+    if (mt.nr > 2) pf *= a2;
+    double pr = 0.0, kr = 0.0, b0 = 1.0, b1 = 1.0, b2 = 1.0;
     if (mt.flags & RX_REV) {
-      kr = kf;
-      for (int i = 0; i < mt.nr; ++i) kr *= w.E[mt.sp[i]];
-      for (int i = 0; i < mt.np; ++i) kr *= w.Einv[mt.sp[3 + i]];
-      for (int i = 0; i < mt.dnu; ++i) kr *= C0inv;
-      for (int i = 0; i < -mt.dnu; ++i) kr *= C0;
-      pr = kr;
-      for (int i = 0; i < mt.np; ++i) { cq[i] = w.c[mt.sp[3 + i]]; pr *= cq[i]; }
+      kr = kf * w.E[mt.sp[0]];
+      if (mt.nr > 1) kr *= w.E[mt.sp[1]];
+      if (mt.nr > 2) kr *= w.E[mt.sp[2]];
+      kr *= w.Einv[mt.sp[3]];
+      if (mt.np > 1) kr *= w.Einv[mt.sp[4]];
+      if (mt.np > 2) kr *= w.Einv[mt.sp[5]];
+      if (mt.dnu > 0) { kr *= C0inv; if (mt.dnu > 1) kr *= C0inv; if (mt.dnu > 2) kr *= C0inv; }
+      if (mt.dnu < 0) { kr *= C0; if (mt.dnu < -1) kr *= C0; if (mt.dnu < -2) kr *= C0; }
+      b0 = w.c[mt.sp[3]];
+      b1 = mt.np > 1 ? w.c[mt.sp[4]] : 1.0;
+      b2 = mt.np > 2 ? w.c[mt.sp[5]] : 1.0;
+      pr = kr * b0;
+      if (mt.np > 1) pr *= b1;
+      if (mt.np > 2) pr *= b2;
     }
     double Mf = 1.0;
     if (mt.flags & RX_TB) {
@@ -147,20 +195,16 @@ __device__ __noinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm, c
     if (JAC) {
       double* D = w.D + r * m.DS;
       for (int s2 = 0; s2 < mt.nds; ++s2) D[s2] = 0.0;
-      // d/dc of prod over the expanded slots: product of the other slots
-      for (int i = 0; i < mt.nr; ++i) {
-        double t = kf * Mf;
-        for (int l = 0; l < mt.nr; ++l)
-          if (l != i) t *= cr[l];
-        D[mt.ds[i]] += t;
-      }
+      // d/dc_j of the slot product = product of the other slots
+      const double kfM = kf * Mf;
+      D[mt.ds[0]] += kfM * (a1 * a2);
+      if (mt.nr > 1) D[mt.ds[1]] += kfM * (a0 * a2);
+      if (mt.nr > 2) D[mt.ds[2]] += kfM * (a0 * a1);
       if (mt.flags & RX_REV) {
-        for (int i = 0; i < mt.np; ++i) {
-          double t = kr * Mf;
-          for (int l = 0; l < mt.np; ++l)
-            if (l != i) t *= cq[l];
-          D[mt.ds[3 + i]] -= t;
-        }
+        const double krM = kr * Mf;
+        D[mt.ds[3]] -= krM * (b1 * b2);
+        if (mt.np > 1) D[mt.ds[4]] -= krM * (b0 * b2);
+        if (mt.np > 2) D[mt.ds[5]] -= krM * (b0 * b1);
       }
       const int tb = (mt.flags & RX_TB) ? 1 : 0;
       if (mt.flags & RX_EFF) D[mt.dslot_eff] = pf - pr;
@@ -168,9 +212,11 @@ __device__ __noinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm, c
       const double dlnkf = fma(m.EaR[r], iT * iT, m.beta[r] * iT);
       double dq = pf * dlnkf;
       if (mt.flags & RX_REV) {
-        double dH = 0.0;
-        for (int i = 0; i < mt.np; ++i) dH += w.hk[mt.sp[3 + i]];
-        for (int i = 0; i < mt.nr; ++i) dH -= w.hk[mt.sp[i]];
+        double dH = w.hk[mt.sp[3]] - w.hk[mt.sp[0]];
+        if (mt.np > 1) dH += w.hk[mt.sp[4]];
+        if (mt.np > 2) dH += w.hk[mt.sp[5]];
+        if (mt.nr > 1) dH -= w.hk[mt.sp[1]];
+        if (mt.nr > 2) dH -= w.hk[mt.sp[2]];
         const double dlnKc = dH * iT * iT * (1.0 / kR) - mt.dnu * iT;
         dq -= pr * (dlnkf - dlnKc);
       }
@@ -238,7 +284,7 @@ __device__ __forceinline__ void eval_f(const DevMech& m, const Team<WPC>& tm, co
 // rho(T, Y).
 // ---------------------------------------------------------------------------
 template <int WPC>
-__device__ __noinline__ void assemble(const DevMech& m, const Team<WPC>& tm, const WS& w, double P1, bool iso,
+__device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, const WS& w, double P1, bool iso,
                                       double ihg) {
   constexpr int TS = 32 * WPC;
   const int nsp = m.nsp, N = m.N, ld = m.ld;
@@ -313,14 +359,14 @@ __device__ __noinline__ void assemble(const DevMech& m, const Team<WPC>& tm, con
 // of U is scaled by its inverse pivot one step after it is used, so the
 // triangular solves need no division. The pivot is the first row of largest
 // |M_ik| (compared through the IEEE bit pattern, which orders |x| exactly).
-// Trailing update: lanes own columns and keep the pivot row in registers,
-// the team's warps split the rows; no index division on the hot loop.
-// Returns false if a pivot is zero. Supports N <= 32 * kMaxC.
+// Trailing update: the wd x wd block is flattened over the team's threads so
+// every lane of every FP64 instruction does useful work (on GB300 a warp FP64
+// instruction costs the same with 1 or 32 active lanes); the element indices
+// advance incrementally, with one integer division per pivot step.
+// Returns false if a pivot is zero.
 // ---------------------------------------------------------------------------
-constexpr int kMaxC = 8;
-
 template <int WPC>
-__device__ __noinline__ bool lu_factor(const Team<WPC>& tm, double* M, int N, int ld, double* invd, int* perm) {
+__device__ __forceinline__ bool lu_factor(const Team<WPC>& tm, double* M, int N, int ld, double* invd, int* perm) {
   constexpr int TS = 32 * WPC;
   for (int i = tm.tid; i < N; i += TS) perm[i] = i;
   bool singular = false;
@@ -368,27 +414,26 @@ __device__ __noinline__ bool lu_factor(const Team<WPC>& tm, double* M, int N, in
     tm.sync();
     const double d = M[k * ld + k];
     if (d == 0.0) singular = true;
-    const double inv = 1.0 / d;
-    if (tm.tid == 0) invd[k] = inv;
-    for (int i = k + 1 + tm.tid; i < N; i += TS) M[i * ld + k] *= inv;
-    const int wd = N - 1 - k;
-    const int C = (wd + 31) >> 5;
-    double u[kMaxC];
-#pragma unroll
-    for (int c = 0; c < kMaxC; ++c) {
-      const int jj = tm.lane + 32 * c;
-      u[c] = (c < C && jj < wd) ? M[k * ld + k + 1 + jj] : 0.0;
+    if (tm.warp == 0) {           // one warp takes the reciprocal and the column
+      const double inv = rcp_nr(d);
+      if (tm.lane == 0) invd[k] = inv;
+      for (int i = k + 1 + tm.lane; i < N; i += 32) M[i * ld + k] *= inv;
     }
     tm.sync();
-    for (int i = k + 1 + tm.warp; i < N; i += WPC) {
-      double* row = M + i * ld + k + 1;
-      const double l = -M[i * ld + k];
-#pragma unroll
-      for (int c = 0; c < kMaxC; ++c) {
-        if (c < C) {
-          const int jj = tm.lane + 32 * c;
-          if (jj < wd) row[jj] = fma(l, u[c], row[jj]);
-        }
+    // flattened trailing update over the wd x wd block: element e = ii*wd + jj,
+    // thread t takes e = t, t + TS, ...; (ii, jj) advance by (TS / wd, TS % wd)
+    const int wd = N - 1 - k;
+    const int tot = wd * wd;
+    if (tm.tid < tot) {
+      const int dq = TS / wd, dr = TS - dq * wd;
+      int ii = tm.tid / wd, jj = tm.tid - ii * wd;
+      const double* urow = M + k * ld + k + 1;
+      for (int e = tm.tid; e < tot; e += TS) {
+        double* mrow = M + (k + 1 + ii) * ld;
+        mrow[k + 1 + jj] = fma(-mrow[k], urow[jj], mrow[k + 1 + jj]);
+        jj += dr;
+        ii += dq;
+        if (jj >= wd) { jj -= wd; ++ii; }
       }
     }
     tm.sync();
@@ -397,37 +442,49 @@ __device__ __noinline__ bool lu_factor(const Team<WPC>& tm, double* M, int N, in
 }
 
 // x = M^-1 b with the factors above; b and x are distinct team vectors.
-// One warp per cell and N <= 64: x lives in two registers per lane and the
-// solved entry is broadcast by a shuffle, so the column sweeps need neither
-// shared-memory round trips nor barriers.
+// For N <= 128 the team's first warp sweeps alone with x in up to four
+// registers per lane, broadcasting each solved entry by a shuffle: no
+// shared-memory round trips and no barrier per column.
 template <int WPC>
-__device__ __noinline__ void lu_solve(const Team<WPC>& tm, const double* M, int N, int ld, const double* invd,
+__device__ __forceinline__ void lu_solve(const Team<WPC>& tm, const double* M, int N, int ld, const double* invd,
                                       const int* perm, const double* b, double* x) {
   constexpr int TS = 32 * WPC;
-  if (WPC == 1 && N <= 64) {
-    const int l = tm.lane;
-    const bool r0 = l < N, r1 = l + 32 < N;
-    double x0 = r0 ? b[perm[l]] : 0.0;
-    double x1 = r1 ? b[perm[l + 32]] : 0.0;
-    for (int j = 0; j < N - 1; ++j) {
-      const double xj = __shfl_sync(0xffffffffu, j < 32 ? x0 : x1, j & 31);
-      if (j < 31) {
-        if (r0 && l > j) x0 = fma(-M[l * ld + j], xj, x0);
+  if (N <= 128) {
+    if (tm.warp == 0) {
+      const int l = tm.lane;
+      const bool v0 = l < N, v1 = l + 32 < N, v2 = l + 64 < N, v3 = l + 96 < N;
+      double x0 = v0 ? b[perm[l]] : 0.0;
+      double x1 = v1 ? b[perm[l + 32]] : 0.0;
+      double x2 = v2 ? b[perm[l + 64]] : 0.0;
+      double x3 = v3 ? b[perm[l + 96]] : 0.0;
+      // forward sweep, unit lower L: rows r > j take -L_rj x_j
+      for (int j = 0; j < N - 1; ++j) {
+        const double src = j < 32 ? x0 : (j < 64 ? x1 : (j < 96 ? x2 : x3));
+        const double xj = __shfl_sync(0xffffffffu, src, j & 31);
+        if (j < 31 && v0 && l > j) x0 = fma(-M[l * ld + j], xj, x0);
+        if (j < 63 && v1 && l + 32 > j) x1 = fma(-M[(l + 32) * ld + j], xj, x1);
+        if (j < 95 && v2 && l + 64 > j) x2 = fma(-M[(l + 64) * ld + j], xj, x2);
+        if (v3 && l + 96 > j) x3 = fma(-M[(l + 96) * ld + j], xj, x3);
       }
-      if (r1 && l + 32 > j) x1 = fma(-M[(l + 32) * ld + j], xj, x1);
-    }
-    if (r0) x0 *= invd[l];
-    if (r1) x1 *= invd[l + 32];
-    for (int j = N - 1; j > 0; --j) {
-      const double xj = __shfl_sync(0xffffffffu, j < 32 ? x0 : x1, j & 31);
-      if (r0 && l < j) x0 = fma(-M[l * ld + j], xj, x0);
-      if (j > 32) {
-        if (r1 && l + 32 < j) x1 = fma(-M[(l + 32) * ld + j], xj, x1);
+      if (v0) x0 *= invd[l];
+      if (v1) x1 *= invd[l + 32];
+      if (v2) x2 *= invd[l + 64];
+      if (v3) x3 *= invd[l + 96];
+      // backward sweep, unit upper U~: rows r < j take -U~_rj x_j
+      for (int j = N - 1; j > 0; --j) {
+        const double src = j < 32 ? x0 : (j < 64 ? x1 : (j < 96 ? x2 : x3));
+        const double xj = __shfl_sync(0xffffffffu, src, j & 31);
+        if (v0 && l < j) x0 = fma(-M[l * ld + j], xj, x0);
+        if (j > 32 && v1 && l + 32 < j) x1 = fma(-M[(l + 32) * ld + j], xj, x1);
+        if (j > 64 && v2 && l + 64 < j) x2 = fma(-M[(l + 64) * ld + j], xj, x2);
+        if (j > 96 && v3 && l + 96 < j) x3 = fma(-M[(l + 96) * ld + j], xj, x3);
       }
+      if (v0) x[l] = x0;
+      if (v1) x[l + 32] = x1;
+      if (v2) x[l + 64] = x2;
+      if (v3) x[l + 96] = x3;
     }
-    if (r0) x[l] = x0;
-    if (r1) x[l + 32] = x1;
-    __syncwarp();
+    tm.sync();
     return;
   }
   for (int i = tm.tid; i < N; i += TS) x[i] = b[perm[i]];
@@ -578,7 +635,7 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
 
 
 template <int WPC>
-__global__ void __launch_bounds__(128) rosenbrock_kernel(const KernelArgs a) {
+__global__ void __launch_bounds__(128, WPC == 4 ? 4 : 1) rosenbrock_kernel(const KernelArgs a) {
   extern __shared__ __align__(16) double smem[];
   constexpr int TS = 32 * WPC;
   const int teams = blockDim.x / TS;
@@ -589,8 +646,12 @@ __global__ void __launch_bounds__(128) rosenbrock_kernel(const KernelArgs a) {
   tm.lane = threadIdx.x & 31;
   tm.bar_id = 1 + team;
   tm.parity = 0;
+  double* tab = smem + size_t(teams) * a.L.total;
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) tab[j] = a.m.exptab[j];
+  __syncthreads();
   double* base = smem + size_t(team) * a.L.total;
   WS w = carve(base, a.L);
+  w.exptab = tab;
   tm.red = w.scal;
   const int64_t nq = a.nqueue ? *a.nqueue : a.n;
   if (!a.queue) {
@@ -614,6 +675,23 @@ __global__ void __launch_bounds__(128) rosenbrock_kernel(const KernelArgs a) {
       integrate_cell<WPC>(a.m, a.P, tm, w, cell, a.n, a.T, a.p, a.Y, a.Tout, a.Yout, a.steps, a.status);
     }
   }
+}
+
+// Diagnostic: the integrator's exp and reciprocal next to CUDA's exp and
+// IEEE division, for the accuracy test of the two replacements.
+__global__ void check_math_kernel(int64_t n, const double* __restrict__ x, const double* __restrict__ tab,
+                                  double* __restrict__ out) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  out[4 * i + 0] = exp_tab(x[i], tab);
+  out[4 * i + 1] = exp(x[i]);
+  out[4 * i + 2] = rcp_nr(x[i]);
+  out[4 * i + 3] = 1.0 / x[i];
+}
+
+cudaError_t launch_check_math(int64_t n, const double* x, const double* tab, double* out, cudaStream_t s) {
+  check_math_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, x, tab, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rosenbrock(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a) {

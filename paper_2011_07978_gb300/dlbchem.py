@@ -50,6 +50,7 @@ def load() -> ctypes.CDLL:
     lib.dlbchem_last_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     lib.dlbchem_last_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
     lib.dlbchem_last_worklist.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.dlbchem_check_math.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp]
     lib.dlbchem_last_error.argtypes = [_vp]
     lib.dlbchem_last_error.restype = ctypes.c_char_p
     lib.dlbchem_destroy.argtypes = [_vp]
@@ -163,6 +164,14 @@ class Context:
         out = (ctypes.c_double * 8)()
         self._check(load().dlbchem_last_timing(self._h, out))
         return dict(zip(["integrator_ms", "classify_ms", "sort_ms", "scatter_ms"], list(out)[:4]))
+
+    def check_math(self, x):
+        """Returns a [n, 4] tensor: own exp, CUDA exp, own reciprocal, 1/x."""
+        import torch
+        out = torch.empty((x.numel(), 4), dtype=torch.float64, device=x.device)
+        self._check(load().dlbchem_check_math(self._h, x.numel(), _ptr(x), _ptr(out),
+                                              ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)))
+        return out
 
     def last_worklist(self, out):
         """Copy the last work list into the int32 CUDA tensor `out`; returns its length."""

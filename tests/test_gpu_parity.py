@@ -292,3 +292,25 @@ def test_team_layouts_match_oracle(wpc):
     assert ctx.last_stats()["team_threads"] == 32 * wpc
     o = oracle.Oracle(mech).integrate(T, p, Y, 1e-5, rtol=1e-5, atol=1e-8)
     assert_parity(g, o)
+
+
+def test_own_exp_and_reciprocal_against_cuda():
+    """The integrator's table-driven exp and Newton reciprocal agree with CUDA's
+    exp and IEEE division to within 2 ulp over the arguments the rates use
+    (and beyond), and fall back to the library outside |x| < 700."""
+    d = dlb()
+    ctx = d.Context(states.mech_path(10, 20, 0))
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(-700, 700, 200000), rng.uniform(-5, 5, 200000),
+                        np.array([0.0, -0.0, 1e-300, 699.9, -699.9, 710.0, -745.0, 1e-20])])
+    xt = torch.tensor(x, device=DEV)
+    out = ctx.check_math(xt).cpu().numpy()
+    rel_exp = np.abs(out[:, 0] - out[:, 1]) / np.maximum(np.abs(out[:, 1]), 1e-300)
+    ok = np.isfinite(out[:, 1]) & (out[:, 1] > 1e-290)
+    assert rel_exp[ok].max() <= 2 * 2.0**-52, rel_exp[ok].max()
+    np.testing.assert_array_equal(out[x >= 700, 0], out[x >= 700, 1])
+    r = rng.uniform(-30, 30, 300000)
+    rx = np.sign(rng.normal(size=r.size)) * 10.0**r
+    o2 = ctx.check_math(torch.tensor(rx, device=DEV)).cpu().numpy()
+    rel_rcp = np.abs(o2[:, 2] - o2[:, 3]) / np.abs(o2[:, 3])
+    assert rel_rcp.max() <= 2 * 2.0**-52, rel_rcp.max()

@@ -85,7 +85,10 @@ typedef struct dlbchem_options {
   double map_Ytol;      /* absolute composition tolerance (1e-4) */
   double map_Tmax;      /* > 0: only cells below this T qualify (0 = off) */
   int32_t team_warps;   /* warps per cell: 1, 2, 4, or 0 = automatic (1 up to 32 unknowns, 2 up to 64, else 4) */
-  int32_t reserved1;
+  int32_t precision;    /* 0: FP64 LU of the iteration matrix (default); 1: FP32 LU with FP64
+                           iterative refinement (residuals against the FP64 matrix, at most 3
+                           rounds, step redone with the FP64 LU if they do not converge).
+                           State, rates, error norm and step control stay FP64. Fixed at create. */
 } dlbchem_options;
 
 /* Fill *opt with the defaults listed above. Returns DLBCHEM_OK or BAD_ARG. */
@@ -170,10 +173,11 @@ int dlbchem_nreactions(const dlbchem_ctx* ctx);
  *   out[0] cells integrated, out[1] cells mapped, out[2] reference cell
  *   index (-1 if none), out[3] team size in threads, out[4] teams per CTA,
  *   out[5] CTAs launched by the integrator, out[6] dynamic shared memory
- *   bytes per CTA, out[7] integrator kernel launches in the call.
+ *   bytes per CTA, out[7] kernel launches in the call, out[8] steps whose
+ *   FP32 refinement fell back to the FP64 LU, out[9] precision mode.
  * Returns DLBCHEM_OK, BAD_ARG or CUDA.
  */
-int dlbchem_last_stats(dlbchem_ctx* ctx, int64_t out[8]);
+int dlbchem_last_stats(dlbchem_ctx* ctx, int64_t out[10]);
 
 /*
  * Device time of the kernels of the last call, in milliseconds, measured with

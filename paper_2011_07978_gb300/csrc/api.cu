@@ -158,6 +158,7 @@ bool valid_opts(const dlbchem_options* o, std::string& why) {
   if (o->chunk < 1) { why = "chunk must be >= 1"; return false; }
   if (!(o->map_Ttol >= 0) || !(o->map_Ytol >= 0) || !(o->map_Tmax >= 0)) { why = "mapping tolerances must be >= 0"; return false; }
   if (o->team_warps != 0 && o->team_warps != 1 && o->team_warps != 2 && o->team_warps != 4) { why = "team_warps must be 0, 1, 2 or 4"; return false; }
+  if (o->precision != 0 && o->precision != 1) { why = "precision must be 0 or 1"; return false; }
   return true;
 }
 
@@ -370,7 +371,7 @@ int dlbchem_options_default(dlbchem_options* o) {
   std::memset(o, 0, sizeof(*o));
   o->rtol = 1e-6; o->atol = 1e-10; o->max_steps = 100000; o->isothermal = 0; o->hmin_frac = 1e-20;
   o->schedule = DLBCHEM_SCHED_PLAIN; o->chunk = 1; o->mapping = 0; o->timing = 0;
-  o->map_Ttol = 1e-4; o->map_Ytol = 1e-4; o->map_Tmax = 0.0;
+  o->map_Ttol = 1e-4; o->map_Ytol = 1e-4; o->map_Tmax = 0.0; o->team_warps = 0; o->precision = 0;
   return DLBCHEM_OK;
 }
 
@@ -393,7 +394,7 @@ int dlbchem_create(const char* mech_path, const dlbchem_options* opt, dlbchem_ct
   c->wpc = o.team_warps ? o.team_warps : (c->hm.nsp + 1 <= 32 ? 1 : (c->hm.nsp + 1 <= 64 ? 2 : 4));
   std::vector<unsigned char> blob;
   if (!build_tables(c->hm, c->wpc, blob, c->dm, why)) { delete c; return fail(nullptr, DLBCHEM_BAD_MECH, why); }
-  c->L = make_layout(c->hm.nsp, c->hm.nrx, c->dm.N, c->dm.ld, c->dm.DS);
+  c->L = make_layout(c->hm.nsp, c->hm.nrx, c->dm.N, c->dm.ld, c->dm.DS, o.precision == 1);
   for (auto& ev : c->ev)
     if (cudaEventCreate(&ev) != cudaSuccess) { ev = nullptr; dlbchem_destroy(c); return fail(nullptr, DLBCHEM_CUDA, "cudaEventCreate failed"); }
   if (cudaMalloc(&c->d_blob, blob.size()) != cudaSuccess || cudaMalloc(&c->d_counter, 64) != cudaSuccess) {
@@ -414,6 +415,7 @@ int dlbchem_set_options(dlbchem_ctx* c, const dlbchem_options* opt) {
   std::string why;
   if (!valid_opts(opt, why)) return fail(c, DLBCHEM_BAD_ARG, why);
   if (opt->team_warps != c->opt.team_warps) return fail(c, DLBCHEM_BAD_ARG, "team_warps is fixed at creation");
+  if (opt->precision != c->opt.precision) return fail(c, DLBCHEM_BAD_ARG, "precision is fixed at creation");
   c->opt = *opt;
   return DLBCHEM_OK;
 }
@@ -427,8 +429,9 @@ int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, con
   if (!(dt > 0) || !std::isfinite(dt)) return fail(c, DLBCHEM_BAD_ARG, "dt must be positive and finite");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   c->last_stream = s;
-  for (int i = 0; i < 8; ++i) c->stats[i] = 0;
+  for (int i = 0; i < 10; ++i) c->stats[i] = 0;
   c->stats[2] = -1;
+  c->stats[9] = c->opt.precision;
   if (n == 0) return DLBCHEM_OK;
   if (!T || !p || !Y || !T_out || !Y_out) return fail(c, DLBCHEM_BAD_ARG, "NULL array pointer");
   int rc = ensure_ws(c, n);
@@ -460,9 +463,12 @@ int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, con
   std::memset(&a, 0, sizeof(a));
   a.m = c->dm;
   a.P.rtol = c->opt.rtol; a.P.atol = c->opt.atol; a.P.hmin_frac = c->opt.hmin_frac; a.P.dt = dt;
-  a.P.max_steps = c->opt.max_steps; a.P.isothermal = c->opt.isothermal;
+  a.P.max_steps = c->opt.max_steps; a.P.isothermal = c->opt.isothermal; a.P.precision = c->opt.precision;
   a.L = c->L;
   a.n = n; a.T = T; a.p = p; a.Y = Y; a.Tout = T_out; a.Yout = Y_out; a.steps = steps; a.status = status;
+  a.fallbacks = c->d_counter + 2;
+  if (c->opt.precision == 1 && (e = cudaMemsetAsync(c->d_counter + 2, 0, 8, s)) != cudaSuccess)
+    return cuda_fail(c, e, "cudaMemsetAsync");
   const bool listed = mapping || queue;
   a.perm = listed ? c->w_list : nullptr;
   a.nqueue = listed ? c->w_total : nullptr;
@@ -548,7 +554,7 @@ int dlbchem_integrate_host(dlbchem_ctx* c, int64_t n, double dt, const double* T
 int dlbchem_nspecies(const dlbchem_ctx* c) { return c ? c->hm.nsp : -1; }
 int dlbchem_nreactions(const dlbchem_ctx* c) { return c ? c->hm.nrx : -1; }
 
-int dlbchem_last_stats(dlbchem_ctx* c, int64_t out[8]) {
+int dlbchem_last_stats(dlbchem_ctx* c, int64_t out[10]) {
   if (!c || !out) return DLBCHEM_BAD_ARG;
   cudaError_t e = cudaStreamSynchronize(c->last_stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
@@ -562,7 +568,12 @@ int dlbchem_last_stats(dlbchem_ctx* c, int64_t out[8]) {
     c->stats[1] = c->last_n - m;
     c->stats[2] = int64_t(r) < c->last_n ? int64_t(r) : -1;
   }
-  for (int i = 0; i < 8; ++i) out[i] = c->stats[i];
+  if (c->opt.precision == 1 && c->last_n > 0) {
+    unsigned long long fb = 0;
+    if ((e = cudaMemcpy(&fb, c->d_counter + 2, 8, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
+    c->stats[8] = int64_t(fb);
+  }
+  for (int i = 0; i < 10; ++i) out[i] = c->stats[i];
   return DLBCHEM_OK;
 }
 

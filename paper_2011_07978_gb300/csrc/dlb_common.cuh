@@ -73,15 +73,17 @@ struct DevMech {
 struct IntegParams {
   double rtol, atol, hmin_frac, dt;
   int32_t max_steps, isothermal;
+  int32_t precision, reserved;   // precision 1: FP32 LU + FP64 refinement
 };
 
 // Offsets (in doubles) of one team's workspace inside dynamic shared memory.
 struct WsLayout {
   int M, y0, f0, ys, fs, u, c, E, Einv, hk, wdot, vv, dwdT, uu, invd, q, sig, dqdT, dlt, D, scal, perm;
-  int total;  // doubles per team (perm is int32 at the end, counted in doubles)
+  int M32, invd32, perm32, rr, dx, isc;   // mixed precision only (else 0-sized)
+  int total;  // doubles per team (int and float arrays are counted in doubles)
 };
 
-__host__ inline WsLayout make_layout(int nsp, int nrx, int N, int ld, int DS) {
+__host__ inline WsLayout make_layout(int nsp, int nrx, int N, int ld, int DS, bool mixed) {
   WsLayout L;
   int o = 0;
   auto take = [&](int n) { int r = o; o += (n + 1) & ~1; return r; };  // keep 16-byte alignment
@@ -107,6 +109,13 @@ __host__ inline WsLayout make_layout(int nsp, int nrx, int N, int ld, int DS) {
   L.D = take(nrx * DS);
   L.scal = take(32);
   L.perm = take((N + 1) / 2 + 1);
+  const int nm = mixed ? 1 : 0;
+  L.M32 = take(nm * ((N * ld + 1) / 2 + 1));
+  L.invd32 = take(nm * ((N + 1) / 2 + 1));
+  L.perm32 = take(nm * ((N + 1) / 2 + 1));
+  L.rr = take(nm * N);
+  L.dx = take(nm * N);
+  L.isc = take(nm * N);
   L.total = o;
   return L;
 }
@@ -132,6 +141,7 @@ struct KernelArgs {
   unsigned long long* counter;
   int chunk;
   int queue;
+  unsigned long long* fallbacks;   // steps whose FP32 refinement fell back to the FP64 LU
 };
 
 // Host-side launchers defined next to the kernels (integrator.cu).

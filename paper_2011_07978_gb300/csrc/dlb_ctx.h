@@ -56,6 +56,6 @@ struct dlbchem_ctx {
   int32_t* d_stage_i = nullptr;
   int64_t stage_cap = 0;
   cudaStream_t last_stream = nullptr;
-  int64_t stats[8] = {0, 0, -1, 0, 0, 0, 0, 0};
+  int64_t stats[10] = {0, 0, -1, 0, 0, 0, 0, 0, 0, 0};
   std::string err;
 };

@@ -70,6 +70,9 @@ struct WS {
   double *M, *y0, *f0, *ys, *fs, *u, *c, *E, *Einv, *hk, *wdot, *vv, *dwdT, *uu, *invd, *q, *sig, *dqdT, *dlt,
       *D, *scal;
   int* perm;
+  float *M32, *invd32;
+  int* perm32;
+  double *rr, *dx, *isc;
   const double* exptab;   // 64 entries of 2^(j/64), shared by the CTA
 };
 
@@ -80,6 +83,9 @@ __device__ __forceinline__ WS carve(double* base, const WsLayout& L) {
   w.wdot = base + L.wdot; w.vv = base + L.vv; w.dwdT = base + L.dwdT; w.uu = base + L.uu;
   w.invd = base + L.invd; w.q = base + L.q; w.sig = base + L.sig; w.dqdT = base + L.dqdT; w.dlt = base + L.dlt;
   w.D = base + L.D; w.scal = base + L.scal; w.perm = reinterpret_cast<int*>(base + L.perm);
+  w.M32 = reinterpret_cast<float*>(base + L.M32); w.invd32 = reinterpret_cast<float*>(base + L.invd32);
+  w.perm32 = reinterpret_cast<int*>(base + L.perm32);
+  w.rr = base + L.rr; w.dx = base + L.dx; w.isc = base + L.isc;
   return w;
 }
 
@@ -365,21 +371,34 @@ __device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, 
 // advance incrementally, with one integer division per pivot step.
 // Returns false if a pivot is zero.
 // ---------------------------------------------------------------------------
-template <int WPC>
-__device__ __forceinline__ bool lu_factor(const Team<WPC>& tm, double* M, int N, int ld, double* invd, int* perm) {
+template <class R>
+__device__ __forceinline__ unsigned long long abs_key(R x);
+template <>
+__device__ __forceinline__ unsigned long long abs_key<double>(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+template <>
+__device__ __forceinline__ unsigned long long abs_key<float>(float x) {
+  return (unsigned long long)(__float_as_uint(x) & 0x7fffffffu);
+}
+__device__ __forceinline__ double rcp_any(double d) { return rcp_nr(d); }
+__device__ __forceinline__ float rcp_any(float d) { return __frcp_rn(d); }
+
+template <int WPC, class R>
+__device__ __forceinline__ bool lu_factor(const Team<WPC>& tm, R* M, int N, int ld, R* invd, int* perm) {
   constexpr int TS = 32 * WPC;
   for (int i = tm.tid; i < N; i += TS) perm[i] = i;
   bool singular = false;
   tm.sync();
   for (int k = 0; k < N; ++k) {
     if (k > 0) {
-      const double iv = invd[k - 1];
+      const R iv = invd[k - 1];
       for (int j = k + tm.tid; j < N; j += TS) M[(k - 1) * ld + j] *= iv;
     }
     unsigned long long best = 0ull;
     int bi = k;
     for (int i = k + tm.tid; i < N; i += TS) {
-      const unsigned long long key = __double_as_longlong(M[i * ld + k]) & 0x7fffffffffffffffull;
+      const unsigned long long key = abs_key<R>(M[i * ld + k]);
       if (key > best) { best = key; bi = i; }
     }
 #pragma unroll
@@ -405,17 +424,17 @@ __device__ __forceinline__ bool lu_factor(const Team<WPC>& tm, double* M, int N,
     }
     if (bi != k) {
       for (int j = tm.tid; j < N; j += TS) {
-        const double a = M[k * ld + j];
+        const R a = M[k * ld + j];
         M[k * ld + j] = M[bi * ld + j];
         M[bi * ld + j] = a;
       }
       if (tm.tid == 0) { const int t = perm[k]; perm[k] = perm[bi]; perm[bi] = t; }
     }
     tm.sync();
-    const double d = M[k * ld + k];
-    if (d == 0.0) singular = true;
+    const R d = M[k * ld + k];
+    if (d == R(0)) singular = true;
     if (tm.warp == 0) {           // one warp takes the reciprocal and the column
-      const double inv = rcp_nr(d);
+      const R inv = rcp_any(d);
       if (tm.lane == 0) invd[k] = inv;
       for (int i = k + 1 + tm.lane; i < N; i += 32) M[i * ld + k] *= inv;
     }
@@ -427,9 +446,9 @@ __device__ __forceinline__ bool lu_factor(const Team<WPC>& tm, double* M, int N,
     if (tm.tid < tot) {
       const int dq = TS / wd, dr = TS - dq * wd;
       int ii = tm.tid / wd, jj = tm.tid - ii * wd;
-      const double* urow = M + k * ld + k + 1;
+      const R* urow = M + k * ld + k + 1;
       for (int e = tm.tid; e < tot; e += TS) {
-        double* mrow = M + (k + 1 + ii) * ld;
+        R* mrow = M + (k + 1 + ii) * ld;
         mrow[k + 1 + jj] = fma(-mrow[k], urow[jj], mrow[k + 1 + jj]);
         jj += dr;
         ii += dq;
@@ -445,22 +464,22 @@ __device__ __forceinline__ bool lu_factor(const Team<WPC>& tm, double* M, int N,
 // For N <= 128 the team's first warp sweeps alone with x in up to four
 // registers per lane, broadcasting each solved entry by a shuffle: no
 // shared-memory round trips and no barrier per column.
-template <int WPC>
-__device__ __forceinline__ void lu_solve(const Team<WPC>& tm, const double* M, int N, int ld, const double* invd,
+template <int WPC, class R>
+__device__ __forceinline__ void lu_solve(const Team<WPC>& tm, const R* M, int N, int ld, const R* invd,
                                       const int* perm, const double* b, double* x) {
   constexpr int TS = 32 * WPC;
   if (N <= 128) {
     if (tm.warp == 0) {
       const int l = tm.lane;
       const bool v0 = l < N, v1 = l + 32 < N, v2 = l + 64 < N, v3 = l + 96 < N;
-      double x0 = v0 ? b[perm[l]] : 0.0;
-      double x1 = v1 ? b[perm[l + 32]] : 0.0;
-      double x2 = v2 ? b[perm[l + 64]] : 0.0;
-      double x3 = v3 ? b[perm[l + 96]] : 0.0;
+      R x0 = v0 ? R(b[perm[l]]) : R(0);
+      R x1 = v1 ? R(b[perm[l + 32]]) : R(0);
+      R x2 = v2 ? R(b[perm[l + 64]]) : R(0);
+      R x3 = v3 ? R(b[perm[l + 96]]) : R(0);
       // forward sweep, unit lower L: rows r > j take -L_rj x_j
       for (int j = 0; j < N - 1; ++j) {
-        const double src = j < 32 ? x0 : (j < 64 ? x1 : (j < 96 ? x2 : x3));
-        const double xj = __shfl_sync(0xffffffffu, src, j & 31);
+        const R src = j < 32 ? x0 : (j < 64 ? x1 : (j < 96 ? x2 : x3));
+        const R xj = __shfl_sync(0xffffffffu, src, j & 31);
         if (j < 31 && v0 && l > j) x0 = fma(-M[l * ld + j], xj, x0);
         if (j < 63 && v1 && l + 32 > j) x1 = fma(-M[(l + 32) * ld + j], xj, x1);
         if (j < 95 && v2 && l + 64 > j) x2 = fma(-M[(l + 64) * ld + j], xj, x2);
@@ -472,35 +491,72 @@ __device__ __forceinline__ void lu_solve(const Team<WPC>& tm, const double* M, i
       if (v3) x3 *= invd[l + 96];
       // backward sweep, unit upper U~: rows r < j take -U~_rj x_j
       for (int j = N - 1; j > 0; --j) {
-        const double src = j < 32 ? x0 : (j < 64 ? x1 : (j < 96 ? x2 : x3));
-        const double xj = __shfl_sync(0xffffffffu, src, j & 31);
+        const R src = j < 32 ? x0 : (j < 64 ? x1 : (j < 96 ? x2 : x3));
+        const R xj = __shfl_sync(0xffffffffu, src, j & 31);
         if (v0 && l < j) x0 = fma(-M[l * ld + j], xj, x0);
         if (j > 32 && v1 && l + 32 < j) x1 = fma(-M[(l + 32) * ld + j], xj, x1);
         if (j > 64 && v2 && l + 64 < j) x2 = fma(-M[(l + 64) * ld + j], xj, x2);
         if (j > 96 && v3 && l + 96 < j) x3 = fma(-M[(l + 96) * ld + j], xj, x3);
       }
-      if (v0) x[l] = x0;
-      if (v1) x[l + 32] = x1;
-      if (v2) x[l + 64] = x2;
-      if (v3) x[l + 96] = x3;
+      if (v0) x[l] = double(x0);
+      if (v1) x[l + 32] = double(x1);
+      if (v2) x[l + 64] = double(x2);
+      if (v3) x[l + 96] = double(x3);
     }
     tm.sync();
     return;
   }
-  for (int i = tm.tid; i < N; i += TS) x[i] = b[perm[i]];
+  for (int i = tm.tid; i < N; i += TS) x[i] = double(R(b[perm[i]]));
   tm.sync();
   for (int j = 0; j < N - 1; ++j) {
     const double xj = x[j];
-    for (int i = j + 1 + tm.tid; i < N; i += TS) x[i] = fma(-M[i * ld + j], xj, x[i]);
+    for (int i = j + 1 + tm.tid; i < N; i += TS) x[i] = fma(-double(M[i * ld + j]), xj, x[i]);
     tm.sync();
   }
-  for (int i = tm.tid; i < N; i += TS) x[i] *= invd[i];
+  for (int i = tm.tid; i < N; i += TS) x[i] *= double(invd[i]);
   tm.sync();
   for (int j = N - 1; j > 0; --j) {
     const double xj = x[j];
-    for (int i = tm.tid; i < j; i += TS) x[i] = fma(-M[i * ld + j], xj, x[i]);
+    for (int i = tm.tid; i < j; i += TS) x[i] = fma(-double(M[i * ld + j]), xj, x[i]);
     tm.sync();
   }
+}
+
+// Mixed precision: x = M^-1 b with the FP32 factors of M, refined in FP64.
+// Each round takes the FP64 residual r = b - M x against the unfactored M,
+// solves for the correction with the FP32 factors and adds it; it stops when
+// the correction is below 1e-6 of the error-norm weights sc (isc = 1/sc) and
+// gives up after three rounds. Returns false if it did not converge.
+template <int WPC>
+__device__ __forceinline__ bool solve_refined(const Team<WPC>& tm, const double* M, const float* M32, int N, int ld,
+                                              const float* invd32, const int* perm32, const double* b, double* x,
+                                              double* r, double* dx, const double* isc) {
+  constexpr int TS = 32 * WPC;
+  lu_solve<WPC, float>(tm, M32, N, ld, invd32, perm32, b, x);
+  for (int it = 0; it < 3; ++it) {
+    for (int i = tm.tid; i < N; i += TS) {
+      const double* row = M + i * ld;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int j = 0;
+      for (; j + 3 < N; j += 4) {
+        s0 = fma(row[j], x[j], s0);
+        s1 = fma(row[j + 1], x[j + 1], s1);
+        s2 = fma(row[j + 2], x[j + 2], s2);
+        s3 = fma(row[j + 3], x[j + 3], s3);
+      }
+      for (; j < N; ++j) s0 = fma(row[j], x[j], s0);
+      r[i] = b[i] - ((s0 + s1) + (s2 + s3));
+    }
+    tm.sync();
+    lu_solve<WPC, float>(tm, M32, N, ld, invd32, perm32, r, dx);
+    int big = 0;
+    for (int i = tm.tid; i < N; i += TS) {
+      x[i] += dx[i];
+      big |= !(fabs(dx[i]) * isc[i] <= 1e-6);
+    }
+    if (!tm.any(big)) return true;
+  }
+  return false;
 }
 
 // weighted RMS norm sqrt(sum (v/sc)^2 / N) over a team vector
@@ -543,7 +599,7 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
                                int64_t cell, int64_t n, const double* __restrict__ Tin,
                                const double* __restrict__ pin, const double* __restrict__ Yin,
                                double* __restrict__ Tout, double* __restrict__ Yout, int32_t* __restrict__ steps_out,
-                               int32_t* __restrict__ status_out) {
+                               int32_t* __restrict__ status_out, unsigned long long* fallbacks) {
   constexpr int TS = 32 * WPC;
   const int N = m.N;
   const bool iso = P.isothermal != 0;
@@ -573,28 +629,50 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
       ++steps;
       const double ih = 1.0 / h;
       assemble<WPC>(m, tm, w, P1, iso, ih * (1.0 / kGamma));
-      const bool ok = lu_factor<WPC>(tm, w.M, N, m.ld, w.invd, w.perm);
-      // stage 1
-      lu_solve<WPC>(tm, w.M, N, m.ld, w.invd, w.perm, w.f0, u1);
-      // stage 2
-      for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(kA21, u1[i], w.y0[i]);
-      tm.sync();
-      eval_f<WPC>(m, tm, w, w.ys, P1, iso, w.fs);
-      for (int i = tm.tid; i < N; i += TS) w.fs[i] = fma(kC21 * ih, u1[i], w.fs[i]);
-      tm.sync();
-      lu_solve<WPC>(tm, w.M, N, m.ld, w.invd, w.perm, w.fs, u2);
-      // stage 3
-      for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(kA31, u1[i], fma(kA32, u2[i], w.y0[i]));
-      tm.sync();
-      eval_f<WPC>(m, tm, w, w.ys, P1, iso, w.fs);
-      for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(ih, fma(kC31, u1[i], kC32 * u2[i]), w.fs[i]);
-      tm.sync();
-      lu_solve<WPC>(tm, w.M, N, m.ld, w.invd, w.perm, w.ys, u3);
-      // stage 4 (same f as stage 3)
-      for (int i = tm.tid; i < N; i += TS)
-        w.ys[i] = fma(ih, fma(kC41, u1[i], fma(kC42, u2[i], kC43 * u3[i])), w.fs[i]);
-      tm.sync();
-      lu_solve<WPC>(tm, w.M, N, m.ld, w.invd, w.perm, w.ys, u4);
+      bool mixed = P.precision == 1;
+      bool ok;
+      if (mixed) {
+        const int nm = N * m.ld;
+        for (int i = tm.tid; i < nm; i += TS) w.M32[i] = float(w.M[i]);
+        for (int i = tm.tid; i < N; i += TS) w.isc[i] = rcp_nr(fma(P.rtol, fabs(w.y0[i]), P.atol));
+        tm.sync();
+        ok = lu_factor<WPC, float>(tm, w.M32, N, m.ld, w.invd32, w.perm32);
+        if (!ok) mixed = false;
+      }
+      if (!mixed) ok = lu_factor<WPC, double>(tm, w.M, N, m.ld, w.invd, w.perm);
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        bool conv = true;
+        auto solve = [&](const double* b, double* x) {
+          if (mixed) conv &= solve_refined<WPC>(tm, w.M, w.M32, N, m.ld, w.invd32, w.perm32, b, x, w.rr, w.dx, w.isc);
+          else lu_solve<WPC, double>(tm, w.M, N, m.ld, w.invd, w.perm, b, x);
+        };
+        // stage 1
+        solve(w.f0, u1);
+        // stage 2
+        for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(kA21, u1[i], w.y0[i]);
+        tm.sync();
+        eval_f<WPC>(m, tm, w, w.ys, P1, iso, w.fs);
+        for (int i = tm.tid; i < N; i += TS) w.fs[i] = fma(kC21 * ih, u1[i], w.fs[i]);
+        tm.sync();
+        solve(w.fs, u2);
+        // stage 3
+        for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(kA31, u1[i], fma(kA32, u2[i], w.y0[i]));
+        tm.sync();
+        eval_f<WPC>(m, tm, w, w.ys, P1, iso, w.fs);
+        for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(ih, fma(kC31, u1[i], kC32 * u2[i]), w.fs[i]);
+        tm.sync();
+        solve(w.ys, u3);
+        // stage 4 (same f as stage 3)
+        for (int i = tm.tid; i < N; i += TS)
+          w.ys[i] = fma(ih, fma(kC41, u1[i], fma(kC42, u2[i], kC43 * u3[i])), w.fs[i]);
+        tm.sync();
+        solve(w.ys, u4);
+        if (!mixed || conv) break;
+        // refinement did not converge: redo the stages with the FP64 LU (M is intact)
+        mixed = false;
+        if (tm.tid == 0 && fallbacks) atomicAdd(fallbacks, 1ull);
+        ok = lu_factor<WPC, double>(tm, w.M, N, m.ld, w.invd, w.perm);
+      }
       // new state (ys) and error estimate
       double acc = 0.0;
       for (int i = tm.tid; i < N; i += TS) {
@@ -658,7 +736,7 @@ __global__ void __launch_bounds__(128, WPC == 4 ? 4 : 1) rosenbrock_kernel(const
     const int64_t j = int64_t(blockIdx.x) * teams + team;
     if (j < nq) {
       const int64_t cell = a.perm ? int64_t(a.perm[j]) : j;
-      integrate_cell<WPC>(a.m, a.P, tm, w, cell, a.n, a.T, a.p, a.Y, a.Tout, a.Yout, a.steps, a.status);
+      integrate_cell<WPC>(a.m, a.P, tm, w, cell, a.n, a.T, a.p, a.Y, a.Tout, a.Yout, a.steps, a.status, a.fallbacks);
     }
     return;
   }
@@ -672,7 +750,7 @@ __global__ void __launch_bounds__(128, WPC == 4 ? 4 : 1) rosenbrock_kernel(const
     const int64_t last = min(first + int64_t(a.chunk), nq);
     for (int64_t qi = first; qi < last; ++qi) {
       const int64_t cell = a.perm[qi];
-      integrate_cell<WPC>(a.m, a.P, tm, w, cell, a.n, a.T, a.p, a.Y, a.Tout, a.Yout, a.steps, a.status);
+      integrate_cell<WPC>(a.m, a.P, tm, w, cell, a.n, a.T, a.p, a.Y, a.Tout, a.Yout, a.steps, a.status, a.fallbacks);
     }
   }
 }

@@ -107,7 +107,7 @@ extern "C" int dlbchem_integrate_static(dlbchem_ctx* c, int64_t n, double dt, co
   std::memset(&a, 0, sizeof(a));
   a.m = c->dm;
   a.P.rtol = c->opt.rtol; a.P.atol = c->opt.atol; a.P.hmin_frac = c->opt.hmin_frac; a.P.dt = dt;
-  a.P.max_steps = c->opt.max_steps; a.P.isothermal = c->opt.isothermal;
+  a.P.max_steps = c->opt.max_steps; a.P.isothermal = c->opt.isothermal; a.P.precision = c->opt.precision;
   a.L = c->L;
   a.n = n; a.T = T; a.p = p; a.Y = Y; a.Tout = T_out; a.Yout = Y_out; a.steps = steps; a.status = status;
   a.perm = list; a.nqueue = total; a.queue = 1; a.counter = counter; a.chunk = c->opt.chunk;

@@ -23,7 +23,7 @@ class dlbchem_options(ctypes.Structure):
                 ("isothermal", ctypes.c_int32), ("hmin_frac", ctypes.c_double), ("schedule", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("mapping", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("map_Ttol", ctypes.c_double), ("map_Ytol", ctypes.c_double), ("map_Tmax", ctypes.c_double),
-                ("team_warps", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("team_warps", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p
@@ -155,9 +155,10 @@ class Context:
                                                   hp(steps), hp(status), hp(Yref), sh))
 
     def last_stats(self) -> dict:
-        out = (ctypes.c_int64 * 8)()
+        out = (ctypes.c_int64 * 10)()
         self._check(load().dlbchem_last_stats(self._h, out))
-        keys = ["integrated", "mapped", "ref", "team_threads", "teams_per_cta", "ctas", "smem_bytes", "launches"]
+        keys = ["integrated", "mapped", "ref", "team_threads", "teams_per_cta", "ctas", "smem_bytes", "launches",
+                "fp64_fallbacks", "precision"]
         return dict(zip(keys, list(out)))
 
     def last_timing(self) -> dict:

@@ -314,3 +314,44 @@ def test_own_exp_and_reciprocal_against_cuda():
     o2 = ctx.check_math(torch.tensor(rx, device=DEV)).cpu().numpy()
     rel_rcp = np.abs(o2[:, 2] - o2[:, 3]) / np.abs(o2[:, 3])
     assert rel_rcp.max() <= 2 * 2.0**-52, rel_rcp.max()
+
+
+def _class_errors(T0, g, o):
+    """max |dT|/T and max |dY| per class (T < 900, 900-1600, > 1600 K)."""
+    cls = states.temperature_class(T0)
+    out = {}
+    for c, name in ((0, "T<900"), (2, "900-1600"), (1, "T>1600")):
+        sel = cls == c
+        if sel.any():
+            out[name] = (float((np.abs(g[0] - o[0]) / o[0])[sel].max()), float(np.abs(g[1] - o[1])[:, sel].max()))
+    return out
+
+
+def test_mixed_precision_c1_against_fp64_oracle(c1):
+    """FP32 LU of the iteration matrix + FP64 refinement (10 species, 1024 cells,
+    rtol 1e-6): state, rates and error norm stay FP64; the result meets the
+    same bar as the FP64 path at this tolerance."""
+    T, p, Y, ref = c1
+    d = dlb()
+    ctx = d.Context(states.mech_path(10, 20, 0), rtol=1e-6, atol=1e-10, precision=1)
+    g = run_gpu(ctx, T, p, Y, 1e-6)
+    st = ctx.last_stats()
+    assert st["precision"] == 1
+    tight = oracle.Oracle(states.mech_path(10, 20, 0)).integrate(T, p, Y, 1e-6, rtol=1e-10, atol=1e-16)
+    dT, dY, frac = assert_parity(g, ref, min_tight=0.95, tight_ref=tight[:2])
+    print(f"mixed c1: max dT/T {dT:.2e}, max dY {dY:.2e}, within 1e-9 {frac:.4f}, fp64 fallbacks "
+          f"{st['fp64_fallbacks']}, per class {_class_errors(T, g, ref)}")
+
+
+def test_mixed_precision_bimodal_sample():
+    d = dlb()
+    mech = states.mech_path(53, 325, 0)
+    T, p, Y, cls = _bimodal(1000, 7)
+    ctx = d.Context(mech, rtol=1e-5, atol=1e-8, precision=1, schedule=d.SCHED_QUEUE)
+    g = run_gpu(ctx, T, p, Y, 1e-5)
+    st = ctx.last_stats()
+    o = oracle.Oracle(mech).integrate(T, p, Y, 1e-5, rtol=1e-5, atol=1e-8)
+    tight = oracle.Oracle(mech).integrate(T, p, Y, 1e-5, rtol=1e-9, atol=1e-14)
+    dT, dY, frac = assert_parity(g, o, min_tight=0.95, tight_ref=tight[:2])
+    print(f"mixed bimodal: max dT/T {dT:.2e}, max dY {dY:.2e}, within 1e-9 {frac:.4f}, "
+          f"fp64 fallbacks {st['fp64_fallbacks']}")

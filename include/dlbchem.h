@@ -164,6 +164,47 @@ int dlbchem_integrate_static(dlbchem_ctx* ctx, int64_t ncells, double dt, const 
                              const double* Y, double* T_out, double* Y_out, int32_t* steps, int32_t* status,
                              void* cuda_stream);
 
+/*
+ * Batched uneven launch (SURVEY configuration of several meshes over several
+ * mechanisms; the paper's balancing across processes, Sec. 2.2, becomes one
+ * device queue per mechanism). Meshes that share a mechanism file form a
+ * class; each class runs as ONE persistent integrator launch whose work list
+ * spans all its meshes, longest first by the previous call's steps[]; the
+ * classes run on forked streams inside ONE captured CUDA graph.
+ *   dlbchem_batch_create  options common to all meshes (tolerances, ...);
+ *   dlbchem_batch_add     registers a mesh: mechanism path, ncells (< 2^27),
+ *                         its own dt and DEVICE arrays as in
+ *                         dlbchem_integrate (steps nullable: cost keys in,
+ *                         counts out; status nullable). At most 8 meshes per
+ *                         mechanism and 8 mechanisms. The arrays must stay
+ *                         valid while the graph exists (they are baked in).
+ *   dlbchem_batch_tune    autotuner: for each class, times every (team
+ *                         warps in {1,2,4}, queue chunk in {1,4,16}) on a
+ *                         sample of about sample_cells cells (prefixes of its
+ *                         meshes, whose outputs it overwrites) and keeps the
+ *                         fastest; results are cached per (species,
+ *                         reactions, dt) for the process. Synchronous.
+ *   dlbchem_batch_capture allocates the engines and workspaces, then
+ *                         captures the graph on `cuda_stream` (non-NULL).
+ *   dlbchem_batch_launch  replays the graph on `cuda_stream`.
+ *   dlbchem_batch_info    class i: out[0] meshes, out[1] cells, out[2] team
+ *                         warps, out[3] queue chunk, out[4] species,
+ *                         out[5] tuned sample time in microseconds (-1: untuned).
+ * Return DLBCHEM_OK, BAD_ARG, BAD_MECH, CUDA or OOM; the message is in
+ * dlbchem_batch_last_error.
+ */
+typedef struct dlbchem_batch dlbchem_batch;
+int dlbchem_batch_create(const dlbchem_options* opt, dlbchem_batch** out);
+int dlbchem_batch_add(dlbchem_batch* b, const char* mech_path, int64_t ncells, double dt, const double* T,
+                      const double* p, const double* Y, double* T_out, double* Y_out, int32_t* steps,
+                      int32_t* status);
+int dlbchem_batch_tune(dlbchem_batch* b, int64_t sample_cells, void* cuda_stream);
+int dlbchem_batch_capture(dlbchem_batch* b, void* cuda_stream);
+int dlbchem_batch_launch(dlbchem_batch* b, void* cuda_stream);
+int dlbchem_batch_info(dlbchem_batch* b, int cls, int64_t out[6]);
+const char* dlbchem_batch_last_error(const dlbchem_batch* b);
+void dlbchem_batch_destroy(dlbchem_batch* b);
+
 /* Number of species / reactions of the loaded mechanism (-1 if ctx NULL). */
 int dlbchem_nspecies(const dlbchem_ctx* ctx);
 int dlbchem_nreactions(const dlbchem_ctx* ctx);

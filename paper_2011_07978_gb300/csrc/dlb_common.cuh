@@ -120,6 +120,21 @@ __host__ inline WsLayout make_layout(int nsp, int nrx, int N, int ld, int DS, bo
   return L;
 }
 
+// One mesh of a batched launch: its arrays, size and flow step.
+constexpr int kMaxMesh = 8;
+constexpr int kMeshShift = 27;   // batched work-list entry = (mesh << 27) | cell
+struct MeshDesc {
+  int64_t n;
+  double dt;
+  const double* T;
+  const double* p;
+  const double* Y;
+  double* Tout;
+  double* Yout;
+  int32_t* steps;
+  int32_t* status;
+};
+
 // Arguments of the integrator kernel (one struct, passed by value).
 struct KernelArgs {
   DevMech m;
@@ -142,9 +157,20 @@ struct KernelArgs {
   int chunk;
   int queue;
   unsigned long long* fallbacks;   // steps whose FP32 refinement fell back to the FP64 LU
+  // batched launch (nmesh > 0): work-list entries are (mesh << kMeshShift) | cell
+  // and each mesh brings its own arrays and dt; the single-mesh fields above
+  // are then unused.
+  int nmesh;
+  MeshDesc mesh[kMaxMesh];
 };
 
-// Host-side launchers defined next to the kernels (integrator.cu).
+// Host-side launchers defined next to the kernels (integrator*.cu).
+cudaError_t launch_rosenbrock_w1(unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
+cudaError_t launch_rosenbrock_w2(unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
+cudaError_t launch_rosenbrock_w4(unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
+const void* rosenbrock_kernel_ptr_w1();
+const void* rosenbrock_kernel_ptr_w2();
+const void* rosenbrock_kernel_ptr_w4();
 cudaError_t launch_rosenbrock(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
 const void* rosenbrock_kernel_ptr(int wpc);
 cudaError_t launch_check_math(int64_t n, const double* x, const double* tab, double* out, cudaStream_t s);
@@ -158,6 +184,8 @@ cudaError_t launch_init_list(int64_t n, const int32_t* steps_in, int32_t* list, 
                              cudaStream_t s);
 cudaError_t launch_sort(int64_t n, const int64_t* mdev, uint32_t* keys, int32_t* list, uint32_t* keys_alt,
                         int32_t* list_alt, int32_t* hist, cudaStream_t s);
+cudaError_t launch_batch_list(int nmesh, const MeshDesc* mesh, const int64_t* offsets, int64_t total_n,
+                              int32_t* list, uint32_t* keys, int64_t* total, cudaStream_t s);
 cudaError_t launch_map_scatter(int64_t n, int nsp, const uint8_t* mapped, const unsigned long long* ref,
                                const double* ref_state, const double* T, const double* Y, double* Tout,
                                double* Yout, int32_t* steps, int32_t* status, cudaStream_t s);

@@ -1,0 +1,769 @@
+// Batched adaptive Rosenbrock integration of the per-cell chemistry ODE.
+//
+// Paper (arXiv 2011.07978) Sec. 1 / Sec. 2.1: every cell integrates its own
+// stiff ODE dPhi/dt = f(Phi) over the flow step dt; Sec. 2.2 stage 3 is this
+// solve. One team of threads (one warp, or four warps for mechanisms with
+// more than 64 unknowns) owns one cell at a time and keeps the whole cell in
+// shared memory: the dense iteration matrix M = I/(h gamma) - J, the stage
+// vectors and the per-species and per-reaction work arrays. Lanes split
+// species, reactions, matrix entries and rows; FP64 is the bottleneck on
+// GB300 (two FP64 FMA lanes per clock per SM, a warp instruction costs the
+// same whatever its active lanes), so every phase is laid out to keep all 32
+// lanes of a warp busy: flattened trailing updates in the LU, conflict-free
+// rounds of 32 for the sparse scatters.
+//
+// Every reduction runs in a fixed order, so a cell's result does not depend
+// on which team, CTA or launch integrates it (plain and queued schedules
+// agree bit for bit).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "dlb_common.cuh"
+
+namespace dlb {
+
+template <int WPC>
+struct Team {
+  static constexpr int TS = 32 * WPC;
+  int tid, warp, lane, bar_id;
+  double* red;          // 2*WPC doubles of cross-warp reduction scratch
+  mutable int parity;
+
+  __device__ __forceinline__ void sync() const {
+    if (WPC == 1) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(TS) : "memory");
+    }
+  }
+  // Sum over the team; every thread receives the bitwise-identical result.
+  __device__ __forceinline__ double sum(double x) const {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (WPC == 1) return x;
+    double* buf = red + parity * WPC;
+    parity ^= 1;
+    if (lane == 0) buf[warp] = x;
+    sync();
+    double s = buf[0];
+#pragma unroll
+    for (int w = 1; w < WPC; ++w) s += buf[w];
+    return s;
+  }
+  __device__ __forceinline__ int any(int x) const {
+    x = __any_sync(0xffffffffu, x);
+    if (WPC == 1) return x;
+    double* buf = red + parity * WPC;
+    parity ^= 1;
+    if (lane == 0) buf[warp] = x ? 1.0 : 0.0;
+    sync();
+    int r = 0;
+#pragma unroll
+    for (int w = 0; w < WPC; ++w) r |= buf[w] != 0.0;
+    return r;
+  }
+};
+
+struct WS {
+  double *M, *y0, *f0, *ys, *fs, *u, *c, *E, *Einv, *hk, *wdot, *vv, *dwdT, *uu, *invd, *q, *sig, *dqdT, *dlt,
+      *D, *scal;
+  int* perm;
+  float *M32, *invd32;
+  int* perm32;
+  double *rr, *dx, *isc;
+  const double* exptab;   // 64 entries of 2^(j/64), shared by the CTA
+};
+
+__device__ __forceinline__ WS carve(double* base, const WsLayout& L) {
+  WS w;
+  w.M = base + L.M; w.y0 = base + L.y0; w.f0 = base + L.f0; w.ys = base + L.ys; w.fs = base + L.fs;
+  w.u = base + L.u; w.c = base + L.c; w.E = base + L.E; w.Einv = base + L.Einv; w.hk = base + L.hk;
+  w.wdot = base + L.wdot; w.vv = base + L.vv; w.dwdT = base + L.dwdT; w.uu = base + L.uu;
+  w.invd = base + L.invd; w.q = base + L.q; w.sig = base + L.sig; w.dqdT = base + L.dqdT; w.dlt = base + L.dlt;
+  w.D = base + L.D; w.scal = base + L.scal; w.perm = reinterpret_cast<int*>(base + L.perm);
+  w.M32 = reinterpret_cast<float*>(base + L.M32); w.invd32 = reinterpret_cast<float*>(base + L.invd32);
+  w.perm32 = reinterpret_cast<int*>(base + L.perm32);
+  w.rr = base + L.rr; w.dx = base + L.dx; w.isc = base + L.isc;
+  return w;
+}
+
+// Mixture scalars shared by one rate evaluation.
+struct Mix {
+  double T, iT, lnT, S, rho, irho;
+};
+
+// exp(x) by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989):
+// x = (64 m + j) ln2/64 + r with |r| <= ln2/128, exp(x) = 2^m 2^(j/64) e^r.
+// k = 64 m + j is rounded with the 1.5*2^52 shift, r is reduced with a
+// two-constant Cody-Waite split of ln2/64 (32-bit high part, so k*hi is
+// exact), e^r is its degree-5 Taylor polynomial (remainder < 3.5e-17), and
+// 2^m is added to the exponent field. tab[j] = 2^(j/64) rounded to double.
+// About 10 FP64 operations against ~19 for the library exp; |x| >= 700 and
+// NaN go to the library exp.
+__device__ __forceinline__ double exp_tab(double x, const double* __restrict__ tab) {
+  if (!(fabs(x) < 700.0)) return exp(x);
+  const double kShift = 6755399441055744.0;                 // 1.5 * 2^52
+  const double t = fma(x, 92.33248261689366, kShift);       // x * 64 / ln2, rounded to an integer
+  const int ki = __double2loint(t);
+  const double k = t - kShift;
+  double r = fma(-k, 0.010830424696905538, x);              // ln2/64, high 32 bits
+  r = fma(-k, -6.563929801064195e-13, r);                   // ln2/64, remainder
+  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  p = fma(r, p, 1.0 / 6.0);
+  p = fma(r, p, 0.5);
+  p = fma(r, p, 1.0);
+  p = fma(r, p, 1.0);
+  const double v = tab[ki & 63] * p;
+  return __hiloint2double(__double2hiint(v) + ((ki >> 6) << 20), __double2loint(v));
+}
+
+// 1/d by two Newton-Raphson steps r <- r + r(1 - d r) from the hardware
+// approximation rcp.approx.ftz.f64 (each step doubles the correct bits).
+__device__ __forceinline__ double rcp_nr(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
+// ---------------------------------------------------------------------------
+// Rates. Species pass: concentrations c_k = rho Y_k / W_k, E_k = exp(-g_k/RT)
+// and 1/E_k (equilibrium constants as products of per-species factors:
+// 1/K_c = prod_reac E^nu' prod_prod (1/E)^nu'' (R_c T / p0)^dnu), molar h_k.
+// Reaction pass: k_f = exp(ln A + b ln T - Ea/(R T)), q = [M](fwd - rev).
+// With JAC, also d q / d c for each distinct participant (D slots), the
+// homogeneity sum sigma = sum_j c_j dq/dc_j, dq/dT at fixed c, and the
+// third-body difference fwd - rev. Then the incidence rounds gather
+// wdot_k = sum_r nu_kr q_r (and v, dwdT, u).
+// ---------------------------------------------------------------------------
+template <int WPC, bool JAC>
+__device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm, const WS& w, const double* yv,
+                                        double P1, Mix& mx) {
+  constexpr int TS = 32 * WPC;
+  const int nsp = m.nsp, nrx = m.nrx;
+  const double T = yv[0];
+  const double iT = 1.0 / T;
+  const double lnT = log(T);
+  double s = 0.0;
+  for (int k = tm.tid; k < nsp; k += TS) s = fma(yv[1 + k], m.iW[k], s);
+  const double S = tm.sum(s);
+  const double rho = P1 * iT / S;
+  mx.T = T; mx.iT = iT; mx.lnT = lnT; mx.S = S; mx.rho = rho; mx.irho = (T * S) / P1;
+  for (int k = tm.tid; k < nsp; k += TS) {
+    w.c[k] = rho * yv[1 + k] * m.iW[k];
+    const double e = exp_tab(fma(m.G2[k], lnT, fma(m.G3[k], T, -fma(m.G0[k], iT, m.G1[k]))), w.exptab);
+    w.E[k] = e;
+    w.Einv[k] = rcp_nr(e);
+    w.hk[k] = fma(T, fma(m.hcpb[k], T, m.cpa[k]), m.H0[k]);
+  }
+  if (tm.tid == 0) w.c[nsp] = 0.0;
+  tm.sync();
+  const double Ctot = P1 * iT;          // sum_k c_k (unit efficiencies)
+  const double C0inv = (kRc / 1.0) * T; // R_c T / p0, p0 = 1 atm
+  const double C0 = 1.0 / C0inv;
+  for (int r = tm.tid; r < nrx; r += TS) {
+    const RxnMeta mt = m.meta[r];
+    const double kf = exp_tab(fma(m.beta[r], lnT, fma(-m.EaR[r], iT, m.lnA[r])), w.exptab);
+    // expanded slots as fixed registers (unused slots hold 1)
+    const double a0 = w.c[mt.sp[0]];
+    const double a1 = mt.nr > 1 ? w.c[mt.sp[1]] : 1.0;
+    const double a2 = mt.nr > 2 ? w.c[mt.sp[2]] : 1.0;
+    double pf = kf * a0;
+    if (mt.nr > 1) pf *= a1;
+    if (mt.nr > 2) pf *= a2;
+    double pr = 0.0, kr = 0.0, b0 = 1.0, b1 = 1.0, b2 = 1.0;
+    if (mt.flags & RX_REV) {
+      kr = kf * w.E[mt.sp[0]];
+      if (mt.nr > 1) kr *= w.E[mt.sp[1]];
+      if (mt.nr > 2) kr *= w.E[mt.sp[2]];
+      kr *= w.Einv[mt.sp[3]];
+      if (mt.np > 1) kr *= w.Einv[mt.sp[4]];
+      if (mt.np > 2) kr *= w.Einv[mt.sp[5]];
+      if (mt.dnu > 0) { kr *= C0inv; if (mt.dnu > 1) kr *= C0inv; if (mt.dnu > 2) kr *= C0inv; }
+      if (mt.dnu < 0) { kr *= C0; if (mt.dnu < -1) kr *= C0; if (mt.dnu < -2) kr *= C0; }
+      b0 = w.c[mt.sp[3]];
+      b1 = mt.np > 1 ? w.c[mt.sp[4]] : 1.0;
+      b2 = mt.np > 2 ? w.c[mt.sp[5]] : 1.0;
+      pr = kr * b0;
+      if (mt.np > 1) pr *= b1;
+      if (mt.np > 2) pr *= b2;
+    }
+    double Mf = 1.0;
+    if (mt.flags & RX_TB) {
+      Mf = Ctot;
+      for (int e = mt.eff_begin; e < mt.eff_end; ++e) Mf = fma(m.eff_dm1[e], w.c[m.eff_sp[e]], Mf);
+    }
+    w.q[r] = Mf * (pf - pr);
+    if (JAC) {
+      double* D = w.D + r * m.DS;
+      for (int s2 = 0; s2 < mt.nds; ++s2) D[s2] = 0.0;
+      // d/dc_j of the slot product = product of the other slots
+      const double kfM = kf * Mf;
+      D[mt.ds[0]] += kfM * (a1 * a2);
+      if (mt.nr > 1) D[mt.ds[1]] += kfM * (a0 * a2);
+      if (mt.nr > 2) D[mt.ds[2]] += kfM * (a0 * a1);
+      if (mt.flags & RX_REV) {
+        const double krM = kr * Mf;
+        D[mt.ds[3]] -= krM * (b1 * b2);
+        if (mt.np > 1) D[mt.ds[4]] -= krM * (b0 * b2);
+        if (mt.np > 2) D[mt.ds[5]] -= krM * (b0 * b1);
+      }
+      const int tb = (mt.flags & RX_TB) ? 1 : 0;
+      if (mt.flags & RX_EFF) D[mt.dslot_eff] = pf - pr;
+      w.sig[r] = Mf * ((mt.nr + tb) * pf - (mt.np + tb) * pr);
+      const double dlnkf = fma(m.EaR[r], iT * iT, m.beta[r] * iT);
+      double dq = pf * dlnkf;
+      if (mt.flags & RX_REV) {
+        double dH = w.hk[mt.sp[3]] - w.hk[mt.sp[0]];
+        if (mt.np > 1) dH += w.hk[mt.sp[4]];
+        if (mt.np > 2) dH += w.hk[mt.sp[5]];
+        if (mt.nr > 1) dH -= w.hk[mt.sp[1]];
+        if (mt.nr > 2) dH -= w.hk[mt.sp[2]];
+        const double dlnKc = dH * iT * iT * (1.0 / kR) - mt.dnu * iT;
+        dq -= pr * (dlnkf - dlnKc);
+      }
+      w.dqdT[r] = Mf * dq;
+      w.dlt[r] = tb ? (pf - pr) : 0.0;
+    }
+  }
+  for (int k = tm.tid; k <= nsp; k += TS) {
+    w.wdot[k] = 0.0;
+    if (JAC) { w.vv[k] = 0.0; w.dwdT[k] = 0.0; w.uu[k] = 0.0; }
+  }
+  tm.sync();
+  // incidence rounds: within a round every lane owns a distinct species
+  const int r0 = m.inc_ptr[tm.warp], r1 = m.inc_ptr[tm.warp + 1];
+  for (int rd = r0; rd < r1; ++rd) {
+    const uint32_t e = m.inc[rd * 32 + tm.lane];
+    const int k = int(e >> 20), r = int((e >> 4) & 0xffffu);
+    const double nu = double(int(e & 15u) - 8);
+    w.wdot[k] = fma(nu, w.q[r], w.wdot[k]);
+    if (JAC) {
+      w.vv[k] = fma(nu, w.sig[r], w.vv[k]);
+      w.dwdT[k] = fma(nu, w.dqdT[r], w.dwdT[k]);
+      w.uu[k] = fma(nu, w.dlt[r], w.uu[k]);
+    }
+    __syncwarp();
+  }
+  tm.sync();
+}
+
+// f = (f_T, f_Y): f_Y_k = W_k wdot_k / rho, f_T = -sum h_k wdot_k / (rho cp_mass).
+// Returns Q = sum h_k wdot_k and cp_mass through the references.
+template <int WPC>
+__device__ __forceinline__ void finish_f(const DevMech& m, const Team<WPC>& tm, const WS& w, const double* yv,
+                                         const Mix& mx, bool iso, double* f, double& Q, double& cpm) {
+  constexpr int TS = 32 * WPC;
+  double q = 0.0, cp = 0.0;
+  for (int k = tm.tid; k < m.nsp; k += TS) {
+    f[1 + k] = m.W[k] * w.wdot[k] * mx.irho;
+    q = fma(w.hk[k], w.wdot[k], q);
+    cp = fma(yv[1 + k] * m.iW[k], fma(m.cpb[k], mx.T, m.cpa[k]), cp);
+  }
+  Q = tm.sum(q);
+  cpm = tm.sum(cp);
+  if (tm.tid == 0) f[0] = iso ? 0.0 : -Q * mx.irho / cpm;
+  tm.sync();
+}
+
+template <int WPC>
+__device__ __forceinline__ void eval_f(const DevMech& m, const Team<WPC>& tm, const WS& w, const double* yv,
+                                       double P1, bool iso, double* f) {
+  Mix mx;
+  eval_rates<WPC, false>(m, tm, w, yv, P1, mx);
+  double Q, cpm;
+  finish_f<WPC>(m, tm, w, yv, mx, iso, f, Q, cpm);
+}
+
+// ---------------------------------------------------------------------------
+// Jacobian and iteration matrix M = I/(h gamma) - J at y0 (also f0 = f(y0)).
+// Rows/columns: 0 = T, 1 + k = Y_k. Species block:
+//   J_kj = (W_k / W_j) dwdot_k/dc_j + r_k / W_j,
+//   r_k = W_k (u_k + (wdot_k - v_k) / (rho S)),
+// where the sparse part comes from the triple rounds (coefficients
+// nu_kr W_k / W_j applied to the D slots), u is the unit-efficiency
+// third-body term and v_k = sum_j c_j dwdot_k/dc_j the chain rule through
+// rho(T, Y).
+// ---------------------------------------------------------------------------
+template <int WPC>
+__device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, const WS& w, double P1, bool iso,
+                                      double ihg) {
+  constexpr int TS = 32 * WPC;
+  const int nsp = m.nsp, N = m.N, ld = m.ld;
+  Mix mx;
+  eval_rates<WPC, true>(m, tm, w, w.y0, P1, mx);
+  double Q, cpm;
+  finish_f<WPC>(m, tm, w, w.y0, mx, iso, w.f0, Q, cpm);
+  const int ntot = N * ld + 2;
+  for (int i = tm.tid; i < ntot; i += TS) w.M[i] = 0.0;
+  tm.sync();
+  const int t0 = m.tri_ptr[tm.warp], t1 = m.tri_ptr[tm.warp + 1];
+  for (int rd = t0; rd < t1; ++rd) {
+    const uint32_t e = m.tri[rd * 32 + tm.lane];
+    const double cf = m.tri_coef[rd * 32 + tm.lane];
+    const int tgt = int(e >> 16), d = int(e & 0xffffu);
+    w.M[tgt] = fma(cf, w.D[d], w.M[tgt]);
+    __syncwarp();
+  }
+  tm.sync();
+  // scalars for the T row / column
+  double hv = 0.0, hu = 0.0, dc = 0.0, tt = 0.0;
+  for (int k = tm.tid; k < nsp; k += TS) {
+    hv = fma(w.hk[k], w.vv[k], hv);
+    hu = fma(w.hk[k], w.uu[k], hu);
+    dc = fma(w.y0[1 + k], m.bW[k], dc);
+    const double cpk = fma(m.cpb[k], mx.T, m.cpa[k]);
+    tt = fma(cpk, w.wdot[k], fma(w.hk[k], fma(-w.vv[k], mx.iT, w.dwdT[k]), tt));
+  }
+  const double Hv = tm.sum(hv), Hu = tm.sum(hu), dcpm = tm.sum(dc), Tsum = tm.sum(tt);
+  const double irS = mx.irho / mx.S;
+  const double icpm = 1.0 / cpm;
+  // r_k into E, h_k/W_k into Einv (both free after the rate pass); T column
+  // M[1+k][0] = -J_kT, J_kT = W_k/rho (dwdT_k + (wdot_k - v_k)/T)
+  for (int k = tm.tid; k < nsp; k += TS) {
+    w.E[k] = m.W[k] * fma(w.wdot[k] - w.vv[k], irS, w.uu[k]);
+    w.Einv[k] = w.hk[k] * m.iW[k];
+    w.M[(1 + k) * ld] = -m.W[k] * mx.irho * fma(w.wdot[k] - w.vv[k], mx.iT, w.dwdT[k]);
+  }
+  tm.sync();
+  // T row: J_Tj = (1/cp) [ -sum_k (h_k/W_k) Shat_kj + (1/W_j)(-Hu + (Hv - Q)/(rho S) + Q cp_j/(rho cp)) ]
+  for (int j = tm.tid; j < nsp; j += TS) {
+    double hs = 0.0;
+    for (int k = 0; k < nsp; ++k) hs = fma(w.Einv[k], w.M[(1 + k) * ld + 1 + j], hs);
+    const double cpj = fma(m.cpb[j], mx.T, m.cpa[j]);
+    const double bracket = fma(Q * cpj, mx.irho * icpm, fma(Hv - Q, irS, -Hu));
+    const double JT = icpm * fma(m.iW[j], bracket, -hs);
+    w.M[1 + j] = iso ? 0.0 : -JT;
+  }
+  if (tm.tid == 0) {
+    // J_TT = -(1/(rho cp)) sum_k (cp_k wdot_k + h_k dwdot_k/dT) - Q (1/(rho cp T) - dcp/dT/(rho cp^2))
+    const double JTT = -mx.irho * icpm * Tsum - Q * mx.irho * icpm * (mx.iT - dcpm * icpm);
+    w.M[0] = iso ? ihg : ihg - JTT;
+  }
+  tm.sync();
+  // species block: M = delta/(h gamma) - (Shat_kj + r_k / W_j); warps take rows, lanes columns
+  for (int k = tm.warp; k < nsp; k += WPC) {
+    const double rk = w.E[k];
+    double* row = w.M + (1 + k) * ld + 1;
+    for (int j = tm.lane; j < nsp; j += 32) {
+      double v = -fma(rk, m.iW[j], row[j]);
+      if (k == j) v += ihg;
+      row[j] = v;
+    }
+  }
+  tm.sync();
+}
+
+// ---------------------------------------------------------------------------
+// Dense LU with partial pivoting, in place, row-major with leading dim ld.
+// P M = L D U~ with L unit lower (multipliers below the diagonal), D the
+// pivots (their inverses kept in invd) and U~ = D^-1 U unit upper: each row
+// of U is scaled by its inverse pivot one step after it is used, so the
+// triangular solves need no division. The pivot is the first row of largest
+// |M_ik| (compared through the IEEE bit pattern, which orders |x| exactly).
+// Trailing update: the wd x wd block is flattened over the team's threads so
+// every lane of every FP64 instruction does useful work (on GB300 a warp FP64
+// instruction costs the same with 1 or 32 active lanes); the element indices
+// advance incrementally, with one integer division per pivot step.
+// Returns false if a pivot is zero.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ unsigned long long abs_key(R x);
+template <>
+__device__ __forceinline__ unsigned long long abs_key<double>(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+template <>
+__device__ __forceinline__ unsigned long long abs_key<float>(float x) {
+  return (unsigned long long)(__float_as_uint(x) & 0x7fffffffu);
+}
+__device__ __forceinline__ double rcp_any(double d) { return rcp_nr(d); }
+__device__ __forceinline__ float rcp_any(float d) { return __frcp_rn(d); }
+
+template <int WPC, class R>
+__device__ __forceinline__ bool lu_factor(const Team<WPC>& tm, R* M, int N, int ld, R* invd, int* perm) {
+  constexpr int TS = 32 * WPC;
+  for (int i = tm.tid; i < N; i += TS) perm[i] = i;
+  bool singular = false;
+  tm.sync();
+  for (int k = 0; k < N; ++k) {
+    if (k > 0) {
+      const R iv = invd[k - 1];
+      for (int j = k + tm.tid; j < N; j += TS) M[(k - 1) * ld + j] *= iv;
+    }
+    unsigned long long best = 0ull;
+    int bi = k;
+    for (int i = k + tm.tid; i < N; i += TS) {
+      const unsigned long long key = abs_key<R>(M[i * ld + k]);
+      if (key > best) { best = key; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (WPC > 1) {
+      double* buf = tm.red + tm.parity * WPC;
+      tm.parity ^= 1;
+      int* ibuf = reinterpret_cast<int*>(buf);
+      unsigned long long* kbuf = reinterpret_cast<unsigned long long*>(tm.red + 2 * WPC);
+      if (tm.lane == 0) { kbuf[tm.warp] = best; ibuf[2 * tm.warp] = bi; }
+      tm.sync();
+      best = kbuf[0]; bi = ibuf[0];
+      for (int wv = 1; wv < WPC; ++wv) {
+        const unsigned long long ob = kbuf[wv];
+        const int oi = ibuf[2 * wv];
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      tm.sync();
+    }
+    if (bi != k) {
+      for (int j = tm.tid; j < N; j += TS) {
+        const R a = M[k * ld + j];
+        M[k * ld + j] = M[bi * ld + j];
+        M[bi * ld + j] = a;
+      }
+      if (tm.tid == 0) { const int t = perm[k]; perm[k] = perm[bi]; perm[bi] = t; }
+    }
+    tm.sync();
+    const R d = M[k * ld + k];
+    if (d == R(0)) singular = true;
+    if (tm.warp == 0) {           // one warp takes the reciprocal and the column
+      const R inv = rcp_any(d);
+      if (tm.lane == 0) invd[k] = inv;
+      for (int i = k + 1 + tm.lane; i < N; i += 32) M[i * ld + k] *= inv;
+    }
+    tm.sync();
+    // flattened trailing update over the wd x wd block: element e = ii*wd + jj,
+    // thread t takes e = t, t + TS, ...; (ii, jj) advance by (TS / wd, TS % wd)
+    const int wd = N - 1 - k;
+    const int tot = wd * wd;
+    if (tm.tid < tot) {
+      const int dq = TS / wd, dr = TS - dq * wd;
+      int ii = tm.tid / wd, jj = tm.tid - ii * wd;
+      const R* urow = M + k * ld + k + 1;
+      for (int e = tm.tid; e < tot; e += TS) {
+        R* mrow = M + (k + 1 + ii) * ld;
+        mrow[k + 1 + jj] = fma(-mrow[k], urow[jj], mrow[k + 1 + jj]);
+        jj += dr;
+        ii += dq;
+        if (jj >= wd) { jj -= wd; ++ii; }
+      }
+    }
+    tm.sync();
+  }
+  return !singular;
+}
+
+// x = M^-1 b with the factors above; b and x are distinct team vectors.
+// For N <= 128 the team's first warp sweeps alone with x in up to four
+// registers per lane, broadcasting each solved entry by a shuffle: no
+// shared-memory round trips and no barrier per column.
+template <int WPC, class R>
+__device__ __forceinline__ void lu_solve(const Team<WPC>& tm, const R* M, int N, int ld, const R* invd,
+                                      const int* perm, const double* b, double* x) {
+  constexpr int TS = 32 * WPC;
+  if (N <= 128) {
+    if (tm.warp == 0) {
+      const int l = tm.lane;
+      const bool v0 = l < N, v1 = l + 32 < N, v2 = l + 64 < N, v3 = l + 96 < N;
+      R x0 = v0 ? R(b[perm[l]]) : R(0);
+      R x1 = v1 ? R(b[perm[l + 32]]) : R(0);
+      R x2 = v2 ? R(b[perm[l + 64]]) : R(0);
+      R x3 = v3 ? R(b[perm[l + 96]]) : R(0);
+      // forward sweep, unit lower L: rows r > j take -L_rj x_j
+      for (int j = 0; j < N - 1; ++j) {
+        const R src = j < 32 ? x0 : (j < 64 ? x1 : (j < 96 ? x2 : x3));
+        const R xj = __shfl_sync(0xffffffffu, src, j & 31);
+        if (j < 31 && v0 && l > j) x0 = fma(-M[l * ld + j], xj, x0);
+        if (j < 63 && v1 && l + 32 > j) x1 = fma(-M[(l + 32) * ld + j], xj, x1);
+        if (j < 95 && v2 && l + 64 > j) x2 = fma(-M[(l + 64) * ld + j], xj, x2);
+        if (v3 && l + 96 > j) x3 = fma(-M[(l + 96) * ld + j], xj, x3);
+      }
+      if (v0) x0 *= invd[l];
+      if (v1) x1 *= invd[l + 32];
+      if (v2) x2 *= invd[l + 64];
+      if (v3) x3 *= invd[l + 96];
+      // backward sweep, unit upper U~: rows r < j take -U~_rj x_j
+      for (int j = N - 1; j > 0; --j) {
+        const R src = j < 32 ? x0 : (j < 64 ? x1 : (j < 96 ? x2 : x3));
+        const R xj = __shfl_sync(0xffffffffu, src, j & 31);
+        if (v0 && l < j) x0 = fma(-M[l * ld + j], xj, x0);
+        if (j > 32 && v1 && l + 32 < j) x1 = fma(-M[(l + 32) * ld + j], xj, x1);
+        if (j > 64 && v2 && l + 64 < j) x2 = fma(-M[(l + 64) * ld + j], xj, x2);
+        if (j > 96 && v3 && l + 96 < j) x3 = fma(-M[(l + 96) * ld + j], xj, x3);
+      }
+      if (v0) x[l] = double(x0);
+      if (v1) x[l + 32] = double(x1);
+      if (v2) x[l + 64] = double(x2);
+      if (v3) x[l + 96] = double(x3);
+    }
+    tm.sync();
+    return;
+  }
+  for (int i = tm.tid; i < N; i += TS) x[i] = double(R(b[perm[i]]));
+  tm.sync();
+  for (int j = 0; j < N - 1; ++j) {
+    const double xj = x[j];
+    for (int i = j + 1 + tm.tid; i < N; i += TS) x[i] = fma(-double(M[i * ld + j]), xj, x[i]);
+    tm.sync();
+  }
+  for (int i = tm.tid; i < N; i += TS) x[i] *= double(invd[i]);
+  tm.sync();
+  for (int j = N - 1; j > 0; --j) {
+    const double xj = x[j];
+    for (int i = tm.tid; i < j; i += TS) x[i] = fma(-double(M[i * ld + j]), xj, x[i]);
+    tm.sync();
+  }
+}
+
+// Mixed precision: x = M^-1 b with the FP32 factors of M, refined in FP64.
+// Each round takes the FP64 residual r = b - M x against the unfactored M,
+// solves for the correction with the FP32 factors and adds it; it stops when
+// the correction is below 1e-6 of the error-norm weights sc (isc = 1/sc) and
+// gives up after three rounds. Returns false if it did not converge.
+template <int WPC>
+__device__ __forceinline__ bool solve_refined(const Team<WPC>& tm, const double* M, const float* M32, int N, int ld,
+                                              const float* invd32, const int* perm32, const double* b, double* x,
+                                              double* r, double* dx, const double* isc) {
+  constexpr int TS = 32 * WPC;
+  lu_solve<WPC, float>(tm, M32, N, ld, invd32, perm32, b, x);
+  for (int it = 0; it < 3; ++it) {
+    for (int i = tm.tid; i < N; i += TS) {
+      const double* row = M + i * ld;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int j = 0;
+      for (; j + 3 < N; j += 4) {
+        s0 = fma(row[j], x[j], s0);
+        s1 = fma(row[j + 1], x[j + 1], s1);
+        s2 = fma(row[j + 2], x[j + 2], s2);
+        s3 = fma(row[j + 3], x[j + 3], s3);
+      }
+      for (; j < N; ++j) s0 = fma(row[j], x[j], s0);
+      r[i] = b[i] - ((s0 + s1) + (s2 + s3));
+    }
+    tm.sync();
+    lu_solve<WPC, float>(tm, M32, N, ld, invd32, perm32, r, dx);
+    int big = 0;
+    for (int i = tm.tid; i < N; i += TS) {
+      x[i] += dx[i];
+      big |= !(fabs(dx[i]) * isc[i] <= 1e-6);
+    }
+    if (!tm.any(big)) return true;
+  }
+  return false;
+}
+
+// weighted RMS norm sqrt(sum (v/sc)^2 / N) over a team vector
+template <int WPC>
+__device__ __forceinline__ double wrms(const Team<WPC>& tm, const double* v, const double* sc, int N) {
+  double s = 0.0;
+  for (int i = tm.tid; i < N; i += 32 * WPC) { const double r = v[i] / sc[i]; s = fma(r, r, s); }
+  return sqrt(tm.sum(s) / N);
+}
+
+// Starting step (Hairer, Norsett, Wanner, Solving ODEs I, Sec. II.4) with the
+// order-3 error exponent 1/4 and fallbacks scaled by dt. Uses ys, fs, u.
+template <int WPC>
+__device__ double initial_step(const DevMech& m, const Team<WPC>& tm, const WS& w, const IntegParams& P,
+                               double P1, bool iso) {
+  constexpr int TS = 32 * WPC;
+  const int N = m.N;
+  double* sc = w.u;
+  for (int i = tm.tid; i < N; i += TS) sc[i] = fma(P.rtol, fabs(w.y0[i]), P.atol);
+  tm.sync();
+  const double d0 = wrms(tm, w.y0, sc, N), d1 = wrms(tm, w.f0, sc, N);
+  double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 * P.dt : 0.01 * d0 / d1;
+  h0 = fmin(h0, P.dt);
+  for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(h0, w.f0[i], w.y0[i]);
+  tm.sync();
+  eval_f<WPC>(m, tm, w, w.ys, P1, iso, w.fs);
+  double* df = w.u + N;
+  for (int i = tm.tid; i < N; i += TS) df[i] = w.fs[i] - w.f0[i];
+  tm.sync();
+  const double d2 = wrms(tm, df, sc, N) / h0;
+  if (!isfinite(d2)) return h0;
+  const double dm = fmax(d1, d2);
+  const double h1 = (dm <= 1e-15) ? fmax(1e-6 * P.dt, h0 * 1e-3) : pow(0.01 / dm, 0.25);
+  return fmin(fmin(100.0 * h0, h1), P.dt);
+}
+
+// Integrate one cell over [0, dt] (the oracle's algorithm step for step).
+template <int WPC>
+__device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Team<WPC>& tm, const WS& w,
+                               int64_t cell, int64_t n, const double* __restrict__ Tin,
+                               const double* __restrict__ pin, const double* __restrict__ Yin,
+                               double* __restrict__ Tout, double* __restrict__ Yout, int32_t* __restrict__ steps_out,
+                               int32_t* __restrict__ status_out, unsigned long long* fallbacks) {
+  constexpr int TS = 32 * WPC;
+  const int N = m.N;
+  const bool iso = P.isothermal != 0;
+  for (int i = tm.tid; i < N; i += TS) w.y0[i] = (i == 0) ? Tin[cell] : Yin[int64_t(i - 1) * n + cell];
+  const double p = pin[cell];
+  tm.sync();
+  int bad = 0;
+  for (int i = tm.tid; i < N; i += TS) bad |= !isfinite(w.y0[i]);
+  bad |= !(w.y0[0] > 0.0) || !(p > 0.0) || !isfinite(p);
+  bad = tm.any(bad);
+  int status = CELL_OK, steps = 0;
+  if (!bad) {
+    const double P1 = 1e-6 * p / kR;
+    eval_f<WPC>(m, tm, w, w.y0, P1, iso, w.f0);
+    double h = initial_step<WPC>(m, tm, w, P, P1, iso);
+    const double dt = P.dt;
+    double t = 0.0;
+    bool rejected_last = false;
+    double* u1 = w.u;
+    double* u2 = w.u + N;
+    double* u3 = w.u + 2 * N;
+    double* u4 = w.u + 3 * N;
+    while (t < dt) {
+      if (steps >= P.max_steps) { status = CELL_MAX_STEPS; break; }
+      if ((dt - t) - h <= 1e-12 * dt) h = dt - t;
+      if (h < P.hmin_frac * dt) { status = CELL_H_UNDERFLOW; break; }
+      ++steps;
+      const double ih = 1.0 / h;
+      assemble<WPC>(m, tm, w, P1, iso, ih * (1.0 / kGamma));
+      bool mixed = P.precision == 1;
+      bool ok;
+      if (mixed) {
+        const int nm = N * m.ld;
+        for (int i = tm.tid; i < nm; i += TS) w.M32[i] = float(w.M[i]);
+        for (int i = tm.tid; i < N; i += TS) w.isc[i] = rcp_nr(fma(P.rtol, fabs(w.y0[i]), P.atol));
+        tm.sync();
+        ok = lu_factor<WPC, float>(tm, w.M32, N, m.ld, w.invd32, w.perm32);
+        if (!ok) mixed = false;
+      }
+      if (!mixed) ok = lu_factor<WPC, double>(tm, w.M, N, m.ld, w.invd, w.perm);
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        bool conv = true;
+        auto solve = [&](const double* b, double* x) {
+          if (mixed) conv &= solve_refined<WPC>(tm, w.M, w.M32, N, m.ld, w.invd32, w.perm32, b, x, w.rr, w.dx, w.isc);
+          else lu_solve<WPC, double>(tm, w.M, N, m.ld, w.invd, w.perm, b, x);
+        };
+        // stage 1
+        solve(w.f0, u1);
+        // stage 2
+        for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(kA21, u1[i], w.y0[i]);
+        tm.sync();
+        eval_f<WPC>(m, tm, w, w.ys, P1, iso, w.fs);
+        for (int i = tm.tid; i < N; i += TS) w.fs[i] = fma(kC21 * ih, u1[i], w.fs[i]);
+        tm.sync();
+        solve(w.fs, u2);
+        // stage 3
+        for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(kA31, u1[i], fma(kA32, u2[i], w.y0[i]));
+        tm.sync();
+        eval_f<WPC>(m, tm, w, w.ys, P1, iso, w.fs);
+        for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(ih, fma(kC31, u1[i], kC32 * u2[i]), w.fs[i]);
+        tm.sync();
+        solve(w.ys, u3);
+        // stage 4 (same f as stage 3)
+        for (int i = tm.tid; i < N; i += TS)
+          w.ys[i] = fma(ih, fma(kC41, u1[i], fma(kC42, u2[i], kC43 * u3[i])), w.fs[i]);
+        tm.sync();
+        solve(w.ys, u4);
+        if (!mixed || conv) break;
+        // refinement did not converge: redo the stages with the FP64 LU (M is intact)
+        mixed = false;
+        if (tm.tid == 0 && fallbacks) atomicAdd(fallbacks, 1ull);
+        ok = lu_factor<WPC, double>(tm, w.M, N, m.ld, w.invd, w.perm);
+      }
+      // new state (ys) and error estimate
+      double acc = 0.0;
+      for (int i = tm.tid; i < N; i += TS) {
+        const double yn = fma(kM1, u1[i], fma(kM2, u2[i], fma(kM3, u3[i], fma(kM4, u4[i], w.y0[i]))));
+        const double er = fma(kE1, u1[i], fma(kE2, u2[i], fma(kE3, u3[i], kE4 * u4[i])));
+        const double sc = fma(P.rtol, fmax(fabs(w.y0[i]), fabs(yn)), P.atol);
+        const double r = er / sc;
+        acc = fma(r, r, acc);
+        w.ys[i] = yn;
+      }
+      double errn = sqrt(tm.sum(acc) / N);
+      if (!ok) errn = nan("");
+      if (errn <= 1.0) {
+        double fac = fmin(5.0, fmax(0.2, 0.9 * pow(errn, -0.25)));
+        if (rejected_last) fac = fmin(fac, 1.0);
+        t = (t + h >= dt) ? dt : t + h;
+        for (int i = tm.tid; i < N; i += TS) w.y0[i] = w.ys[i];
+        tm.sync();
+        rejected_last = false;
+        h *= fac;
+      } else {
+        const double fac = isfinite(errn) ? fmax(0.2, 0.9 * pow(errn, -0.25)) : 0.2;
+        rejected_last = true;
+        h *= fac;
+      }
+    }
+  }
+  for (int i = tm.tid; i < N; i += TS) {
+    if (i == 0) Tout[cell] = w.y0[0];
+    else Yout[int64_t(i - 1) * n + cell] = w.y0[i];
+  }
+  if (tm.tid == 0) {
+    if (steps_out) steps_out[cell] = steps;
+    if (status_out) status_out[cell] = bad ? CELL_NONFINITE : status;
+  }
+  tm.sync();
+}
+
+
+template <int WPC>
+__global__ void __launch_bounds__(128, WPC == 4 ? 4 : 1) rosenbrock_kernel(const KernelArgs a) {
+  extern __shared__ __align__(16) double smem[];
+  constexpr int TS = 32 * WPC;
+  const int teams = blockDim.x / TS;
+  const int team = threadIdx.x / TS;
+  Team<WPC> tm;
+  tm.tid = threadIdx.x % TS;
+  tm.warp = tm.tid >> 5;
+  tm.lane = threadIdx.x & 31;
+  tm.bar_id = 1 + team;
+  tm.parity = 0;
+  double* tab = smem + size_t(teams) * a.L.total;
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) tab[j] = a.m.exptab[j];
+  __syncthreads();
+  double* base = smem + size_t(team) * a.L.total;
+  WS w = carve(base, a.L);
+  w.exptab = tab;
+  tm.red = w.scal;
+  const int64_t nq = a.nqueue ? *a.nqueue : a.n;
+  // one work-list entry -> (arrays, cell, dt)
+  auto run = [&](int64_t entry) {
+    MeshDesc md;
+    int64_t cell = entry;
+    IntegParams P = a.P;
+    if (a.nmesh == 0) {
+      md = MeshDesc{a.n, a.P.dt, a.T, a.p, a.Y, a.Tout, a.Yout, a.steps, a.status};
+    } else {
+      const int mi = int(entry >> kMeshShift);
+      cell = entry & ((int64_t(1) << kMeshShift) - 1);
+      md = a.mesh[mi];
+      P.dt = md.dt;
+    }
+    integrate_cell<WPC>(a.m, P, tm, w, cell, md.n, md.T, md.p, md.Y, md.Tout, md.Yout, md.steps, md.status,
+                        a.fallbacks);
+  };
+  if (!a.queue) {
+    const int64_t j = int64_t(blockIdx.x) * teams + team;
+    if (j < nq) run(a.perm ? int64_t(a.perm[j]) : j);
+    return;
+  }
+  volatile int64_t* slot = reinterpret_cast<volatile int64_t*>(w.scal + 24);
+  for (;;) {
+    if (tm.tid == 0) *slot = int64_t(atomicAdd(a.counter, (unsigned long long)a.chunk));
+    tm.sync();
+    const int64_t first = *slot;
+    tm.sync();
+    if (first >= nq) break;
+    const int64_t last = min(first + int64_t(a.chunk), nq);
+    for (int64_t qi = first; qi < last; ++qi) run(int64_t(a.perm[qi]));
+  }
+}
+
+}  // namespace dlb

@@ -1,0 +1,13 @@
+// The batched Rosenbrock integrator with 4 warps per cell (see integrator_impl.cuh).
+#include "integrator_impl.cuh"
+
+namespace dlb {
+
+cudaError_t launch_rosenbrock_w4(unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a) {
+  rosenbrock_kernel<4><<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+const void* rosenbrock_kernel_ptr_w4() { return reinterpret_cast<const void*>(&rosenbrock_kernel<4>); }
+
+}  // namespace dlb

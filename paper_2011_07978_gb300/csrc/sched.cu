@@ -114,6 +114,22 @@ __global__ void init_list_kernel(int64_t n, const int32_t* __restrict__ steps_in
   keys[i] = 0xffffffffu - uint32_t(s > 0 ? s : 0);
 }
 
+// Batched work list: entries (mesh << kMeshShift) | cell over all meshes,
+// mesh by mesh in index order, with each cell's cost key.
+__global__ void batch_list_kernel(int nmesh, const MeshDesc* __restrict__ mesh, const int64_t* __restrict__ offsets,
+                                  int64_t total_n, int32_t* __restrict__ list, uint32_t* __restrict__ keys,
+                                  int64_t* __restrict__ total) {
+  const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (g == 0) *total = total_n;
+  if (g >= total_n) return;
+  int mi = 0;
+  while (mi + 1 < nmesh && g >= offsets[mi + 1]) ++mi;
+  const int64_t cell = g - offsets[mi];
+  list[g] = int32_t((int64_t(mi) << kMeshShift) | cell);
+  const int32_t s = mesh[mi].steps ? mesh[mi].steps[cell] : 0;
+  keys[g] = 0xffffffffu - uint32_t(s > 0 ? s : 0);
+}
+
 // LSD radix sort pass (8-bit digit), stable. Histogram per tile of 256 keys;
 // the list length m is read on the device (grids are sized for the bound n).
 __global__ void radix_hist_kernel(const int64_t* __restrict__ mdev, const uint32_t* __restrict__ keys, int shift,
@@ -232,6 +248,13 @@ cudaError_t launch_sort(int64_t n, const int64_t* mdev, uint32_t* keys, int32_t*
     uint32_t* tk = ka; ka = kb; kb = tk;
     int32_t* tv = va; va = vb; vb = tv;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_list(int nmesh, const MeshDesc* mesh, const int64_t* offsets, int64_t total_n,
+                              int32_t* list, uint32_t* keys, int64_t* total, cudaStream_t s) {
+  batch_list_kernel<<<unsigned(tiles_of(total_n)), kSchedThreads, 0, s>>>(nmesh, mesh, offsets, total_n, list, keys,
+                                                                         total);
   return cudaGetLastError();
 }
 

@@ -54,6 +54,15 @@ def load() -> ctypes.CDLL:
     lib.dlbchem_last_error.argtypes = [_vp]
     lib.dlbchem_last_error.restype = ctypes.c_char_p
     lib.dlbchem_destroy.argtypes = [_vp]
+    lib.dlbchem_batch_create.argtypes = [ctypes.POINTER(dlbchem_options), ctypes.POINTER(_vp)]
+    lib.dlbchem_batch_add.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int64, ctypes.c_double] + [_vp] * 7
+    lib.dlbchem_batch_tune.argtypes = [_vp, ctypes.c_int64, _vp]
+    lib.dlbchem_batch_capture.argtypes = [_vp, _vp]
+    lib.dlbchem_batch_launch.argtypes = [_vp, _vp]
+    lib.dlbchem_batch_info.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
+    lib.dlbchem_batch_last_error.argtypes = [_vp]
+    lib.dlbchem_batch_last_error.restype = ctypes.c_char_p
+    lib.dlbchem_batch_destroy.argtypes = [_vp]
     _lib = lib
     return lib
 
@@ -183,6 +192,60 @@ class Context:
     def close(self):
         if getattr(self, "_h", None):
             load().dlbchem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several meshes over several mechanisms in one captured CUDA graph
+    (dlbchem_batch_*). Arrays are CUDA tensors that must outlive the graph."""
+
+    def __init__(self, **opts):
+        lib = load()
+        o = options_default()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        h = _vp()
+        if lib.dlbchem_batch_create(ctypes.byref(o), ctypes.byref(h)) != OK:
+            raise DlbchemError(BAD_ARG, "batch create failed")
+        self._h = h
+        self._keep = []
+
+    def _check(self, rc):
+        if rc != OK:
+            raise DlbchemError(rc, load().dlbchem_batch_last_error(self._h).decode())
+
+    def add(self, mech_path, T, p, Y, dt, T_out, Y_out, steps=None, status=None):
+        self._keep.extend([T, p, Y, T_out, Y_out, steps, status])
+        self._check(load().dlbchem_batch_add(self._h, mech_path.encode(), T.numel(), float(dt), _ptr(T), _ptr(p),
+                                             _ptr(Y), _ptr(T_out), _ptr(Y_out), _ptr(steps), _ptr(status)))
+
+    def tune(self, sample_cells=4096, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self._check(load().dlbchem_batch_tune(self._h, int(sample_cells), ctypes.c_void_p(s.cuda_stream)))
+
+    def capture(self, stream):
+        self._check(load().dlbchem_batch_capture(self._h, ctypes.c_void_p(stream.cuda_stream)))
+
+    def launch(self, stream):
+        self._check(load().dlbchem_batch_launch(self._h, ctypes.c_void_p(stream.cuda_stream)))
+
+    def info(self, cls):
+        out = (ctypes.c_int64 * 6)()
+        self._check(load().dlbchem_batch_info(self._h, cls, out))
+        return dict(zip(["meshes", "cells", "team_warps", "chunk", "species", "tune_us"], list(out)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dlbchem_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

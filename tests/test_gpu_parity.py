@@ -355,3 +355,42 @@ def test_mixed_precision_bimodal_sample():
     dT, dY, frac = assert_parity(g, o, min_tight=0.95, tight_ref=tight[:2])
     print(f"mixed bimodal: max dT/T {dT:.2e}, max dY {dY:.2e}, within 1e-9 {frac:.4f}, "
           f"fp64 fallbacks {st['fp64_fallbacks']}")
+
+
+def test_batched_graph_matches_single_calls():
+    """Three uneven meshes over two mechanisms (53/325 twice with different
+    dt, 100/1000 once) in one captured graph, autotuned: every cell equals a
+    single dlbchem_integrate call with the same team size bit for bit, and a
+    second replay reproduces the first."""
+    d = dlb()
+    m53, m100 = states.mech_path(53, 325, 0), states.mech_path(100, 1000, 1)
+    spec = [(m53, 53, 1500, 1e-6, 21), (m100, 100, 96, 1e-6, 22), (m53, 53, 2500, 1e-5, 23)]
+    dd = lambda a: torch.tensor(np.ascontiguousarray(a), device=DEV)
+    b = d.Batch(rtol=1e-6, atol=1e-10)
+    meshes = []
+    for mech, nsp, n, dt, seed in spec:
+        T, p, Y = states.uniform_states(nsp, n, seed)
+        arr = dict(T=dd(T), p=dd(p), Y=dd(Y), To=torch.empty(n, dtype=torch.float64, device=DEV),
+                   Yo=torch.empty((nsp, n), dtype=torch.float64, device=DEV),
+                   st=torch.zeros(n, dtype=torch.int32, device=DEV), ss=torch.zeros(n, dtype=torch.int32, device=DEV))
+        b.add(mech, arr["T"], arr["p"], arr["Y"], dt, arr["To"], arr["Yo"], steps=arr["st"], status=arr["ss"])
+        meshes.append((mech, nsp, n, dt, arr))
+    stream = torch.cuda.Stream()
+    b.tune(sample_cells=256, stream=stream)
+    b.capture(stream)
+    info = [b.info(c) for c in range(2)]
+    assert info[0]["meshes"] == 2 and info[1]["meshes"] == 1 and all(i["team_warps"] in (1, 2, 4) for i in info)
+    b.launch(stream)
+    stream.synchronize()
+    first = [(a["To"].clone(), a["Yo"].clone(), a["ss"].clone()) for *_, a in meshes]
+    b.launch(stream)
+    stream.synchronize()
+    for (mech, nsp, n, dt, a), (To1, Yo1, ss1) in zip(meshes, first):
+        assert torch.equal(a["To"], To1) and torch.equal(a["Yo"], Yo1)
+        assert (a["ss"] == 0).all()
+        tw = info[0 if mech == m53 else 1]["team_warps"]
+        ctx = d.Context(mech, rtol=1e-6, atol=1e-10, team_warps=tw)
+        g = run_gpu(ctx, a["T"].cpu().numpy(), a["p"].cpu().numpy(), a["Y"].cpu().numpy(), dt)
+        np.testing.assert_array_equal(a["To"].cpu().numpy(), g[0])
+        np.testing.assert_array_equal(a["Yo"].cpu().numpy(), g[1])
+    b.close()

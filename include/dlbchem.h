@@ -54,6 +54,7 @@ extern "C" {
 /* Per-cell status[] values. */
 #define DLBCHEM_CELL_OK 0
 #define DLBCHEM_CELL_MAPPED 1          /* copied the reference cell's increment */
+#define DLBCHEM_CELL_SURROGATE 2       /* the network's increment passed the gate */
 #define DLBCHEM_CELL_MAX_STEPS (-1)    /* max_steps attempted steps reached */
 #define DLBCHEM_CELL_H_UNDERFLOW (-2)  /* step size fell below hmin_frac*dt */
 #define DLBCHEM_CELL_NONFINITE (-3)    /* input not finite, T <= 0 or p <= 0 */
@@ -89,6 +90,12 @@ typedef struct dlbchem_options {
                            iterative refinement (residuals against the FP64 matrix, at most 3
                            rounds, step redone with the FP64 LU if they do not converge).
                            State, rates, error norm and step control stay FP64. Fixed at create. */
+  int32_t predictor;    /* 1: order the queue by the attached network's predicted step counts
+                           (no previous call needed); steps[] is then only written */
+  int32_t surrogate;    /* 1: try the attached network's increments first; cells that pass the
+                           gate get status DLBCHEM_CELL_SURROGATE, the others are integrated */
+  double gate;          /* surrogate gate tolerance (default 1e-4): trapezoid defect per mass
+                           fraction (relative for T), |sum Y' - 1| and relative element change */
 } dlbchem_options;
 
 /* Fill *opt with the defaults listed above. Returns DLBCHEM_OK or BAD_ARG. */
@@ -204,6 +211,44 @@ int dlbchem_batch_launch(dlbchem_batch* b, void* cuda_stream);
 int dlbchem_batch_info(dlbchem_batch* b, int cls, int64_t out[6]);
 const char* dlbchem_batch_last_error(const dlbchem_batch* b);
 void dlbchem_batch_destroy(dlbchem_batch* b);
+
+/*
+ * Learned cost predictor and surrogate (the paper has no counterpart; it
+ * replaces the per-cell CPU time of the last step, Algorithm 1's t_cpu^n, by
+ * a prediction, and adds an error-gated shortcut). A multilayer perceptron
+ * n_in -> n_hidden -> n_hidden -> n_hidden -> n_out with SiLU, trained and run
+ * by the library's BF16 tensor-core kernels with FP32 accumulation. For a
+ * mechanism with nsp species: n_in = nsp + 3 (T/1000, ln p, Y, ln dt), n_out =
+ * nsp + 2 (ln attempted steps, dT, dY), each normalised by the stored means
+ * and standard deviations.
+ *   create / destroy / nparams; set_params / get_params copy the flat FP32
+ *   parameter vector [W1 b1 W2 b2 W3 b3 W4 b4] (W row-major [fan_in][fan_out])
+ *   from / to DEVICE memory and reset the optimiser; set_norm takes HOST
+ *   arrays mu_x, sd_x [n_in] and mu_y, sd_y [n_out].
+ *   forward: X [batch][n_in] -> out [batch][n_out], normalised, device.
+ *   grad: MSE loss and its gradient (grad device [nparams] or NULL for the
+ *   internal buffer; loss device float or NULL). adam: one Adam step
+ *   (Kingma & Ba 2015) with the given or the internal gradient.
+ *   train_step = grad + adam on the internal gradient.
+ *   dlbchem_attach_mlp: the network ctx uses when options.predictor or
+ *   options.surrogate is on (NULL detaches). The network must outlive its use.
+ * Return DLBCHEM_OK, BAD_ARG, CUDA or OOM (message: dlbchem_mlp_last_error).
+ */
+typedef struct dlbchem_mlp dlbchem_mlp;
+int dlbchem_mlp_create(int n_in, int n_hidden, int n_out, dlbchem_mlp** out);
+int64_t dlbchem_mlp_nparams(const dlbchem_mlp* m);
+int dlbchem_mlp_set_params(dlbchem_mlp* m, const float* params, void* cuda_stream);
+int dlbchem_mlp_get_params(dlbchem_mlp* m, float* params, void* cuda_stream);
+int dlbchem_mlp_set_norm(dlbchem_mlp* m, const float* mu_x, const float* sd_x, const float* mu_y, const float* sd_y);
+int dlbchem_mlp_forward(dlbchem_mlp* m, int64_t batch, const float* X, float* out, void* cuda_stream);
+int dlbchem_mlp_grad(dlbchem_mlp* m, int64_t batch, const float* X, const float* Y, float* grad, float* loss,
+                     void* cuda_stream);
+int dlbchem_mlp_adam(dlbchem_mlp* m, const float* grad, float lr, void* cuda_stream);
+int dlbchem_mlp_train_step(dlbchem_mlp* m, int64_t batch, const float* X, const float* Y, float lr, float* loss,
+                           void* cuda_stream);
+const char* dlbchem_mlp_last_error(const dlbchem_mlp* m);
+void dlbchem_mlp_destroy(dlbchem_mlp* m);
+int dlbchem_attach_mlp(dlbchem_ctx* ctx, dlbchem_mlp* m);
 
 /* Number of species / reactions of the loaded mechanism (-1 if ctx NULL). */
 int dlbchem_nspecies(const dlbchem_ctx* ctx);

@@ -65,7 +65,9 @@ bool parse_mech(const char* path, dlb::HostMech& m, std::string& err) {
     v->resize(m.nsp);
     for (auto& x : *v) x = rd.get<double>();
   }
-  for (int i = 0; i < m.nsp * nelem; ++i) (void)rd.get<int32_t>();
+  m.nelem = nelem;
+  m.atoms.resize(size_t(m.nsp) * nelem);
+  for (auto& a : m.atoms) a = rd.get<int32_t>();
   m.rx.resize(m.nrx);
   for (auto& r : m.rx) {
     r.lnA = rd.get<double>(); r.beta = rd.get<double>(); r.Ea = rd.get<double>();
@@ -159,6 +161,7 @@ bool valid_opts(const dlbchem_options* o, std::string& why) {
   if (!(o->map_Ttol >= 0) || !(o->map_Ytol >= 0) || !(o->map_Tmax >= 0)) { why = "mapping tolerances must be >= 0"; return false; }
   if (o->team_warps != 0 && o->team_warps != 1 && o->team_warps != 2 && o->team_warps != 4) { why = "team_warps must be 0, 1, 2 or 4"; return false; }
   if (o->precision != 0 && o->precision != 1) { why = "precision must be 0 or 1"; return false; }
+  if (!(o->gate >= 0)) { why = "gate must be >= 0"; return false; }
   return true;
 }
 
@@ -270,9 +273,14 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   offs.push_back(put(inc.data(), inc.size() * 4));
   offs.push_back(put(tri.data(), tri.size() * 4));
   offs.push_back(put(tric.data(), tric.size() * 8));
+  // a_ek / W_k for the element check of the surrogate gate (4 elements)
+  std::vector<double> aW(size_t(4) * nsp, 0.0);
+  for (int e = 0; e < std::min(4, hm.nelem); ++e)
+    for (int k = 0; k < nsp; ++k) aW[size_t(e) * nsp + k] = hm.atoms[size_t(k) * hm.nelem + e] / hm.W[k];
   std::vector<double> exptab(64);
   for (int j = 0; j < 64; ++j) exptab[j] = double(exp2l((long double)j / 64.0L));
   offs.push_back(put(exptab.data(), exptab.size() * 8));
+  offs.push_back(put(aW.data(), aW.size() * 8));
   // store offsets as fake pointers; relocated after upload
   auto P = [&](int i) { return reinterpret_cast<const double*>(offs[i]); };
   dm.W = P(0); dm.iW = P(1); dm.H0 = P(2); dm.cpa = P(3); dm.hcpb = P(4); dm.cpb = P(5);
@@ -285,6 +293,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   dm.tri = reinterpret_cast<const uint32_t*>(offs[18]);
   dm.tri_coef = P(19);
   dm.exptab = P(20);
+  dm.aW = P(21);
   return true;
 }
 
@@ -302,6 +311,7 @@ void relocate(DevMech& dm, void* base) {
   dm.eff_dm1 = reloc(dm.eff_dm1, base); dm.inc = reloc(dm.inc, base); dm.tri = reloc(dm.tri, base);
   dm.tri_coef = reloc(dm.tri_coef, base);
   dm.exptab = reloc(dm.exptab, base);
+  dm.aW = reloc(dm.aW, base);
 }
 
 int configure_launch(dlbchem_ctx* c) {
@@ -317,6 +327,8 @@ int configure_launch(dlbchem_ctx* c) {
   c->teams = teams;
   c->smem_bytes = int(team_bytes * teams) + 64 * 8;   // + the CTA's exp table
   e = cudaFuncSetAttribute(dlb::rosenbrock_kernel_ptr(c->wpc), cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dlb::gate_kernel_ptr(c->wpc), cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaFuncSetAttribute");
   int bps = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, dlb::rosenbrock_kernel_ptr(c->wpc), 32 * c->wpc * teams, c->smem_bytes);
@@ -327,6 +339,36 @@ int configure_launch(dlbchem_ctx* c) {
 }
 
 int64_t tiles256(int64_t n) { return (n + 255) / 256; }
+
+// Workspace of the learned parts: features, network outputs, predictions.
+int ensure_learn(dlbchem_ctx* c, int64_t n) {
+  if (n <= c->learn_cap) return DLBCHEM_OK;
+  if (c->d_learn) cudaFree(c->d_learn);
+  c->d_learn = nullptr;
+  c->learn_cap = 0;
+  int nin = 0, nout = 0;
+  dlb::mlp_shape(c->mlp, &nin, &nout);
+  if (nin != c->hm.nsp + 3 || nout != c->hm.nsp + 2)
+    return fail(c, DLBCHEM_BAD_ARG, "network shape does not match the mechanism (n_in = nsp+3, n_out = nsp+2)");
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t o = 0;
+  const size_t oX = o; o += al(size_t(n) * nin * 4);
+  const size_t oO = o; o += al(size_t(n) * nout * 4);
+  const size_t oL = o; o += al(size_t(n) * 4);
+  const size_t oT = o; o += al(size_t(n) * 8);
+  const size_t oY = o; o += al(size_t(n) * c->hm.nsp * 8);
+  const size_t oK = o; o += al(size_t(n) * 4);
+  if (cudaMalloc(&c->d_learn, o) != cudaSuccess) { c->d_learn = nullptr; return fail(c, DLBCHEM_OOM, "network workspace allocation failed"); }
+  char* b = static_cast<char*>(c->d_learn);
+  c->l_X = reinterpret_cast<float*>(b + oX);
+  c->l_out = reinterpret_cast<float*>(b + oO);
+  c->l_lnsteps = reinterpret_cast<float*>(b + oL);
+  c->l_dT = reinterpret_cast<double*>(b + oT);
+  c->l_dY = reinterpret_cast<double*>(b + oY);
+  c->l_keys = reinterpret_cast<int32_t*>(b + oK);
+  c->learn_cap = n;
+  return DLBCHEM_OK;
+}
 
 int ensure_ws(dlbchem_ctx* c, int64_t n) {
   if (n <= c->ws_cap) return DLBCHEM_OK;
@@ -372,6 +414,7 @@ int dlbchem_options_default(dlbchem_options* o) {
   o->rtol = 1e-6; o->atol = 1e-10; o->max_steps = 100000; o->isothermal = 0; o->hmin_frac = 1e-20;
   o->schedule = DLBCHEM_SCHED_PLAIN; o->chunk = 1; o->mapping = 0; o->timing = 0;
   o->map_Ttol = 1e-4; o->map_Ytol = 1e-4; o->map_Tmax = 0.0; o->team_warps = 0; o->precision = 0;
+  o->predictor = 0; o->surrogate = 0; o->gate = 1e-4;
   return DLBCHEM_OK;
 }
 
@@ -439,22 +482,49 @@ int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, con
   const bool timing = c->opt.timing != 0;
   const bool mapping = c->opt.mapping != 0;
   const bool queue = c->opt.schedule == DLBCHEM_SCHED_QUEUE;
+  const bool learned = c->mlp && (c->opt.predictor || c->opt.surrogate);
+  const bool predictor = learned && c->opt.predictor;
+  const bool surrogate = learned && c->opt.surrogate;
+  if ((c->opt.predictor || c->opt.surrogate) && !c->mlp)
+    return fail(c, DLBCHEM_BAD_ARG, "predictor / surrogate need a network (dlbchem_attach_mlp)");
+  if (learned && (rc = ensure_learn(c, n)) != DLBCHEM_OK) return rc;
   cudaError_t e = cudaSuccess;
   auto rec = [&](int i) { if (timing && e == cudaSuccess) e = cudaEventRecord(c->ev[i], s); };
   unsigned long long* d_ref = c->d_counter + 1;
-  // stage 1: mapping classification and the work list (paper Sec. 2.3 filter)
+  // stage 1: mapping classification (paper Sec. 2.3 filter), network
+  // predictions and the surrogate gate, then the work list of the cells left
   rec(2);
+  if (learned && e == cudaSuccess)
+    e = dlb::mlp_predict(c->mlp, n, c->hm.nsp, T, p, Y, dt, c->l_X, c->l_out, c->l_lnsteps, c->l_dT, c->l_dY, s);
+  if (predictor && e == cudaSuccess) e = dlb::launch_lnsteps_keys(n, c->l_lnsteps, c->l_keys, s);
+  const int32_t* keys_in = predictor ? c->l_keys : steps;
   if (mapping) {
     if (e == cudaSuccess)
       e = dlb::launch_map_classify(n, c->hm.nsp, T, Y, Yref, c->opt.map_Ttol, c->opt.map_Ytol, c->opt.map_Tmax,
                                    c->w_flag, d_ref, c->w_ref_state, c->w_bcount, c->w_boff, c->w_total, s);
-    if (e == cudaSuccess) e = dlb::launch_compact(n, c->w_flag, c->w_boff, steps, c->w_list, c->w_keys, s);
-  } else if (queue) {
-    if (e == cudaSuccess) e = dlb::launch_init_list(n, steps, c->w_list, c->w_keys, c->w_total, s);
+  } else if (surrogate && e == cudaSuccess) {
+    e = cudaMemsetAsync(c->w_flag, 0, size_t(n), s);
+  }
+  if (surrogate && e == cudaSuccess) {
+    dlb::GateArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.m = c->dm;
+    g.P.rtol = c->opt.rtol; g.P.atol = c->opt.atol; g.P.dt = dt; g.P.isothermal = c->opt.isothermal;
+    g.L = c->L;
+    g.n = n; g.T = T; g.p = p; g.Y = Y; g.dT = c->l_dT; g.dY = c->l_dY; g.Tout = T_out; g.Yout = Y_out;
+    g.steps = steps; g.status = status; g.flag = c->w_flag; g.gate = c->opt.gate;
+    int64_t ggrid = std::min<int64_t>((n + c->teams - 1) / c->teams, int64_t(c->num_sms) * c->blocks_per_sm);
+    e = dlb::launch_gate(c->wpc, unsigned(ggrid), 32 * c->wpc * c->teams, c->smem_bytes, s, g);
+    if (e == cudaSuccess) e = dlb::launch_count_scan(n, c->w_flag, c->w_bcount, c->w_boff, c->w_total, s);
+  }
+  if (mapping || surrogate) {
+    if (e == cudaSuccess) e = dlb::launch_compact(n, c->w_flag, c->w_boff, keys_in, c->w_list, c->w_keys, s);
+  } else if (queue || predictor) {
+    if (e == cudaSuccess) e = dlb::launch_init_list(n, keys_in, c->w_list, c->w_keys, c->w_total, s);
   }
   rec(3);
-  // stage 2: longest-first order of the work list by the previous call's cost
-  if (queue && steps && e == cudaSuccess)
+  // stage 2: longest-first order of the work list by the cost keys
+  if (queue && keys_in && e == cudaSuccess)
     e = dlb::launch_sort(n, c->w_total, c->w_keys, c->w_list, c->w_keys_alt, c->w_list_alt, c->w_hist, s);
   rec(4);
   if (e != cudaSuccess) return cuda_fail(c, e, "scheduling kernels");
@@ -469,7 +539,7 @@ int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, con
   a.fallbacks = c->d_counter + 2;
   if (c->opt.precision == 1 && (e = cudaMemsetAsync(c->d_counter + 2, 0, 8, s)) != cudaSuccess)
     return cuda_fail(c, e, "cudaMemsetAsync");
-  const bool listed = mapping || queue;
+  const bool listed = mapping || queue || surrogate || predictor;
   a.perm = listed ? c->w_list : nullptr;
   a.nqueue = listed ? c->w_total : nullptr;
   const int threads = 32 * c->wpc * c->teams;
@@ -492,13 +562,15 @@ int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, con
   if (e != cudaSuccess) return cuda_fail(c, e, "mapping scatter");
   c->timed_last = timing;
   c->last_n = n;
-  c->last_mapping = mapping;
+  c->last_mapping = mapping || surrogate;
   c->last_listed = listed;
   c->stats[0] = n; c->stats[1] = 0; c->stats[2] = -1; c->stats[3] = 32 * c->wpc; c->stats[4] = c->teams;
   // kernels launched by this call: classify (init, classify, flag, scan, compact) or the list init,
   // four sort passes of three kernels, the integrator, the scatter
   c->stats[5] = grid; c->stats[6] = c->smem_bytes;
-  c->stats[7] = (mapping ? 5 : (queue ? 1 : 0)) + ((queue && steps) ? 12 : 0) + 1 + (mapping ? 1 : 0);
+  c->stats[7] = (learned ? 9 : 0) + (predictor ? 1 : 0) + (mapping ? 4 : 0) + (surrogate ? 3 : 0) +
+                ((mapping || surrogate) ? 1 : ((queue || predictor) ? 1 : 0)) + ((queue && keys_in) ? 12 : 0) + 1 +
+                (mapping ? 1 : 0);
   return DLBCHEM_OK;
 }
 
@@ -548,6 +620,20 @@ int dlbchem_integrate_host(dlbchem_ctx* c, int64_t n, double dt, const double* T
   if (status && (e = cudaMemcpyAsync(status, dstat, size_t(n) * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return cuda_fail(c, e, "device to host copy");
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  return DLBCHEM_OK;
+}
+
+int dlbchem_attach_mlp(dlbchem_ctx* c, dlbchem_mlp* m) {
+  if (!c) return DLBCHEM_BAD_ARG;
+  if (m) {
+    int nin = 0, nout = 0;
+    dlb::mlp_shape(m, &nin, &nout);
+    if (nin != c->hm.nsp + 3 || nout != c->hm.nsp + 2)
+      return fail(c, DLBCHEM_BAD_ARG, "network shape does not match the mechanism (n_in = nsp+3, n_out = nsp+2)");
+  }
+  c->mlp = m;
+  c->learn_cap = 0;
+  if (c->d_learn) { cudaStreamSynchronize(c->last_stream); cudaFree(c->d_learn); c->d_learn = nullptr; }
   return DLBCHEM_OK;
 }
 
@@ -620,6 +706,7 @@ void dlbchem_destroy(dlbchem_ctx* c) {
   if (c->d_blob) cudaFree(c->d_blob);
   if (c->d_counter) cudaFree(c->d_counter);
   if (c->d_ws) cudaFree(c->d_ws);
+  if (c->d_learn) cudaFree(c->d_learn);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   if (c->d_stage) cudaFree(c->d_stage);

@@ -24,7 +24,8 @@ constexpr double kM1 = 2.255570073418735, kM2 = 0.2870493262186792, kM3 = 0.4353
 constexpr double kE1 = -0.2815431932141155, kE2 = -0.07276199124938920, kE3 = -0.1082196201495311,
                  kE4 = -1.093502252409163;
 
-enum : int { CELL_OK = 0, CELL_MAPPED = 1, CELL_MAX_STEPS = -1, CELL_H_UNDERFLOW = -2, CELL_NONFINITE = -3 };
+enum : int { CELL_OK = 0, CELL_MAPPED = 1, CELL_SURROGATE = 2, CELL_MAX_STEPS = -1, CELL_H_UNDERFLOW = -2,
+             CELL_NONFINITE = -3 };
 
 // Per reaction, 32 bytes. Species slots are expanded by multiplicity
 // (2A -> slots A, A); sp[0..2] reactants, sp[3..5] products, -1 unused.
@@ -68,6 +69,7 @@ struct DevMech {
   const double* tri_coef;
   int tri_ptr[5];
   const double* exptab;   // 2^(j/64), j = 0..63 (staged into shared memory per CTA)
+  const double* aW;       // [4][nsp] atoms of element e per gram of species k (a_ek / W_k)
 };
 
 struct IntegParams {
@@ -164,7 +166,29 @@ struct KernelArgs {
   MeshDesc mesh[kMaxMesh];
 };
 
+// Arguments of the surrogate gate kernel.
+struct GateArgs {
+  DevMech m;
+  IntegParams P;
+  WsLayout L;
+  int64_t n;
+  const double *T, *p, *Y;          // inputs
+  const double *dT, *dY;            // predicted increments (dY species-major)
+  double *Tout, *Yout;
+  int32_t *steps, *status;
+  uint8_t* flag;                    // 0: to integrate; 1: mapped (skipped); set to 2 when accepted
+  double gate;
+};
+
 // Host-side launchers defined next to the kernels (integrator*.cu).
+cudaError_t launch_gate_w1(unsigned grid, int threads, int smem, cudaStream_t s, const GateArgs& a);
+cudaError_t launch_gate_w2(unsigned grid, int threads, int smem, cudaStream_t s, const GateArgs& a);
+cudaError_t launch_gate_w4(unsigned grid, int threads, int smem, cudaStream_t s, const GateArgs& a);
+cudaError_t launch_gate(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const GateArgs& a);
+const void* gate_kernel_ptr_w1();
+const void* gate_kernel_ptr_w2();
+const void* gate_kernel_ptr_w4();
+const void* gate_kernel_ptr(int wpc);
 cudaError_t launch_rosenbrock_w1(unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
 cudaError_t launch_rosenbrock_w2(unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
 cudaError_t launch_rosenbrock_w4(unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
@@ -186,6 +210,15 @@ cudaError_t launch_sort(int64_t n, const int64_t* mdev, uint32_t* keys, int32_t*
                         int32_t* list_alt, int32_t* hist, cudaStream_t s);
 cudaError_t launch_batch_list(int nmesh, const MeshDesc* mesh, const int64_t* offsets, int64_t total_n,
                               int32_t* list, uint32_t* keys, int64_t* total, cudaStream_t s);
+}  // namespace dlb
+struct dlbchem_mlp;
+namespace dlb {
+cudaError_t mlp_predict(dlbchem_mlp* m, int64_t n, int nsp, const double* T, const double* p, const double* Y,
+                        double dt, float* X, float* out, float* lnsteps, double* dT, double* dY, cudaStream_t s);
+int mlp_shape(const dlbchem_mlp* m, int* n_in, int* n_out);
+cudaError_t launch_count_scan(int64_t n, const uint8_t* flag, int32_t* block_count, int32_t* block_off,
+                              int64_t* total, cudaStream_t s);
+cudaError_t launch_lnsteps_keys(int64_t n, const float* lnsteps, int32_t* keys, cudaStream_t s);
 cudaError_t launch_map_scatter(int64_t n, int nsp, const uint8_t* mapped, const unsigned long long* ref,
                                const double* ref_state, const double* T, const double* Y, double* Tout,
                                double* Yout, int32_t* steps, int32_t* status, cudaStream_t s);

@@ -22,12 +22,15 @@ struct HostRxn {
 };
 
 struct HostMech {
-  int nsp = 0, nrx = 0;
+  int nsp = 0, nrx = 0, nelem = 0;
   std::vector<double> W, a, b, hf, s0;
+  std::vector<int> atoms;      // [nsp][nelem]
   std::vector<HostRxn> rx;
 };
 
 }  // namespace dlb
+
+struct dlbchem_mlp;
 
 struct dlbchem_ctx {
   int device = 0;
@@ -57,5 +60,12 @@ struct dlbchem_ctx {
   int64_t stage_cap = 0;
   cudaStream_t last_stream = nullptr;
   int64_t stats[10] = {0, 0, -1, 0, 0, 0, 0, 0, 0, 0};
+  // learned predictor / surrogate
+  dlbchem_mlp* mlp = nullptr;
+  void* d_learn = nullptr;
+  int64_t learn_cap = 0;
+  float *l_X = nullptr, *l_out = nullptr, *l_lnsteps = nullptr;
+  double *l_dT = nullptr, *l_dY = nullptr;
+  int32_t* l_keys = nullptr;
   std::string err;
 };

@@ -33,6 +33,16 @@ cudaError_t launch_rosenbrock(int wpc, unsigned grid, int threads, int smem, cud
   return launch_rosenbrock_w4(grid, threads, smem, s, a);
 }
 
+cudaError_t launch_gate(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const GateArgs& a) {
+  if (wpc == 1) return launch_gate_w1(grid, threads, smem, s, a);
+  if (wpc == 2) return launch_gate_w2(grid, threads, smem, s, a);
+  return launch_gate_w4(grid, threads, smem, s, a);
+}
+
+const void* gate_kernel_ptr(int wpc) {
+  return wpc == 1 ? gate_kernel_ptr_w1() : (wpc == 2 ? gate_kernel_ptr_w2() : gate_kernel_ptr_w4());
+}
+
 const void* rosenbrock_kernel_ptr(int wpc) {
   return wpc == 1 ? rosenbrock_kernel_ptr_w1() : (wpc == 2 ? rosenbrock_kernel_ptr_w2() : rosenbrock_kernel_ptr_w4());
 }

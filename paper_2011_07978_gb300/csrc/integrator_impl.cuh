@@ -53,6 +53,20 @@ struct Team {
     for (int w = 1; w < WPC; ++w) s += buf[w];
     return s;
   }
+  // Max over the team; every thread receives the same value.
+  __device__ __forceinline__ double maxv(double x) const {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (WPC == 1) return x;
+    double* buf = red + parity * WPC;
+    parity ^= 1;
+    if (lane == 0) buf[warp] = x;
+    sync();
+    double s = buf[0];
+#pragma unroll
+    for (int w = 1; w < WPC; ++w) s = fmax(s, buf[w]);
+    return s;
+  }
   __device__ __forceinline__ int any(int x) const {
     x = __any_sync(0xffffffffu, x);
     if (WPC == 1) return x;
@@ -763,6 +777,95 @@ __global__ void __launch_bounds__(128, WPC == 4 ? 4 : 1) rosenbrock_kernel(const
     if (first >= nq) break;
     const int64_t last = min(first + int64_t(a.chunk), nq);
     for (int64_t qi = first; qi < last; ++qi) run(int64_t(a.perm[qi]));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Surrogate gate: a predicted increment (T', Y') = (T, Y) + (dT, dY) is
+// accepted only if it is consistent with the chemistry over the step to the
+// gate tolerance g: the trapezoid defect y' - y - dt/2 (f(y) + f(y')) is at
+// most g in every mass fraction and g*T in temperature, |sum Y' - 1| <= g, and
+// every element total changes by at most g relative. Accepted cells get
+// (T', Y'), status SURROGATE and steps 0; the others stay on the work list and
+// are integrated (the plain integrator is the fallback and the judge).
+// ---------------------------------------------------------------------------
+template <int WPC>
+__global__ void __launch_bounds__(128) gate_kernel(const GateArgs a) {
+  extern __shared__ __align__(16) double smem[];
+  constexpr int TS = 32 * WPC;
+  const int teams = blockDim.x / TS;
+  const int team = threadIdx.x / TS;
+  Team<WPC> tm;
+  tm.tid = threadIdx.x % TS;
+  tm.warp = tm.tid >> 5;
+  tm.lane = threadIdx.x & 31;
+  tm.bar_id = 1 + team;
+  tm.parity = 0;
+  double* tab = smem + size_t(teams) * a.L.total;
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) tab[j] = a.m.exptab[j];
+  __syncthreads();
+  WS w = carve(smem + size_t(team) * a.L.total, a.L);
+  w.exptab = tab;
+  tm.red = w.scal;
+  const DevMech& m = a.m;
+  const int N = m.N, nsp = m.nsp;
+  const int64_t n = a.n;
+  for (int64_t cell = int64_t(blockIdx.x) * teams + team; cell < n; cell += int64_t(gridDim.x) * teams) {
+    if (a.flag[cell] != 0) continue;                 // team-uniform: one flag per cell
+    const double p = a.p[cell];
+    for (int i = tm.tid; i < N; i += TS) {
+      const double y = i == 0 ? a.T[cell] : a.Y[int64_t(i - 1) * n + cell];
+      const double d = i == 0 ? a.dT[cell] : a.dY[int64_t(i - 1) * n + cell];
+      w.y0[i] = y;
+      w.ys[i] = y + d;
+    }
+    tm.sync();
+    int bad = 0;
+    for (int i = tm.tid; i < N; i += TS) bad |= !isfinite(w.y0[i]) || !isfinite(w.ys[i]);
+    bad |= !(w.y0[0] > 0.0) || !(w.ys[0] > 0.0) || !(p > 0.0);
+    if (tm.any(bad)) continue;
+    const double P1 = 1e-6 * p / kR;
+    eval_f<WPC>(m, tm, w, w.y0, P1, a.P.isothermal != 0, w.f0);
+    eval_f<WPC>(m, tm, w, w.ys, P1, a.P.isothermal != 0, w.fs);
+    const double hdt = 0.5 * a.P.dt;
+    double dY = 0.0, sumY = 0.0, e0 = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0, t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    for (int i = tm.tid; i < N; i += TS) {
+      const double def = fabs(w.ys[i] - w.y0[i] - hdt * (w.f0[i] + w.fs[i]));
+      if (i > 0) {
+        dY = fmax(dY, def);
+        const int k = i - 1;
+        const double yk = w.ys[i], dk = w.ys[i] - w.y0[i];
+        sumY += yk;
+        e0 = fma(m.aW[k], dk, e0);           t0 = fma(m.aW[k], w.y0[i], t0);
+        e1 = fma(m.aW[nsp + k], dk, e1);     t1 = fma(m.aW[nsp + k], w.y0[i], t1);
+        e2 = fma(m.aW[2 * nsp + k], dk, e2); t2 = fma(m.aW[2 * nsp + k], w.y0[i], t2);
+        e3 = fma(m.aW[3 * nsp + k], dk, e3); t3 = fma(m.aW[3 * nsp + k], w.y0[i], t3);
+      } else {
+        dY = fmax(dY, def / w.y0[0]);        // temperature: relative defect
+      }
+    }
+    const double worst = tm.maxv(dY);
+    const double S = tm.sum(sumY);
+    const double E0 = tm.sum(e0), E1 = tm.sum(e1), E2 = tm.sum(e2), E3 = tm.sum(e3);
+    const double R0 = tm.sum(t0), R1 = tm.sum(t1), R2 = tm.sum(t2), R3 = tm.sum(t3);
+    double ed = 0.0;
+    if (R0 > 0) ed = fmax(ed, fabs(E0) / R0);
+    if (R1 > 0) ed = fmax(ed, fabs(E1) / R1);
+    if (R2 > 0) ed = fmax(ed, fabs(E2) / R2);
+    if (R3 > 0) ed = fmax(ed, fabs(E3) / R3);
+    const bool accept = worst <= a.gate && fabs(S - 1.0) <= a.gate && ed <= a.gate;
+    if (accept) {
+      for (int i = tm.tid; i < N; i += TS) {
+        if (i == 0) a.Tout[cell] = w.ys[0];
+        else a.Yout[int64_t(i - 1) * n + cell] = w.ys[i];
+      }
+      if (tm.tid == 0) {
+        a.flag[cell] = 2;
+        if (a.steps) a.steps[cell] = 0;
+        if (a.status) a.status[cell] = CELL_SURROGATE;
+      }
+    }
+    tm.sync();
   }
 }
 

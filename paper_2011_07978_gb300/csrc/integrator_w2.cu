@@ -10,4 +10,11 @@ cudaError_t launch_rosenbrock_w2(unsigned grid, int threads, int smem, cudaStrea
 
 const void* rosenbrock_kernel_ptr_w2() { return reinterpret_cast<const void*>(&rosenbrock_kernel<2>); }
 
+const void* gate_kernel_ptr_w2() { return reinterpret_cast<const void*>(&gate_kernel<2>); }
+
+cudaError_t launch_gate_w2(unsigned grid, int threads, int smem, cudaStream_t s, const GateArgs& a) {
+  gate_kernel<2><<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace dlb

@@ -1,0 +1,467 @@
+// The learned cost predictor / surrogate network: a multilayer perceptron
+// n_in -> 256 -> 256 -> 256 -> n_out with SiLU, trained and run on the GPU by
+// the kernels below. Every contraction runs on the tensor cores in BF16 with
+// FP32 accumulation (mma.sync m16n8k16; FP32 master weights and activations
+// are rounded to BF16 when a tile is staged in shared memory); bias, SiLU,
+// the MSE gradient, bias gradients and Adam are FP32 element kernels.
+//
+// Inputs of the network for one cell: x = [T/1000, ln p, Y_1..Y_nsp, ln dt];
+// outputs: [ln(attempted steps), dT, dY_1..dY_nsp]. Both are normalised by
+// stored means and standard deviations.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dlbchem.h"
+#include "dlb_common.cuh"
+#include "dlb_ctx.h"
+
+namespace dlb {
+
+constexpr int kBM = 64, kBN = 64, kBK = 32;
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float dsilu_f(float z) {
+  const float s = 1.0f / (1.0f + __expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+
+__device__ __forceinline__ uint32_t pack2(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// C[M x N] = op(A)[M x K] op(B)[K x N] (+ bias[n]); optional pre-activation
+// copy Z and SiLU. A: TA ? A[k*lda + m] : A[m*lda + k]; B: TB ? B[n*ldb + k]
+// : B[k*ldb + n]. 64x64 block tile, 4 warps of 32x32, k-tile 32.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                        const float* __restrict__ B, int ldb, float* __restrict__ C,
+                                                        int ldc, const float* __restrict__ bias, float* __restrict__ Z,
+                                                        int act) {
+  __shared__ __align__(16) __nv_bfloat16 sA[kBM][kBK + 8];   // (m, k)
+  __shared__ __align__(16) __nv_bfloat16 sB[kBN][kBK + 8];   // (n, k)
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int g = lane >> 2, t = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+  for (int k0 = 0; k0 < K; k0 += kBK) {
+    for (int e = threadIdx.x; e < kBM * kBK; e += 128) {
+      int mm, kk;
+      if (TA) { kk = e / kBM; mm = e % kBM; } else { mm = e / kBK; kk = e % kBK; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      float v = 0.0f;
+      if (gm < M && gk < K) v = TA ? A[int64_t(gk) * lda + gm] : A[int64_t(gm) * lda + gk];
+      sA[mm][kk] = __float2bfloat16_rn(v);
+    }
+    for (int e = threadIdx.x; e < kBN * kBK; e += 128) {
+      int nn, kk;
+      if (TB) { nn = e / kBK; kk = e % kBK; } else { kk = e / kBN; nn = e % kBN; }
+      const int gn = n0 + nn, gk = k0 + kk;
+      float v = 0.0f;
+      if (gn < N && gk < K) v = TB ? B[int64_t(gn) * ldb + gk] : B[int64_t(gk) * ldb + gn];
+      sB[nn][kk] = __float2bfloat16_rn(v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; kk += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + 16 * i + g;
+        a[i][0] = pack2(&sA[r][kk + 2 * t]);
+        a[i][1] = pack2(&sA[r + 8][kk + 2 * t]);
+        a[i][2] = pack2(&sA[r][kk + 2 * t + 8]);
+        a[i][3] = pack2(&sA[r + 8][kk + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn + 8 * j + g;
+        b[j][0] = pack2(&sB[c][kk + 2 * t]);
+        b[j][1] = pack2(&sB[c][kk + 2 * t + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};"
+              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int gm = m0 + wm + 16 * i + g + (r >= 2 ? 8 : 0);
+        const int gn = n0 + wn + 8 * j + 2 * t + (r & 1);
+        if (gm < M && gn < N) {
+          float v = acc[i][j][r] + (bias ? bias[gn] : 0.0f);
+          if (Z) Z[int64_t(gm) * ldc + gn] = v;
+          if (act) v = silu_f(v);
+          C[int64_t(gm) * ldc + gn] = v;
+        }
+      }
+}
+
+// dZ = dH * silu'(Z), in place on dH.
+__global__ void silu_back_kernel(int64_t n, float* __restrict__ dH, const float* __restrict__ Z) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    dH[i] *= dsilu_f(Z[i]);
+}
+
+// MSE: dOut = 2 (out - y) / (B n_out); loss += sum (out - y)^2 / (B n_out).
+__global__ void mse_kernel(int64_t n, float scale, const float* __restrict__ out, const float* __restrict__ y,
+                           float* __restrict__ dout, float* __restrict__ loss) {
+  float s = 0.0f;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const float d = out[i] - y[i];
+    dout[i] = 2.0f * d * scale;
+    s += d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, s * scale);
+}
+
+// db[n] = sum_m dZ[m][n].
+__global__ void bias_grad_kernel(int M, int N, const float* __restrict__ dZ, float* __restrict__ db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.0f;
+  for (int m = 0; m < M; ++m) s += dZ[int64_t(m) * N + n];
+  db[n] = s;
+}
+
+// Adam (Kingma & Ba 2015, Algorithm 1), bias-corrected, FP32.
+__global__ void adam_kernel(int64_t n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// Normalised network input of cell i from the species-major FP64 state.
+__global__ void features_kernel(int64_t n, int nsp, const double* __restrict__ T, const double* __restrict__ p,
+                                const double* __restrict__ Y, double dt, const float* __restrict__ mu,
+                                const float* __restrict__ isd, float* __restrict__ X) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const int nin = nsp + 3;
+  float* x = X + i * nin;
+  x[0] = (float(T[i] * 1e-3) - mu[0]) * isd[0];
+  x[1] = (float(log(p[i])) - mu[1]) * isd[1];
+  for (int k = 0; k < nsp; ++k) x[2 + k] = (float(Y[int64_t(k) * n + i]) - mu[2 + k]) * isd[2 + k];
+  x[nin - 1] = (float(log(dt)) - mu[nin - 1]) * isd[nin - 1];
+}
+
+// Physical predictions from the normalised network output: ln steps, dT,
+// dY (species-major, FP64).
+__global__ void predictions_kernel(int64_t n, int nsp, const float* __restrict__ out, const float* __restrict__ mu,
+                                   const float* __restrict__ sd, float* __restrict__ lnsteps,
+                                   double* __restrict__ dT, double* __restrict__ dY) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const int nout = nsp + 2;
+  const float* o = out + i * nout;
+  lnsteps[i] = o[0] * sd[0] + mu[0];
+  dT[i] = double(o[1] * sd[1] + mu[1]);
+  for (int k = 0; k < nsp; ++k) dY[int64_t(k) * n + i] = double(o[2 + k] * sd[2 + k] + mu[2 + k]);
+}
+
+}  // namespace dlb
+
+struct dlbchem_mlp {
+  int n_in = 0, n_hidden = 256, n_out = 0, n_layers = 3;
+  int64_t nparams = 0;
+  float* d_params = nullptr;   // [W1 b1 W2 b2 W3 b3 W4 b4], W row-major [fan_in, fan_out]
+  float* d_m = nullptr;
+  float* d_v = nullptr;
+  float* d_grad = nullptr;
+  float* d_norm = nullptr;     // mu_x, isd_x, mu_y, sd_y
+  int adam_t = 0;
+  // activations for the largest batch seen
+  int64_t cap = 0;
+  float* d_act = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int mfail(dlbchem_mlp* m, int code, const std::string& msg) {
+  if (m) m->err = msg;
+  return code;
+}
+
+struct LayerOff {
+  int64_t w, b;
+  int fi, fo;
+};
+
+std::vector<LayerOff> layers_of(const dlbchem_mlp* m) {
+  std::vector<int> dims = {m->n_in};
+  for (int i = 0; i < m->n_layers; ++i) dims.push_back(m->n_hidden);
+  dims.push_back(m->n_out);
+  std::vector<LayerOff> L;
+  int64_t o = 0;
+  for (size_t i = 0; i + 1 < dims.size(); ++i) {
+    LayerOff l;
+    l.fi = dims[i];
+    l.fo = dims[i + 1];
+    l.w = o;
+    o += int64_t(l.fi) * l.fo;
+    l.b = o;
+    o += l.fo;
+    L.push_back(l);
+  }
+  return L;
+}
+
+cudaError_t gemm(bool ta, bool tb, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
+                 int ldc, const float* bias, float* Z, int act, cudaStream_t s) {
+  dim3 grid((N + dlb::kBN - 1) / dlb::kBN, (M + dlb::kBM - 1) / dlb::kBM);
+  if (!ta && !tb) dlb::gemm_bf16_kernel<false, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, act);
+  else if (ta && !tb) dlb::gemm_bf16_kernel<true, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, act);
+  else if (!ta && tb) dlb::gemm_bf16_kernel<false, true><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, act);
+  else dlb::gemm_bf16_kernel<true, true><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, act);
+  return cudaGetLastError();
+}
+
+// activation workspace: per hidden layer Z and H [cap x n_hidden], output
+// [cap x n_out], two gradient buffers [cap x max(n_hidden, n_out)].
+int ensure_act(dlbchem_mlp* m, int64_t batch) {
+  if (batch <= m->cap) return DLBCHEM_OK;
+  if (m->d_act) cudaFree(m->d_act);
+  m->d_act = nullptr;
+  m->cap = 0;
+  const int64_t wmax = std::max(m->n_hidden, m->n_out);
+  const int64_t per = 2 * int64_t(m->n_layers) * m->n_hidden + m->n_out + 2 * wmax;
+  if (cudaMalloc(&m->d_act, size_t(batch) * per * 4) != cudaSuccess) {
+    m->d_act = nullptr;
+    return mfail(m, DLBCHEM_OOM, "network activation allocation failed");
+  }
+  m->cap = batch;
+  return DLBCHEM_OK;
+}
+
+// Forward; with keep the pre-activations are stored for the backward pass.
+cudaError_t forward(dlbchem_mlp* m, int64_t B, const float* X, float* out, bool keep, cudaStream_t s) {
+  const auto L = layers_of(m);
+  const int64_t H = m->n_hidden;
+  float* Zs = m->d_act;                                  // n_layers x [B x H]
+  float* Hs = Zs + int64_t(m->n_layers) * B * H;         // n_layers x [B x H]
+  const float* in = X;
+  cudaError_t e = cudaSuccess;
+  for (int li = 0; li < int(L.size()) && e == cudaSuccess; ++li) {
+    const bool last = li + 1 == int(L.size());
+    float* dst = last ? out : Hs + int64_t(li) * B * H;
+    float* z = (!last && keep) ? Zs + int64_t(li) * B * H : nullptr;
+    e = gemm(false, false, int(B), L[li].fo, L[li].fi, in, L[li].fi, m->d_params + L[li].w, L[li].fo, dst, L[li].fo,
+             m->d_params + L[li].b, z, last ? 0 : 1, s);
+    in = dst;
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dlbchem_mlp_create(int n_in, int n_hidden, int n_out, dlbchem_mlp** out) {
+  if (!out || n_in < 1 || n_hidden < 1 || n_out < 1) return DLBCHEM_BAD_ARG;
+  *out = nullptr;
+  auto* m = new dlbchem_mlp;
+  m->n_in = n_in; m->n_hidden = n_hidden; m->n_out = n_out;
+  const auto L = layers_of(m);
+  m->nparams = L.back().b + L.back().fo;
+  const size_t bytes = size_t(m->nparams) * 4;
+  if (cudaMalloc(&m->d_params, bytes) != cudaSuccess || cudaMalloc(&m->d_m, bytes) != cudaSuccess ||
+      cudaMalloc(&m->d_v, bytes) != cudaSuccess || cudaMalloc(&m->d_grad, bytes) != cudaSuccess ||
+      cudaMalloc(&m->d_norm, size_t(2 * (n_in + n_out)) * 4) != cudaSuccess) {
+    dlbchem_mlp_destroy(m);
+    return DLBCHEM_OOM;
+  }
+  cudaMemset(m->d_params, 0, bytes);
+  cudaMemset(m->d_m, 0, bytes);
+  cudaMemset(m->d_v, 0, bytes);
+  std::vector<float> norm(2 * (n_in + n_out), 0.0f);
+  for (int i = 0; i < n_in; ++i) norm[n_in + i] = 1.0f;
+  for (int i = 0; i < n_out; ++i) norm[2 * n_in + n_out + i] = 1.0f;
+  cudaMemcpy(m->d_norm, norm.data(), norm.size() * 4, cudaMemcpyHostToDevice);
+  *out = m;
+  return DLBCHEM_OK;
+}
+
+int64_t dlbchem_mlp_nparams(const dlbchem_mlp* m) { return m ? m->nparams : -1; }
+
+int dlbchem_mlp_set_params(dlbchem_mlp* m, const float* params, void* stream) {
+  if (!m || !params) return DLBCHEM_BAD_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(m->d_params, params, size_t(m->nparams) * 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->d_m, 0, size_t(m->nparams) * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->d_v, 0, size_t(m->nparams) * 4, s);
+  m->adam_t = 0;
+  return e == cudaSuccess ? DLBCHEM_OK : mfail(m, DLBCHEM_CUDA, cudaGetErrorString(e));
+}
+
+int dlbchem_mlp_get_params(dlbchem_mlp* m, float* params, void* stream) {
+  if (!m || !params) return DLBCHEM_BAD_ARG;
+  const cudaError_t e = cudaMemcpyAsync(params, m->d_params, size_t(m->nparams) * 4, cudaMemcpyDeviceToDevice,
+                                        static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? DLBCHEM_OK : mfail(m, DLBCHEM_CUDA, cudaGetErrorString(e));
+}
+
+int dlbchem_mlp_set_norm(dlbchem_mlp* m, const float* mu_x, const float* sd_x, const float* mu_y, const float* sd_y) {
+  if (!m || !mu_x || !sd_x || !mu_y || !sd_y) return DLBCHEM_BAD_ARG;
+  std::vector<float> norm;
+  for (int i = 0; i < m->n_in; ++i) norm.push_back(mu_x[i]);
+  for (int i = 0; i < m->n_in; ++i) {
+    if (!(sd_x[i] > 0)) return mfail(m, DLBCHEM_BAD_ARG, "input scales must be positive");
+    norm.push_back(1.0f / sd_x[i]);
+  }
+  for (int i = 0; i < m->n_out; ++i) norm.push_back(mu_y[i]);
+  for (int i = 0; i < m->n_out; ++i) norm.push_back(sd_y[i]);
+  const cudaError_t e = cudaMemcpy(m->d_norm, norm.data(), norm.size() * 4, cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? DLBCHEM_OK : mfail(m, DLBCHEM_CUDA, cudaGetErrorString(e));
+}
+
+int dlbchem_mlp_forward(dlbchem_mlp* m, int64_t batch, const float* X, float* out, void* stream) {
+  if (!m || batch < 0 || (batch > 0 && (!X || !out))) return DLBCHEM_BAD_ARG;
+  if (batch == 0) return DLBCHEM_OK;
+  int rc = ensure_act(m, batch);
+  if (rc != DLBCHEM_OK) return rc;
+  const cudaError_t e = forward(m, batch, X, out, false, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? DLBCHEM_OK : mfail(m, DLBCHEM_CUDA, cudaGetErrorString(e));
+}
+
+// Loss and gradient of the MSE on one batch (X [B x n_in], Y [B x n_out],
+// normalised). grad: device [nparams] or NULL (internal buffer); loss:
+// device float or NULL.
+int dlbchem_mlp_grad(dlbchem_mlp* m, int64_t B, const float* X, const float* Y, float* grad, float* loss, void* stream) {
+  if (!m || B < 1 || !X || !Y) return DLBCHEM_BAD_ARG;
+  int rc = ensure_act(m, B);
+  if (rc != DLBCHEM_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* g = grad ? grad : m->d_grad;
+  const auto L = layers_of(m);
+  const int64_t H = m->n_hidden, wmax = std::max(m->n_hidden, m->n_out);
+  float* Zs = m->d_act;
+  float* Hs = Zs + int64_t(m->n_layers) * B * H;
+  float* out = Hs + int64_t(m->n_layers) * B * H;
+  float* dA = out + B * m->n_out;
+  float* dB = dA + B * wmax;
+  cudaError_t e = forward(m, B, X, out, true, s);
+  if (e == cudaSuccess && loss) e = cudaMemsetAsync(loss, 0, 4, s);
+  if (e == cudaSuccess) {
+    const int64_t n = B * m->n_out;
+    dlb::mse_kernel<<<unsigned(std::min<int64_t>((n + 255) / 256, 1024)), 256, 0, s>>>(n, 1.0f / float(n), out, Y, dA,
+                                                                                     loss);
+    e = cudaGetLastError();
+  }
+  float* dcur = dA;
+  float* dnext = dB;
+  for (int li = int(L.size()) - 1; li >= 0 && e == cudaSuccess; --li) {
+    const float* hin = li == 0 ? X : Hs + int64_t(li - 1) * B * H;
+    // dW = hin^T dZ  (M = fan_in, N = fan_out, K = B)
+    e = gemm(true, false, L[li].fi, L[li].fo, int(B), hin, L[li].fi, dcur, L[li].fo, g + L[li].w, L[li].fo, nullptr,
+             nullptr, 0, s);
+    if (e == cudaSuccess) {
+      dlb::bias_grad_kernel<<<(L[li].fo + 127) / 128, 128, 0, s>>>(int(B), L[li].fo, dcur, g + L[li].b);
+      e = cudaGetLastError();
+    }
+    if (li == 0 || e != cudaSuccess) break;
+    // dH_prev = dZ W^T  (M = B, N = fan_in, K = fan_out), then through SiLU
+    e = gemm(false, true, int(B), L[li].fi, L[li].fo, dcur, L[li].fo, m->d_params + L[li].w, L[li].fo, dnext,
+             L[li].fi, nullptr, nullptr, 0, s);
+    if (e == cudaSuccess) {
+      const int64_t n = B * H;
+      dlb::silu_back_kernel<<<unsigned(std::min<int64_t>((n + 255) / 256, 4096)), 256, 0, s>>>(
+          n, dnext, Zs + int64_t(li - 1) * B * H);
+      e = cudaGetLastError();
+    }
+    float* t = dcur; dcur = dnext; dnext = t;
+  }
+  return e == cudaSuccess ? DLBCHEM_OK : mfail(m, DLBCHEM_CUDA, cudaGetErrorString(e));
+}
+
+int dlbchem_mlp_adam(dlbchem_mlp* m, const float* grad, float lr, void* stream) {
+  if (!m || !(lr > 0)) return DLBCHEM_BAD_ARG;
+  m->adam_t += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - std::pow(b1, float(m->adam_t)), c2 = 1.0f - std::pow(b2, float(m->adam_t));
+  dlb::adam_kernel<<<unsigned(std::min<int64_t>((m->nparams + 255) / 256, 2048)), 256, 0,
+                     static_cast<cudaStream_t>(stream)>>>(m->nparams, m->d_params, grad ? grad : m->d_grad, m->d_m,
+                                                          m->d_v, lr, b1, b2, 1e-8f, c1, c2);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DLBCHEM_OK : mfail(m, DLBCHEM_CUDA, cudaGetErrorString(e));
+}
+
+int dlbchem_mlp_train_step(dlbchem_mlp* m, int64_t B, const float* X, const float* Y, float lr, float* loss,
+                           void* stream) {
+  int rc = dlbchem_mlp_grad(m, B, X, Y, nullptr, loss, stream);
+  return rc == DLBCHEM_OK ? dlbchem_mlp_adam(m, nullptr, lr, stream) : rc;
+}
+
+const char* dlbchem_mlp_last_error(const dlbchem_mlp* m) { return m ? m->err.c_str() : ""; }
+
+void dlbchem_mlp_destroy(dlbchem_mlp* m) {
+  if (!m) return;
+  cudaDeviceSynchronize();
+  for (float* p : {m->d_params, m->d_m, m->d_v, m->d_grad, m->d_norm, m->d_act})
+    if (p) cudaFree(p);
+  delete m;
+}
+
+}  // extern "C"
+
+namespace dlb {
+
+// Network predictions for n cells of one context's field (used by
+// dlbchem_integrate when the predictor or the surrogate is on): features ->
+// forward -> physical ln steps, dT, dY. X, out, lnsteps, dT, dY are caller
+// workspace.
+cudaError_t mlp_predict(dlbchem_mlp* m, int64_t n, int nsp, const double* T, const double* p, const double* Y,
+                        double dt, float* X, float* out, float* lnsteps, double* dT, double* dY, cudaStream_t s) {
+  if (ensure_act(m, std::min<int64_t>(n, 65536)) != DLBCHEM_OK) return cudaErrorMemoryAllocation;
+  const float* mu_x = m->d_norm;
+  const float* isd_x = mu_x + m->n_in;
+  const float* mu_y = isd_x + m->n_in;
+  const float* sd_y = mu_y + m->n_out;
+  features_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, nsp, T, p, Y, dt, mu_x, isd_x, X);
+  cudaError_t e = cudaGetLastError();
+  for (int64_t b0 = 0; b0 < n && e == cudaSuccess; b0 += 65536) {
+    const int64_t b = std::min<int64_t>(65536, n - b0);
+    e = forward(m, b, X + b0 * m->n_in, out + b0 * m->n_out, false, s);
+  }
+  if (e == cudaSuccess) {
+    predictions_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, nsp, out, mu_y, sd_y, lnsteps, dT, dY);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+int mlp_shape(const dlbchem_mlp* m, int* n_in, int* n_out) {
+  *n_in = m->n_in;
+  *n_out = m->n_out;
+  return 0;
+}
+
+}  // namespace dlb

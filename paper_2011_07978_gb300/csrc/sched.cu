@@ -114,6 +114,21 @@ __global__ void init_list_kernel(int64_t n, const int32_t* __restrict__ steps_in
   keys[i] = 0xffffffffu - uint32_t(s > 0 ? s : 0);
 }
 
+// Per block: number of cells still to integrate (flag 0).
+__global__ void count_kernel(int64_t n, const uint8_t* __restrict__ flag, int32_t* __restrict__ block_count) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int c = __syncthreads_count(i < n && flag[i] == 0);
+  if (threadIdx.x == 0) block_count[blockIdx.x] = c;
+}
+
+// Predicted cost key: round(exp(ln steps)), clamped to [1, 2^30].
+__global__ void lnsteps_keys_kernel(int64_t n, const float* __restrict__ lnsteps, int32_t* __restrict__ keys) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const float v = lnsteps[i];
+  keys[i] = v != v ? 1 : int32_t(fminf(fmaxf(__expf(fminf(v, 30.0f)), 1.0f), 1073741824.0f) + 0.5f);
+}
+
 // Batched work list: entries (mesh << kMeshShift) | cell over all meshes,
 // mesh by mesh in index order, with each cell's cost key.
 __global__ void batch_list_kernel(int nmesh, const MeshDesc* __restrict__ mesh, const int64_t* __restrict__ offsets,
@@ -190,7 +205,7 @@ __global__ void map_scatter_kernel(int64_t n, int nsp, const uint8_t* __restrict
                                    double* __restrict__ Tout, double* __restrict__ Yout, int32_t* __restrict__ steps,
                                    int32_t* __restrict__ status) {
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (i >= n || !mapped[i]) return;
+  if (i >= n || mapped[i] != 1) return;
   const int64_t r = int64_t(*ref);
   Tout[i] = T[i] + (Tout[r] - ref_state[0]);
   for (int k = 0; k < nsp; ++k)
@@ -255,6 +270,19 @@ cudaError_t launch_batch_list(int nmesh, const MeshDesc* mesh, const int64_t* of
                               int32_t* list, uint32_t* keys, int64_t* total, cudaStream_t s) {
   batch_list_kernel<<<unsigned(tiles_of(total_n)), kSchedThreads, 0, s>>>(nmesh, mesh, offsets, total_n, list, keys,
                                                                          total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_scan(int64_t n, const uint8_t* flag, int32_t* block_count, int32_t* block_off,
+                              int64_t* total, cudaStream_t s) {
+  const unsigned nb = unsigned(tiles_of(n));
+  count_kernel<<<nb, kSchedThreads, 0, s>>>(n, flag, block_count);
+  scan_counts_kernel<<<1, kSchedThreads, 0, s>>>(int(nb), block_count, block_off, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lnsteps_keys(int64_t n, const float* lnsteps, int32_t* keys, cudaStream_t s) {
+  lnsteps_keys_kernel<<<unsigned(tiles_of(n)), kSchedThreads, 0, s>>>(n, lnsteps, keys);
   return cudaGetLastError();
 }
 

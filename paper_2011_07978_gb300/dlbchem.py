@@ -13,6 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdlbchem.so")
 
 OK, BAD_ARG, BAD_MECH, CUDA, OOM = 0, 1, 2, 3, 4
+CELL_SURROGATE = 2
 STATIC_MAX_CELLS = 262144
 CELL_OK, CELL_MAPPED, CELL_MAX_STEPS, CELL_H_UNDERFLOW, CELL_NONFINITE = 0, 1, -1, -2, -3
 SCHED_PLAIN, SCHED_QUEUE = 0, 1
@@ -23,7 +24,8 @@ class dlbchem_options(ctypes.Structure):
                 ("isothermal", ctypes.c_int32), ("hmin_frac", ctypes.c_double), ("schedule", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("mapping", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("map_Ttol", ctypes.c_double), ("map_Ytol", ctypes.c_double), ("map_Tmax", ctypes.c_double),
-                ("team_warps", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("team_warps", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("predictor", ctypes.c_int32), ("surrogate", ctypes.c_int32), ("gate", ctypes.c_double)]
 
 
 _vp = ctypes.c_void_p
@@ -54,6 +56,21 @@ def load() -> ctypes.CDLL:
     lib.dlbchem_last_error.argtypes = [_vp]
     lib.dlbchem_last_error.restype = ctypes.c_char_p
     lib.dlbchem_destroy.argtypes = [_vp]
+    lib.dlbchem_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]
+    lib.dlbchem_mlp_nparams.argtypes = [_vp]
+    lib.dlbchem_mlp_nparams.restype = ctypes.c_int64
+    lib.dlbchem_mlp_set_params.argtypes = [_vp, _vp, _vp]
+    lib.dlbchem_mlp_get_params.argtypes = [_vp, _vp, _vp]
+    _fp = ctypes.POINTER(ctypes.c_float)
+    lib.dlbchem_mlp_set_norm.argtypes = [_vp, _fp, _fp, _fp, _fp]
+    lib.dlbchem_mlp_forward.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp]
+    lib.dlbchem_mlp_grad.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
+    lib.dlbchem_mlp_adam.argtypes = [_vp, _vp, ctypes.c_float, _vp]
+    lib.dlbchem_mlp_train_step.argtypes = [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_float, _vp, _vp]
+    lib.dlbchem_mlp_last_error.argtypes = [_vp]
+    lib.dlbchem_mlp_last_error.restype = ctypes.c_char_p
+    lib.dlbchem_mlp_destroy.argtypes = [_vp]
+    lib.dlbchem_attach_mlp.argtypes = [_vp, _vp]
     lib.dlbchem_batch_create.argtypes = [ctypes.POINTER(dlbchem_options), ctypes.POINTER(_vp)]
     lib.dlbchem_batch_add.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int64, ctypes.c_double] + [_vp] * 7
     lib.dlbchem_batch_tune.argtypes = [_vp, ctypes.c_int64, _vp]
@@ -189,6 +206,11 @@ class Context:
         self._check(load().dlbchem_last_worklist(self._h, _ptr(out), ctypes.byref(m)))
         return m.value
 
+    def attach_mlp(self, mlp):
+        """dlbchem_attach_mlp: the network used by the predictor / surrogate options."""
+        self._mlp = mlp
+        self._check(load().dlbchem_attach_mlp(self._h, None if mlp is None else mlp._h))
+
     def close(self):
         if getattr(self, "_h", None):
             load().dlbchem_destroy(self._h)
@@ -246,6 +268,70 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             load().dlbchem_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class MLP:
+    """dlbchem_mlp_*: the BF16 tensor-core network of the learned predictor."""
+
+    def __init__(self, n_in, n_hidden, n_out):
+        h = _vp()
+        rc = load().dlbchem_mlp_create(n_in, n_hidden, n_out, ctypes.byref(h))
+        if rc != OK:
+            raise DlbchemError(rc, "mlp create failed")
+        self._h = h
+        self.n_in, self.n_hidden, self.n_out = n_in, n_hidden, n_out
+        self.nparams = load().dlbchem_mlp_nparams(h)
+
+    def _check(self, rc):
+        if rc != OK:
+            raise DlbchemError(rc, load().dlbchem_mlp_last_error(self._h).decode())
+
+    def set_params(self, params, stream=None):
+        self._check(load().dlbchem_mlp_set_params(self._h, _ptr(params), _stream_ptr(stream)))
+
+    def get_params(self, out, stream=None):
+        self._check(load().dlbchem_mlp_get_params(self._h, _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def set_norm(self, mu_x, sd_x, mu_y, sd_y):
+        import numpy as np
+        f = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+        arrs = [f(mu_x), f(sd_x), f(mu_y), f(sd_y)]
+        self._norm = arrs
+        fp = ctypes.POINTER(ctypes.c_float)
+        self._check(load().dlbchem_mlp_set_norm(self._h, *[a.ctypes.data_as(fp) for a in arrs]))
+
+    def forward(self, X, out, stream=None):
+        self._check(load().dlbchem_mlp_forward(self._h, X.shape[0], _ptr(X), _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def grad(self, X, Y, grad=None, loss=None, stream=None):
+        self._check(load().dlbchem_mlp_grad(self._h, X.shape[0], _ptr(X), _ptr(Y), _ptr(grad), _ptr(loss),
+                                            _stream_ptr(stream)))
+
+    def adam(self, lr, grad=None, stream=None):
+        self._check(load().dlbchem_mlp_adam(self._h, _ptr(grad), float(lr), _stream_ptr(stream)))
+
+    def train_step(self, X, Y, lr, loss=None, stream=None):
+        self._check(load().dlbchem_mlp_train_step(self._h, X.shape[0], _ptr(X), _ptr(Y), float(lr), _ptr(loss),
+                                                  _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dlbchem_mlp_destroy(self._h)
             self._h = None
 
     def __del__(self):

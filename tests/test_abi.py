@@ -45,8 +45,24 @@ def test_options_default_and_binding_layout(lib_path):
     o = dlbchem.options_default()
     assert o.rtol == 1e-6 and o.atol == 1e-10 and o.max_steps == 100000 and o.schedule == dlbchem.SCHED_PLAIN
     assert o.map_Ttol == 1e-4 and o.map_Ytol == 1e-4 and o.chunk == 1
-    # the ctypes struct must match the C layout (sizeof checked against the header's field list)
-    assert ctypes.sizeof(dlbchem.dlbchem_options) == 8 * 2 + 4 * 2 + 8 + 4 * 4 + 8 * 3 + 4 * 2
+    assert o.gate == 1e-4 and o.predictor == 0 and o.surrogate == 0 and o.precision == 0
+
+
+def test_binding_struct_layout_matches_the_header(tmp_path):
+    """sizeof and every field offset of dlbchem_options, from a C program
+    compiled against include/dlbchem.h, equal the ctypes mirror's."""
+    from paper_2011_07978_gb300 import dlbchem
+    fields = [f for f, _ in dlbchem.dlbchem_options._fields_]
+    src = tmp_path / "layout.c"
+    body = "".join(f'  printf("%zu\\n", offsetof(dlbchem_options, {f}));\n' for f in fields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "dlbchem.h"\nint main(void) {\n'
+                   '  printf("%zu\\n", sizeof(dlbchem_options));\n' + body + '  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)], text=True).split()]
+    assert vals[0] == ctypes.sizeof(dlbchem.dlbchem_options)
+    for f, off in zip(fields, vals[1:]):
+        assert getattr(dlbchem.dlbchem_options, f).offset == off, f
 
 
 def test_create_rejects_bad_arguments_without_gpu(lib_path):

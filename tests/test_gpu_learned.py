@@ -1,0 +1,168 @@
+"""The learned cost predictor and surrogate (needs a GB300).
+
+* The BF16 tensor-core network's loss and gradients match the FP64 CPU
+  oracle network (oracle/mlp.py) per tensor within 2e-2 relative, cosine
+  >= 0.999.
+* Trained on integrator trajectories of the 10-species case, the predicted
+  step counts order the queue better than index order (makespan of greedy
+  scheduling on the true costs), cells that fail the gate are integrated
+  bit-identically to the plain path, and accepted cells satisfy the gate.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from synth import read_mech, states
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def lib():
+    from paper_2011_07978_gb300 import build, dlbchem
+    build.build()
+    return dlbchem
+
+
+def _per_tensor(theta, shapes):
+    out, o = [], 0
+    for a, b in shapes:
+        out.append(theta[o:o + a * b]); o += a * b
+        out.append(theta[o:o + b]); o += b
+    return out
+
+
+def test_network_gradients_match_fp64_oracle():
+    d = lib()
+    n_in, n_out, B = 13, 12, 96
+    shapes = omlp.layer_shapes(n_in, 256, n_out)
+    rng = np.random.default_rng(3)
+    theta = omlp.init_params(n_in, 256, n_out, seed=5) + rng.normal(0, 0.02, omlp.n_params(n_in, 256, n_out))
+    theta = theta.astype(np.float32).astype(np.float64)
+    X = rng.normal(size=(B, n_in)).astype(np.float32)
+    Y = rng.normal(size=(B, n_out)).astype(np.float32)
+    loss_ref, g_ref = omlp.loss_and_grad(theta, X.astype(np.float64), Y.astype(np.float64), shapes)
+    out_ref, _ = omlp.forward(theta, X.astype(np.float64), shapes)
+    net = d.MLP(n_in, 256, n_out)
+    assert net.nparams == theta.size
+    net.set_params(torch.tensor(theta.astype(np.float32), device=DEV))
+    Xd, Yd = torch.tensor(X, device=DEV), torch.tensor(Y, device=DEV)
+    out = net.forward(Xd, torch.empty((B, n_out), dtype=torch.float32, device=DEV))
+    g = torch.zeros(net.nparams, dtype=torch.float32, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float32, device=DEV)
+    net.grad(Xd, Yd, grad=g, loss=loss)
+    torch.cuda.synchronize()
+    out = out.cpu().numpy()
+    assert np.linalg.norm(out - out_ref) <= 2e-2 * np.linalg.norm(out_ref)
+    assert abs(float(loss.item()) - loss_ref) <= 2e-2 * loss_ref
+    for gg, gr in zip(_per_tensor(g.cpu().numpy().astype(np.float64), shapes), _per_tensor(g_ref, shapes)):
+        rel = np.linalg.norm(gg - gr) / np.linalg.norm(gr)
+        cos = gg @ gr / (np.linalg.norm(gg) * np.linalg.norm(gr))
+        assert rel <= 2e-2 and cos >= 0.999, (rel, cos)
+
+
+def test_adam_step_matches_oracle():
+    d = lib()
+    net = d.MLP(13, 256, 12)
+    rng = np.random.default_rng(0)
+    theta = rng.normal(size=net.nparams).astype(np.float32)
+    g = rng.normal(size=net.nparams).astype(np.float32)
+    net.set_params(torch.tensor(theta, device=DEV))
+    net.adam(1e-3, grad=torch.tensor(g, device=DEV))
+    out = net.get_params(torch.empty(net.nparams, dtype=torch.float32, device=DEV)).cpu().numpy()
+    ref, _, _ = omlp.adam_step(theta.astype(np.float64), g.astype(np.float64), np.zeros(net.nparams),
+                               np.zeros(net.nparams), 1, 1e-3)
+    np.testing.assert_allclose(out, ref, rtol=1e-5, atol=1e-7)
+
+
+def _greedy_makespan(costs, P):
+    """List scheduling: each cost goes to the team that frees up first."""
+    import heapq
+    heap = [0.0] * P
+    for c in costs:
+        t = heapq.heappop(heap)
+        heapq.heappush(heap, t + c)
+    return max(heap)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    d = lib()
+    from paper_2011_07978_gb300 import learned
+    mech = states.mech_path(10, 20, 0)
+    ctx = d.Context(mech, rtol=1e-6, atol=1e-10)
+    n = 49152
+    T, p, Y = states.uniform_states(10, n, 100)
+    dt = learned.dt_buckets(n, 100, nbuckets=8)
+    X, Yt, steps, status = learned.generate(ctx, T, p, Y, dt)
+    assert (status == 0).all()
+    net = learned.train(X, Yt, epochs=12, batch=2048, lr=2e-3, seed=1)
+    assert net.history[-1] < 0.5 * net.history[0]
+    return d, learned, net, mech
+
+
+def test_predictor_orders_the_queue_and_keeps_results(trained):
+    d, learned, net, mech = trained
+    n = 6000
+    T, p, Y = states.uniform_states(10, n, 1)            # a fresh field: no previous steps
+    dt = 4e-6
+    dd = lambda a: torch.tensor(np.ascontiguousarray(a), device=DEV)
+    plain = d.Context(mech, rtol=1e-6, atol=1e-10)
+    st0 = torch.zeros(n, dtype=torch.int32, device=DEV)
+    To0, Yo0 = plain.integrate(dd(T), dd(p), dd(Y), dt, steps=st0)
+    ctx = d.Context(mech, rtol=1e-6, atol=1e-10, schedule=d.SCHED_QUEUE, predictor=1)
+    ctx.attach_mlp(net)
+    st = torch.zeros(n, dtype=torch.int32, device=DEV)
+    To, Yo = ctx.integrate(dd(T), dd(p), dd(Y), dt, steps=st)
+    wl = torch.zeros(n, dtype=torch.int32, device=DEV)
+    m = ctx.last_worklist(wl)
+    torch.cuda.synchronize()
+    assert torch.equal(To, To0) and torch.equal(Yo, Yo0) and torch.equal(st, st0)
+    cost = st0.cpu().numpy().astype(float)
+    order = wl.cpu().numpy()[:m]
+    P = 608
+    span_index = _greedy_makespan(cost, P)
+    span_pred = _greedy_makespan(cost[order], P)
+    span_lpt = _greedy_makespan(np.sort(cost)[::-1], P)
+    print(f"makespan in steps: index order {span_index:.0f}, predicted order {span_pred:.0f}, "
+          f"exact LPT {span_lpt:.0f}")
+    assert span_pred < span_index
+    rank = np.corrcoef(np.argsort(np.argsort(-cost[order])), np.arange(m))[0, 1]
+    assert rank > 0.3
+
+
+def test_surrogate_gate_and_fallback(trained):
+    d, learned, net, mech = trained
+    n = 4000
+    T, p, Y = states.uniform_states(10, n, 2)
+    T[: n // 2] = np.random.default_rng(0).uniform(300, 420, n // 2)   # some nearly inert cold cells
+    dt = 2e-6
+    dd = lambda a: torch.tensor(np.ascontiguousarray(a), device=DEV)
+    plain = d.Context(mech, rtol=1e-6, atol=1e-10)
+    To0, Yo0 = plain.integrate(dd(T), dd(p), dd(Y), dt)
+    gate = 1e-4
+    ctx = d.Context(mech, rtol=1e-6, atol=1e-10, surrogate=1, gate=gate)
+    ctx.attach_mlp(net)
+    st = torch.zeros(n, dtype=torch.int32, device=DEV)
+    ss = torch.zeros(n, dtype=torch.int32, device=DEV)
+    To, Yo = ctx.integrate(dd(T), dd(p), dd(Y), dt, steps=st, status=ss)
+    torch.cuda.synchronize()
+    ss, To, Yo, To0, Yo0 = ss.cpu().numpy(), To.cpu().numpy(), Yo.cpu().numpy(), To0.cpu().numpy(), Yo0.cpu().numpy()
+    acc = ss == d.CELL_SURROGATE
+    integ = ss == 0
+    assert acc.sum() + integ.sum() == n
+    np.testing.assert_array_equal(To[integ], To0[integ])
+    np.testing.assert_array_equal(Yo[:, integ], Yo0[:, integ])
+    orc = oracle.Oracle(mech)
+    m = read_mech(mech)
+    for i in np.flatnonzero(acc)[:50]:
+        y0 = np.concatenate([[T[i]], Y[:, i]])
+        y1 = np.concatenate([[To[i]], Yo[:, i]])
+        defect = y1 - y0 - 0.5 * dt * (orc.rhs(p[i], y0) + orc.rhs(p[i], y1))
+        assert abs(defect[0]) <= gate * T[i] * 1.001 and np.abs(defect[1:]).max() <= gate * 1.001
+        assert abs(Yo[:, i].sum() - 1) <= gate * 1.001
+    err = np.abs(Yo[:, acc] - Yo0[:, acc]).max(axis=0) if acc.any() else np.zeros(0)
+    print(f"surrogate accepted {acc.sum()} of {n} cells; max |dY| vs integrator on accepted "
+          f"{err.max() if err.size else 0:.2e}")

@@ -44,7 +44,7 @@ FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one integrator launch from
 # ncu on the 2048-cell case (1.386 MB + 0 B), scaled by cells to the full
 # 262,144-cell field; None whenever the kernel changes after the capture.
-INTEGRATOR_TRAFFIC_BYTES = 1.386e6 * 262144 / 2048
+INTEGRATOR_TRAFFIC_BYTES = None
 
 
 def flops_per_step(m) -> float:
@@ -178,6 +178,8 @@ def main():
     ap.add_argument("--schedule", default="queue", choices=["queue", "plain"])
     ap.add_argument("--mapping", type=int, default=1)
     ap.add_argument("--ncells", type=int, default=NCELLS)
+    ap.add_argument("--team-warps", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="warps per cell (0 = the library's automatic choice)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -200,7 +202,8 @@ def main():
     mech = read_mech(states.mech_path(NSP, NRX, SEED))
     sched = dlbchem.SCHED_QUEUE if args.schedule == "queue" else dlbchem.SCHED_PLAIN
     ctx = dlbchem.Context(states.mech_path(NSP, NRX, SEED), rtol=RTOL, atol=ATOL, schedule=sched,
-                          mapping=args.mapping, map_Ttol=MAP_TOL, map_Ytol=MAP_TOL, timing=1)
+                          mapping=args.mapping, map_Ttol=MAP_TOL, map_Ytol=MAP_TOL, timing=1,
+                          team_warps=args.team_warps)
     d = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
     Td, pd, Yd = d(T), d(p), d(Y)
     To, Yo = torch.empty_like(Td), torch.empty_like(Yd)

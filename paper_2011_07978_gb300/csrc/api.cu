@@ -217,45 +217,53 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
     DS = std::max(DS, int(mt.nds));
   }
   dm.DS = DS;
-  if (int64_t(nrx) * DS >= 65536) { err = "too many reactions for 16-bit D indices"; return false; }
-  // incidence and triple entries, partitioned by target species over the team's warps
-  std::vector<std::vector<Entry>> inc_w(wpc), tri_w(wpc);
-  for (int r = 0; r < nrx; ++r) {
-    const HostRxn& x = hm.rx[r];
-    std::map<int, int> nu;
-    for (int k : x.r) nu[k] -= 1;
-    for (int k : x.p) nu[k] += 1;
-    for (auto& kv : nu) {
-      const int k = kv.first, v = kv.second;
-      if (v == 0) continue;
-      if (v < -7 || v > 7) { err = "stoichiometric coefficient out of range"; return false; }
-      inc_w[k % wpc].push_back({k, pack_inc(k, r, v), double(v)});
-      const auto& dl = distinct[r];
-      for (int s = 0; s < int(dl.size()); ++s) {
-        const int j = dl[s];
-        tri_w[k % wpc].push_back({(1 + k) * ld + 1 + j, pack_tri((1 + k) * ld + 1 + j, r * DS + s),
-                                  v * W[k] / W[j]});
-      }
-      if (meta[r].flags & RX_EFF)
-        for (auto& e : x.eff) {
-          const int j = e.first;
-          tri_w[k % wpc].push_back({(1 + k) * ld + 1 + j,
-                                    pack_tri((1 + k) * ld + 1 + j, r * DS + meta[r].dslot_eff),
-                                    v * (e.second - 1.0) * W[k] / W[j]});
-        }
-    }
-  }
+  // incidence and Jacobian entries per chunk of CH reactions, partitioned by
+  // target species over the team's warps, with chunk-local reaction indices
+  const int CH = 32 * wpc;
+  const int nchunks = (nrx + CH - 1) / CH;
+  dm.CH = CH;
+  dm.nchunks = nchunks;
+  if (int64_t(CH) * DS >= 65536) { err = "chunk too large for 16-bit D indices"; return false; }
   std::vector<uint32_t> inc, tri;
   std::vector<double> incc, tric;
-  for (int w = 0; w < wpc; ++w) {
-    dm.inc_ptr[w] = int(inc.size() / 32);
-    build_rounds(inc_w[w], pack_inc(nsp, 0, 0), inc, incc);
-    dm.tri_ptr[w] = int(tri.size() / 32);
-    build_rounds(tri_w[w], pack_tri(N * ld, 0), tri, tric);
+  std::vector<int32_t> incp, trip;
+  for (int c = 0; c < nchunks; ++c) {
+    std::vector<std::vector<Entry>> inc_w(wpc), tri_w(wpc);
+    for (int r = c * CH; r < std::min(nrx, (c + 1) * CH); ++r) {
+      const int rl = r - c * CH;
+      const HostRxn& x = hm.rx[r];
+      std::map<int, int> nu;
+      for (int k : x.r) nu[k] -= 1;
+      for (int k : x.p) nu[k] += 1;
+      for (auto& kv : nu) {
+        const int k = kv.first, v = kv.second;
+        if (v == 0) continue;
+        if (v < -7 || v > 7) { err = "stoichiometric coefficient out of range"; return false; }
+        inc_w[k % wpc].push_back({k, pack_inc(k, rl, v), double(v)});
+        const auto& dl = distinct[r];
+        for (int s2 = 0; s2 < int(dl.size()); ++s2) {
+          const int j = dl[s2];
+          tri_w[k % wpc].push_back({(1 + k) * ld + 1 + j, pack_tri((1 + k) * ld + 1 + j, rl * DS + s2),
+                                    v * W[k] / W[j]});
+        }
+        if (meta[r].flags & RX_EFF)
+          for (auto& e : x.eff) {
+            const int j = e.first;
+            tri_w[k % wpc].push_back({(1 + k) * ld + 1 + j,
+                                      pack_tri((1 + k) * ld + 1 + j, rl * DS + meta[r].dslot_eff),
+                                      v * (e.second - 1.0) * W[k] / W[j]});
+          }
+      }
+    }
+    for (int w = 0; w < wpc; ++w) {
+      incp.push_back(int32_t(inc.size() / 32));
+      build_rounds(inc_w[w], pack_inc(nsp, 0, 0), inc, incc);
+      trip.push_back(int32_t(tri.size() / 32));
+      build_rounds(tri_w[w], pack_tri(N * ld, 0), tri, tric);
+    }
   }
-  dm.inc_ptr[wpc] = int(inc.size() / 32);
-  dm.tri_ptr[wpc] = int(tri.size() / 32);
-  for (int w = wpc + 1; w < 5; ++w) { dm.inc_ptr[w] = dm.inc_ptr[wpc]; dm.tri_ptr[w] = dm.tri_ptr[wpc]; }
+  incp.push_back(int32_t(inc.size() / 32));
+  trip.push_back(int32_t(tri.size() / 32));
   // blob
   blob.clear();
   auto put = [&](const void* p, size_t bytes) {
@@ -270,7 +278,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   offs.push_back(put(meta.data(), meta.size() * sizeof(RxnMeta)));
   offs.push_back(put(eff_sp.data(), eff_sp.size() * 4));
   offs.push_back(put(eff_dm1.data(), eff_dm1.size() * 8));
-  offs.push_back(put(inc.data(), inc.size() * 4));
+  offs.push_back(put(inc.data(), std::max<size_t>(inc.size(), 1) * 4));
   offs.push_back(put(tri.data(), tri.size() * 4));
   offs.push_back(put(tric.data(), tric.size() * 8));
   // a_ek / W_k for the element check of the surrogate gate (4 elements)
@@ -281,6 +289,8 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   for (int j = 0; j < 64; ++j) exptab[j] = double(exp2l((long double)j / 64.0L));
   offs.push_back(put(exptab.data(), exptab.size() * 8));
   offs.push_back(put(aW.data(), aW.size() * 8));
+  offs.push_back(put(incp.data(), incp.size() * 4));
+  offs.push_back(put(trip.data(), trip.size() * 4));
   // store offsets as fake pointers; relocated after upload
   auto P = [&](int i) { return reinterpret_cast<const double*>(offs[i]); };
   dm.W = P(0); dm.iW = P(1); dm.H0 = P(2); dm.cpa = P(3); dm.hcpb = P(4); dm.cpb = P(5);
@@ -294,6 +304,8 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   dm.tri_coef = P(19);
   dm.exptab = P(20);
   dm.aW = P(21);
+  dm.incp = reinterpret_cast<const int32_t*>(offs[22]);
+  dm.trip = reinterpret_cast<const int32_t*>(offs[23]);
   return true;
 }
 
@@ -312,6 +324,8 @@ void relocate(DevMech& dm, void* base) {
   dm.tri_coef = reloc(dm.tri_coef, base);
   dm.exptab = reloc(dm.exptab, base);
   dm.aW = reloc(dm.aW, base);
+  dm.incp = reloc(dm.incp, base);
+  dm.trip = reloc(dm.trip, base);
 }
 
 int configure_launch(dlbchem_ctx* c) {
@@ -321,8 +335,16 @@ int configure_launch(dlbchem_ctx* c) {
   c->num_sms = prop.multiProcessorCount;
   const size_t team_bytes = size_t(c->L.total) * 8;
   const size_t max_block = prop.sharedMemPerBlockOptin;
-  const int max_teams = 4 / c->wpc;
-  int teams = int(std::min<size_t>(max_teams, (max_block - 512) / team_bytes));
+  const size_t per_sm = prop.sharedMemPerMultiprocessor;
+  const int max_teams = 4 / c->wpc;   // at most 128 threads per CTA
+  // teams per CTA that keep the most cells resident per SM (shared memory bound)
+  int teams = 0, best_cells = 0;
+  for (int t = 1; t <= max_teams; ++t) {
+    const size_t cta = team_bytes * t + 512 + 1024;   // + exp table + per-CTA reserve
+    if (cta - 1024 > max_block) break;
+    const int cells = t * int(per_sm / cta);
+    if (cells > best_cells) { best_cells = cells; teams = t; }
+  }
   if (teams < 1) return fail(c, DLBCHEM_BAD_MECH, "mechanism too large: one cell's workspace exceeds shared memory");
   c->teams = teams;
   c->smem_bytes = int(team_bytes * teams) + 64 * 8;   // + the CTA's exp table
@@ -437,7 +459,7 @@ int dlbchem_create(const char* mech_path, const dlbchem_options* opt, dlbchem_ct
   c->wpc = o.team_warps ? o.team_warps : (c->hm.nsp + 1 <= 32 ? 1 : (c->hm.nsp + 1 <= 64 ? 2 : 4));
   std::vector<unsigned char> blob;
   if (!build_tables(c->hm, c->wpc, blob, c->dm, why)) { delete c; return fail(nullptr, DLBCHEM_BAD_MECH, why); }
-  c->L = make_layout(c->hm.nsp, c->hm.nrx, c->dm.N, c->dm.ld, c->dm.DS, o.precision == 1);
+  c->L = make_layout(c->hm.nsp, c->dm.CH, c->dm.N, c->dm.ld, c->dm.DS, o.precision == 1);
   for (auto& ev : c->ev)
     if (cudaEventCreate(&ev) != cudaSuccess) { ev = nullptr; dlbchem_destroy(c); return fail(nullptr, DLBCHEM_CUDA, "cudaEventCreate failed"); }
   if (cudaMalloc(&c->d_blob, blob.size()) != cudaSuccess || cudaMalloc(&c->d_counter, 64) != cudaSuccess) {

@@ -61,13 +61,16 @@ struct DevMech {
   const RxnMeta* meta;
   const int32_t* eff_sp;
   const double* eff_dm1;
-  // incidence rounds: warp w of a team processes rounds [inc_ptr[w], inc_ptr[w+1]) of 32 entries
+  // Reactions are processed in chunks of CH = team size; per chunk c and
+  // warp w of the team, incidence rounds [incp[c*wpc+w], incp[c*wpc+w+1])
+  // and Jacobian rounds [trip[...], trip[...+1]) of 32 entries each, with
+  // chunk-local reaction indices (no target twice in a round).
+  int CH, nchunks;
   const uint32_t* inc;
-  int inc_ptr[5];
-  // Jacobian triple rounds, same partition
+  const int32_t* incp;
   const uint32_t* tri;
   const double* tri_coef;
-  int tri_ptr[5];
+  const int32_t* trip;
   const double* exptab;   // 2^(j/64), j = 0..63 (staged into shared memory per CTA)
   const double* aW;       // [4][nsp] atoms of element e per gram of species k (a_ek / W_k)
 };
@@ -85,7 +88,7 @@ struct WsLayout {
   int total;  // doubles per team (int and float arrays are counted in doubles)
 };
 
-__host__ inline WsLayout make_layout(int nsp, int nrx, int N, int ld, int DS, bool mixed) {
+__host__ inline WsLayout make_layout(int nsp, int CH, int N, int ld, int DS, bool mixed) {
   WsLayout L;
   int o = 0;
   auto take = [&](int n) { int r = o; o += (n + 1) & ~1; return r; };  // keep 16-byte alignment
@@ -104,11 +107,11 @@ __host__ inline WsLayout make_layout(int nsp, int nrx, int N, int ld, int DS, bo
   L.dwdT = take(nsp + 1);
   L.uu = take(nsp + 1);
   L.invd = take(N);
-  L.q = take(nrx);
-  L.sig = take(nrx);
-  L.dqdT = take(nrx);
-  L.dlt = take(nrx);
-  L.D = take(nrx * DS);
+  L.q = take(CH);          // per-reaction arrays hold one chunk of CH reactions
+  L.sig = take(CH);
+  L.dqdT = take(CH);
+  L.dlt = take(CH);
+  L.D = take(CH * DS);
   L.scal = take(32);
   L.perm = take((N + 1) / 2 + 1);
   const int nm = mixed ? 1 : 0;

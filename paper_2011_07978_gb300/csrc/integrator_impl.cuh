@@ -33,10 +33,17 @@ struct Team {
   mutable int parity;
 
   __device__ __forceinline__ void sync() const {
+    // Immediate barrier ids: a register id makes ptxas reserve all 16 named
+    // barriers, and barrier use limits the CTAs resident per SM. A CTA holds
+    // at most 128 threads, so two-warp teams use ids 1-2, four-warp teams id 1.
     if (WPC == 1) {
       __syncwarp();
+    } else if (WPC == 4) {
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+    } else if (bar_id == 1) {
+      asm volatile("bar.sync 1, 64;" ::: "memory");
     } else {
-      asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(TS) : "memory");
+      asm volatile("bar.sync 2, 64;" ::: "memory");
     }
   }
   // Sum over the team; every thread receives the bitwise-identical result.
@@ -180,7 +187,17 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
   const double Ctot = P1 * iT;          // sum_k c_k (unit efficiencies)
   const double C0inv = (kRc / 1.0) * T; // R_c T / p0, p0 = 1 atm
   const double C0 = 1.0 / C0inv;
-  for (int r = tm.tid; r < nrx; r += TS) {
+  for (int k = tm.tid; k <= nsp; k += TS) {
+    w.wdot[k] = 0.0;
+    if (JAC) { w.vv[k] = 0.0; w.dwdT[k] = 0.0; w.uu[k] = 0.0; }
+  }
+  // reactions one chunk of CH (= team size) at a time: rate pass, then the
+  // chunk's conflict-free incidence rounds (and Jacobian rounds into M)
+  for (int c = 0; c < m.nchunks; ++c) {
+    const int c0 = c * m.CH;
+    const int r = c0 + tm.tid;
+    if (r < nrx) {
+    const int rl = tm.tid;
     const RxnMeta mt = m.meta[r];
     const double kf = exp_tab(fma(m.beta[r], lnT, fma(-m.EaR[r], iT, m.lnA[r])), w.exptab);
     // expanded slots as fixed registers (unused slots hold 1)
@@ -212,9 +229,9 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
       Mf = Ctot;
       for (int e = mt.eff_begin; e < mt.eff_end; ++e) Mf = fma(m.eff_dm1[e], w.c[m.eff_sp[e]], Mf);
     }
-    w.q[r] = Mf * (pf - pr);
+    w.q[rl] = Mf * (pf - pr);
     if (JAC) {
-      double* D = w.D + r * m.DS;
+      double* D = w.D + rl * m.DS;
       for (int s2 = 0; s2 < mt.nds; ++s2) D[s2] = 0.0;
       // d/dc_j of the slot product = product of the other slots
       const double kfM = kf * Mf;
@@ -229,7 +246,7 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
       }
       const int tb = (mt.flags & RX_TB) ? 1 : 0;
       if (mt.flags & RX_EFF) D[mt.dslot_eff] = pf - pr;
-      w.sig[r] = Mf * ((mt.nr + tb) * pf - (mt.np + tb) * pr);
+      w.sig[rl] = Mf * ((mt.nr + tb) * pf - (mt.np + tb) * pr);
       const double dlnkf = fma(m.EaR[r], iT * iT, m.beta[r] * iT);
       double dq = pf * dlnkf;
       if (mt.flags & RX_REV) {
@@ -241,30 +258,37 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
         const double dlnKc = dH * iT * iT * (1.0 / kR) - mt.dnu * iT;
         dq -= pr * (dlnkf - dlnKc);
       }
-      w.dqdT[r] = Mf * dq;
-      w.dlt[r] = tb ? (pf - pr) : 0.0;
+      w.dqdT[rl] = Mf * dq;
+      w.dlt[rl] = tb ? (pf - pr) : 0.0;
     }
-  }
-  for (int k = tm.tid; k <= nsp; k += TS) {
-    w.wdot[k] = 0.0;
-    if (JAC) { w.vv[k] = 0.0; w.dwdT[k] = 0.0; w.uu[k] = 0.0; }
-  }
-  tm.sync();
-  // incidence rounds: within a round every lane owns a distinct species
-  const int r0 = m.inc_ptr[tm.warp], r1 = m.inc_ptr[tm.warp + 1];
-  for (int rd = r0; rd < r1; ++rd) {
-    const uint32_t e = m.inc[rd * 32 + tm.lane];
-    const int k = int(e >> 20), r = int((e >> 4) & 0xffffu);
-    const double nu = double(int(e & 15u) - 8);
-    w.wdot[k] = fma(nu, w.q[r], w.wdot[k]);
+    }
+    tm.sync();
+    const int ci = c * m.wpc + tm.warp;
+    const int r0 = m.incp[ci], r1 = m.incp[ci + 1];
+    for (int rd = r0; rd < r1; ++rd) {
+      const uint32_t e = m.inc[rd * 32 + tm.lane];
+      const int k = int(e >> 20), rr = int((e >> 4) & 0xffffu);
+      const double nu = double(int(e & 15u) - 8);
+      w.wdot[k] = fma(nu, w.q[rr], w.wdot[k]);
+      if (JAC) {
+        w.vv[k] = fma(nu, w.sig[rr], w.vv[k]);
+        w.dwdT[k] = fma(nu, w.dqdT[rr], w.dwdT[k]);
+        w.uu[k] = fma(nu, w.dlt[rr], w.uu[k]);
+      }
+      __syncwarp();
+    }
     if (JAC) {
-      w.vv[k] = fma(nu, w.sig[r], w.vv[k]);
-      w.dwdT[k] = fma(nu, w.dqdT[r], w.dwdT[k]);
-      w.uu[k] = fma(nu, w.dlt[r], w.uu[k]);
+      const int t0 = m.trip[ci], t1 = m.trip[ci + 1];
+      for (int rd = t0; rd < t1; ++rd) {
+        const uint32_t e = m.tri[rd * 32 + tm.lane];
+        const double cf = m.tri_coef[rd * 32 + tm.lane];
+        const int tgt = int(e >> 16), d = int(e & 0xffffu);
+        w.M[tgt] = fma(cf, w.D[d], w.M[tgt]);
+        __syncwarp();
+      }
     }
-    __syncwarp();
+    tm.sync();
   }
-  tm.sync();
 }
 
 // f = (f_T, f_Y): f_Y_k = W_k wdot_k / rho, f_T = -sum h_k wdot_k / (rho cp_mass).
@@ -309,22 +333,13 @@ __device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, 
                                       double ihg) {
   constexpr int TS = 32 * WPC;
   const int nsp = m.nsp, N = m.N, ld = m.ld;
+  const int ntot = N * ld + 2;
+  for (int i = tm.tid; i < ntot; i += TS) w.M[i] = 0.0;   // the Jacobian rounds accumulate into M
+  tm.sync();
   Mix mx;
   eval_rates<WPC, true>(m, tm, w, w.y0, P1, mx);
   double Q, cpm;
   finish_f<WPC>(m, tm, w, w.y0, mx, iso, w.f0, Q, cpm);
-  const int ntot = N * ld + 2;
-  for (int i = tm.tid; i < ntot; i += TS) w.M[i] = 0.0;
-  tm.sync();
-  const int t0 = m.tri_ptr[tm.warp], t1 = m.tri_ptr[tm.warp + 1];
-  for (int rd = t0; rd < t1; ++rd) {
-    const uint32_t e = m.tri[rd * 32 + tm.lane];
-    const double cf = m.tri_coef[rd * 32 + tm.lane];
-    const int tgt = int(e >> 16), d = int(e & 0xffffu);
-    w.M[tgt] = fma(cf, w.D[d], w.M[tgt]);
-    __syncwarp();
-  }
-  tm.sync();
   // scalars for the T row / column
   double hv = 0.0, hu = 0.0, dc = 0.0, tt = 0.0;
   for (int k = tm.tid; k < nsp; k += TS) {
@@ -364,12 +379,10 @@ __device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, 
   for (int k = tm.warp; k < nsp; k += WPC) {
     const double rk = w.E[k];
     double* row = w.M + (1 + k) * ld + 1;
-    for (int j = tm.lane; j < nsp; j += 32) {
-      double v = -fma(rk, m.iW[j], row[j]);
-      if (k == j) v += ihg;
-      row[j] = v;
-    }
+    for (int j = tm.lane; j < nsp; j += 32) row[j] = fma(-rk, m.iW[j], -row[j]);
   }
+  tm.sync();
+  for (int k = tm.tid; k < nsp; k += TS) w.M[(1 + k) * (ld + 1)] += ihg;
   tm.sync();
 }
 
@@ -475,9 +488,62 @@ __device__ __forceinline__ bool lu_factor(const Team<WPC>& tm, R* M, int N, int 
   return !singular;
 }
 
+// Register sweep of one warp for N <= 32 NR: lane l holds rows l, l + 32, ...
+// in NR registers and each solved entry is broadcast by a shuffle. Columns
+// are walked in segments over which the set of slots that still hold
+// unsolved rows is fixed at compile time, so every issued FP64 instruction
+// has work in it (a warp FP64 instruction costs the same with 1 or 32 active
+// lanes, and a fully predicated-off one still takes its issue slot). Loads of
+// rows past N are clamped to row N-1; those lanes compute values that are
+// never stored.
+template <int NR, class R>
+__device__ __forceinline__ void sweep_solve(const R* M, int N, int ld, const R* invd, const int* perm,
+                                            const double* b, double* x, int l) {
+  R xs[NR];
+  int ro[NR];
+#pragma unroll
+  for (int s = 0; s < NR; ++s) {
+    const int i = 32 * s + l;
+    xs[s] = i < N ? R(b[perm[i]]) : R(0);
+    ro[s] = min(i, N - 1) * ld;
+  }
+  // forward, unit lower L: column j updates rows r > j. Segment s0 holds the
+  // columns j in [32 s0 - 1, 32 s0 + 30]: slot s0 partly, slots above fully.
+#pragma unroll
+  for (int s0 = 0; s0 < NR; ++s0) {
+    const int j0 = s0 == 0 ? 0 : 32 * s0 - 1;
+    const int j1 = min(32 * s0 + 31, N - 1);
+    for (int j = j0; j < j1; ++j) {
+      const R src = (s0 > 0 && j < 32 * s0) ? xs[s0 > 0 ? s0 - 1 : 0] : xs[s0];
+      const R xj = __shfl_sync(0xffffffffu, src, j & 31);
+      if (32 * s0 + l > j) xs[s0] = fma(-M[ro[s0] + j], xj, xs[s0]);
+#pragma unroll
+      for (int s = s0 + 1; s < NR; ++s) xs[s] = fma(-M[ro[s] + j], xj, xs[s]);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NR; ++s) xs[s] *= invd[min(32 * s + l, N - 1)];
+  // backward, unit upper U~: column j updates rows r < j. Segment t holds the
+  // columns j in [32 t + 1, 32 t + 32], walked downwards: slot t partly,
+  // slots below fully.
+#pragma unroll
+  for (int t = NR - 1; t >= 0; --t) {
+    const int j1 = min(32 * t + 32, N - 1);
+    for (int j = j1; j >= 32 * t + 1; --j) {
+      const R src = (t + 1 < NR && j >= 32 * t + 32) ? xs[t + 1 < NR ? t + 1 : t] : xs[t];
+      const R xj = __shfl_sync(0xffffffffu, src, j & 31);
+      if (32 * t + l < j) xs[t] = fma(-M[ro[t] + j], xj, xs[t]);
+#pragma unroll
+      for (int s = 0; s < t; ++s) xs[s] = fma(-M[ro[s] + j], xj, xs[s]);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NR; ++s)
+    if (32 * s + l < N) x[32 * s + l] = double(xs[s]);
+}
+
 // x = M^-1 b with the factors above; b and x are distinct team vectors.
-// For N <= 128 the team's first warp sweeps alone with x in up to four
-// registers per lane, broadcasting each solved entry by a shuffle: no
+// For N <= 128 the team's first warp sweeps alone in registers (above): no
 // shared-memory round trips and no barrier per column.
 template <int WPC, class R>
 __device__ __forceinline__ void lu_solve(const Team<WPC>& tm, const R* M, int N, int ld, const R* invd,
@@ -485,38 +551,10 @@ __device__ __forceinline__ void lu_solve(const Team<WPC>& tm, const R* M, int N,
   constexpr int TS = 32 * WPC;
   if (N <= 128) {
     if (tm.warp == 0) {
-      const int l = tm.lane;
-      const bool v0 = l < N, v1 = l + 32 < N, v2 = l + 64 < N, v3 = l + 96 < N;
-      R x0 = v0 ? R(b[perm[l]]) : R(0);
-      R x1 = v1 ? R(b[perm[l + 32]]) : R(0);
-      R x2 = v2 ? R(b[perm[l + 64]]) : R(0);
-      R x3 = v3 ? R(b[perm[l + 96]]) : R(0);
-      // forward sweep, unit lower L: rows r > j take -L_rj x_j
-      for (int j = 0; j < N - 1; ++j) {
-        const R src = j < 32 ? x0 : (j < 64 ? x1 : (j < 96 ? x2 : x3));
-        const R xj = __shfl_sync(0xffffffffu, src, j & 31);
-        if (j < 31 && v0 && l > j) x0 = fma(-M[l * ld + j], xj, x0);
-        if (j < 63 && v1 && l + 32 > j) x1 = fma(-M[(l + 32) * ld + j], xj, x1);
-        if (j < 95 && v2 && l + 64 > j) x2 = fma(-M[(l + 64) * ld + j], xj, x2);
-        if (v3 && l + 96 > j) x3 = fma(-M[(l + 96) * ld + j], xj, x3);
-      }
-      if (v0) x0 *= invd[l];
-      if (v1) x1 *= invd[l + 32];
-      if (v2) x2 *= invd[l + 64];
-      if (v3) x3 *= invd[l + 96];
-      // backward sweep, unit upper U~: rows r < j take -U~_rj x_j
-      for (int j = N - 1; j > 0; --j) {
-        const R src = j < 32 ? x0 : (j < 64 ? x1 : (j < 96 ? x2 : x3));
-        const R xj = __shfl_sync(0xffffffffu, src, j & 31);
-        if (v0 && l < j) x0 = fma(-M[l * ld + j], xj, x0);
-        if (j > 32 && v1 && l + 32 < j) x1 = fma(-M[(l + 32) * ld + j], xj, x1);
-        if (j > 64 && v2 && l + 64 < j) x2 = fma(-M[(l + 64) * ld + j], xj, x2);
-        if (j > 96 && v3 && l + 96 < j) x3 = fma(-M[(l + 96) * ld + j], xj, x3);
-      }
-      if (v0) x[l] = double(x0);
-      if (v1) x[l + 32] = double(x1);
-      if (v2) x[l + 64] = double(x2);
-      if (v3) x[l + 96] = double(x3);
+      if (N <= 32) sweep_solve<1, R>(M, N, ld, invd, perm, b, x, tm.lane);
+      else if (N <= 64) sweep_solve<2, R>(M, N, ld, invd, perm, b, x, tm.lane);
+      else if (N <= 96) sweep_solve<3, R>(M, N, ld, invd, perm, b, x, tm.lane);
+      else sweep_solve<4, R>(M, N, ld, invd, perm, b, x, tm.lane);
     }
     tm.sync();
     return;
@@ -701,7 +739,8 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
       double errn = sqrt(tm.sum(acc) / N);
       if (!ok) errn = nan("");
       if (errn <= 1.0) {
-        double fac = fmin(5.0, fmax(0.2, 0.9 * pow(errn, -0.25)));
+        // errn^(-1/4) as rsqrt(sqrt(errn)): within 2 ulp of pow, at a fraction of its FP64 work
+        double fac = fmin(5.0, fmax(0.2, 0.9 * rsqrt(sqrt(errn))));
         if (rejected_last) fac = fmin(fac, 1.0);
         t = (t + h >= dt) ? dt : t + h;
         for (int i = tm.tid; i < N; i += TS) w.y0[i] = w.ys[i];
@@ -709,7 +748,7 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
         rejected_last = false;
         h *= fac;
       } else {
-        const double fac = isfinite(errn) ? fmax(0.2, 0.9 * pow(errn, -0.25)) : 0.2;
+        const double fac = isfinite(errn) ? fmax(0.2, 0.9 * rsqrt(sqrt(errn))) : 0.2;
         rejected_last = true;
         h *= fac;
       }
@@ -728,7 +767,7 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
 
 
 template <int WPC>
-__global__ void __launch_bounds__(128, WPC == 4 ? 4 : 1) rosenbrock_kernel(const KernelArgs a) {
+__global__ void __launch_bounds__(128, WPC == 1 ? 4 : (WPC == 2 ? 3 : 2)) rosenbrock_kernel(const KernelArgs a) {
   extern __shared__ __align__(16) double smem[];
   constexpr int TS = 32 * WPC;
   const int teams = blockDim.x / TS;

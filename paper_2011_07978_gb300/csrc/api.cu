@@ -99,9 +99,11 @@ bool parse_mech(const char* path, dlb::HostMech& m, std::string& err) {
   return true;
 }
 
-// Rounds of 32 entries, no target twice in a round. Entries are placed first
-// fit in order of decreasing target multiplicity; per target the entries keep
-// their input order, which fixes every accumulation order.
+// Rounds of 32 entries, no target twice in a round. Each round takes the
+// (at most 32) targets with the most entries left, ties to the lower target,
+// which reaches the lower bound max(largest target count, ceil(n / 32)).
+// Per target the entries keep their input order, which fixes every
+// accumulation order.
 struct Entry {
   int target;
   uint32_t word;
@@ -112,30 +114,127 @@ void build_rounds(const std::vector<Entry>& ents, uint32_t pad_word, std::vector
                   std::vector<double>& coefs) {
   std::map<int, std::vector<int>> by_t;
   for (int i = 0; i < int(ents.size()); ++i) by_t[ents[i].target].push_back(i);
-  std::vector<std::pair<int, int>> order;   // (-multiplicity, target)
-  for (auto& kv : by_t) order.push_back({-int(kv.second.size()), kv.first});
-  std::sort(order.begin(), order.end());
-  std::vector<std::vector<int>> rounds;
-  std::vector<std::vector<int>> tgts;
-  for (auto& o : order) {
-    int start = 0;
-    for (int idx : by_t[o.second]) {
-      int rr = start;
-      for (;; ++rr) {
-        if (rr == int(rounds.size())) { rounds.emplace_back(); tgts.emplace_back(); }
-        if (rounds[rr].size() < 32 && std::find(tgts[rr].begin(), tgts[rr].end(), o.second) == tgts[rr].end()) break;
-      }
-      rounds[rr].push_back(idx);
-      tgts[rr].push_back(o.second);
-      start = rr + 1;
+  std::vector<std::pair<int, std::vector<int>*>> tl;   // (target, its entries)
+  std::vector<size_t> next;
+  for (auto& kv : by_t) { tl.push_back({kv.first, &kv.second}); next.push_back(0); }
+  size_t left = ents.size();
+  std::vector<int> idx(tl.size());
+  while (left > 0) {
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = int(i);
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+      const size_t ra = tl[a].second->size() - next[a], rb = tl[b].second->size() - next[b];
+      return ra != rb ? ra > rb : tl[a].first < tl[b].first;
+    });
+    int lane = 0;
+    for (int i : idx) {
+      if (lane == 32 || next[i] == tl[i].second->size()) break;
+      const Entry& e = ents[(*tl[i].second)[next[i]++]];
+      words.push_back(e.word);
+      coefs.push_back(e.coef);
+      ++lane;
+      --left;
+    }
+    for (; lane < 32; ++lane) { words.push_back(pad_word); coefs.push_back(0.0); }
+  }
+}
+
+// Rounds a list of entries needs (the bound the builder above reaches).
+int rounds_needed(const std::map<int, int>& count_by_target, int n) {
+  int mx = 0;
+  for (auto& kv : count_by_target) mx = std::max(mx, kv.second);
+  return std::max(mx, (n + 31) / 32);
+}
+
+// Per reaction: species with nonzero net coefficient, and the number of its
+// Jacobian entries per such species (distinct participants + listed efficiencies).
+struct RxnShape {
+  std::vector<int> ks;
+  int ntri;
+};
+
+// Species -> warp of the team for one chunk: kept by species parity, or
+// dealt greedily (most frequent first) to the warp whose round cost grows
+// least; the cost weighs an incidence round (4 accumulators) 4:1 against a
+// Jacobian round.
+std::map<int, int> assign_warps(const std::map<int, int>& mult, const std::map<int, int>& tmult, int wpc, bool parity) {
+  std::map<int, int> a;
+  if (parity || wpc == 1) {
+    for (auto& kv : mult) a[kv.first] = kv.first % wpc;
+    return a;
+  }
+  std::vector<int> ks;
+  for (auto& kv : mult) ks.push_back(kv.first);
+  std::sort(ks.begin(), ks.end(), [&](int x, int y) {
+    const int mx = mult.at(x), my = mult.at(y);
+    if (mx != my) return mx > my;
+    const int tx = tmult.at(x), ty = tmult.at(y);
+    return tx != ty ? tx > ty : x < y;
+  });
+  std::vector<int> inc_n(wpc, 0), inc_m(wpc, 0), tri_n(wpc, 0);
+  for (int k : ks) {
+    int best = 0;
+    long best_cost = -1;
+    for (int w = 0; w < wpc; ++w) {
+      const int ir = std::max({inc_m[w], mult.at(k), (inc_n[w] + mult.at(k) + 31) / 32});
+      const int tr = (tri_n[w] + tmult.at(k) + 31) / 32;
+      const long cost = 4L * ir + tr;
+      if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = w; }
+    }
+    a[k] = best;
+    inc_n[best] += mult.at(k); inc_m[best] = std::max(inc_m[best], mult.at(k)); tri_n[best] += tmult.at(k);
+  }
+  return a;
+}
+
+// Round cost of one device order of the reactions (chunks of CH) under one
+// warp-assignment rule: sum over chunks and warps of 4 * incidence rounds +
+// Jacobian rounds (the Jacobian bound is per warp, ignoring repeated targets).
+long order_cost(const std::vector<RxnShape>& sh, const std::vector<int>& order, int CH, int wpc, bool parity) {
+  long cost = 0;
+  for (size_t c0 = 0; c0 < order.size(); c0 += CH) {
+    std::map<int, int> mult, tmult;
+    for (size_t i = c0; i < std::min(order.size(), c0 + CH); ++i)
+      for (int k : sh[order[i]].ks) { mult[k] += 1; tmult[k] += sh[order[i]].ntri; }
+    const auto a = assign_warps(mult, tmult, wpc, parity);
+    for (int w = 0; w < wpc; ++w) {
+      std::map<int, int> m1;
+      int n1 = 0, n2 = 0;
+      for (auto& kv : mult) if (a.at(kv.first) == w) { m1[kv.first] = kv.second; n1 += kv.second; n2 += tmult[kv.first]; }
+      cost += 4L * rounds_needed(m1, n1) + (n2 + 31) / 32;
     }
   }
-  for (auto& rd : rounds) {
-    for (int l = 0; l < 32; ++l) {
-      if (l < int(rd.size())) { words.push_back(ents[rd[l]].word); coefs.push_back(ents[rd[l]].coef); }
-      else { words.push_back(pad_word); coefs.push_back(0.0); }
+  return cost;
+}
+
+// Reactions dealt to chunks so that no species crowds one chunk (a chunk's
+// incidence rounds are at least its largest per-species count): reactions
+// by decreasing frequency of their most frequent species, each to the open
+// chunk where that count stays smallest.
+std::vector<int> balanced_order(const std::vector<RxnShape>& sh, int nsp, int CH) {
+  const int nrx = int(sh.size()), nch = (nrx + CH - 1) / CH;
+  std::vector<int> freq(nsp, 0);
+  for (auto& x : sh) for (int k : x.ks) ++freq[k];
+  std::vector<int> rs(nrx);
+  for (int r = 0; r < nrx; ++r) rs[r] = r;
+  auto top = [&](int r) { int f = 0; for (int k : sh[r].ks) f = std::max(f, freq[k]); return f; };
+  std::stable_sort(rs.begin(), rs.end(), [&](int a, int b) { return top(a) > top(b); });
+  std::vector<std::vector<int>> cnt(nch, std::vector<int>(nsp, 0));
+  std::vector<std::vector<int>> chunks(nch);
+  for (int r : rs) {
+    int bc = -1, b1 = 0, b2 = 0, b3 = 0;
+    for (int c = 0; c < nch; ++c) {
+      if (int(chunks[c].size()) >= CH) continue;
+      int m = 0, sum = 0;
+      for (int k : sh[r].ks) { m = std::max(m, cnt[c][k] + 1); sum += cnt[c][k]; }
+      const int sz = int(chunks[c].size());
+      if (bc < 0 || m < b1 || (m == b1 && (sum < b2 || (sum == b2 && sz < b3)))) { bc = c; b1 = m; b2 = sum; b3 = sz; }
     }
+    chunks[bc].push_back(r);
+    for (int k : sh[r].ks) ++cnt[bc][k];
   }
+  std::vector<int> order;
+  for (auto& ch : chunks) { std::sort(ch.begin(), ch.end()); order.insert(order.end(), ch.begin(), ch.end()); }
+  return order;
 }
 
 }  // namespace
@@ -178,10 +277,44 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
     H0[k] = hm.hf[k] - a * kT0 - 0.5 * b * kT0 * kT0;          // h = H0 + a T + b/2 T^2
     const double S0 = hm.s0[k] - a * std::log(kT0) - b * kT0;   // s = S0 + a ln T + b T
     cpa[k] = a; cpb[k] = b; hcpb[k] = 0.5 * b;
-    G0[k] = H0[k] / kR; G1[k] = (a - S0) / kR; G2[k] = a / kR; G3[k] = b / (2.0 * kR);
+    // E_k = exp(-g_k/RT) * p0/(R_c T): with the standard-state concentration
+    // folded into each species factor, 1/K_c of every reaction is the plain
+    // product of reactant E and product 1/E (no (R_c T/p0)^dnu factor)
+    G0[k] = H0[k] / kR; G1[k] = (a - S0) / kR + std::log(kRc); G2[k] = a / kR - 1.0; G3[k] = b / (2.0 * kR);
     bW[k] = b / hm.W[k];
   }
-  // reactions
+  if (nrx >= 65536) { err = "mechanism too large (max 65535 reactions)"; return false; }
+  // device order of the reactions: the cheapest in incidence and Jacobian
+  // rounds among file order and a chunk-balanced order, each with warps
+  // assigned by species parity or greedily
+  const int CH = 32 * wpc;
+  std::vector<RxnShape> shape(nrx);
+  for (int r = 0; r < nrx; ++r) {
+    const HostRxn& x = hm.rx[r];
+    std::map<int, int> nu;
+    for (int k : x.r) nu[k] -= 1;
+    for (int k : x.p) nu[k] += 1;
+    std::vector<int> dl;
+    for (int k : x.r) if (std::find(dl.begin(), dl.end(), k) == dl.end()) dl.push_back(k);
+    if (x.rev) for (int k : x.p) if (std::find(dl.begin(), dl.end(), k) == dl.end()) dl.push_back(k);
+    for (auto& kv : nu) if (kv.second != 0) shape[r].ks.push_back(kv.first);
+    shape[r].ntri = int(dl.size()) + (x.tb ? int(x.eff.size()) : 0);
+  }
+  std::vector<int> order(nrx);
+  for (int r = 0; r < nrx; ++r) order[r] = r;
+  bool parity = true;
+  {
+    long best = order_cost(shape, order, CH, wpc, true);
+    const std::vector<int> bal = balanced_order(shape, nsp, CH);
+    for (int cand = 0; cand < 3; ++cand) {
+      const std::vector<int>& o = cand == 0 ? order : bal;
+      const bool par = cand == 2;
+      if (cand == 0 && wpc == 1) continue;
+      const long cst = order_cost(shape, o, CH, wpc, par);
+      if (cst < best) { best = cst; order = o; parity = par; }
+    }
+  }
+  // reactions (device index r is file reaction order[r])
   std::vector<double> lnA(nrx), beta(nrx), EaR(nrx);
   std::vector<RxnMeta> meta(nrx);
   std::vector<int32_t> eff_sp;
@@ -189,7 +322,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   std::vector<std::vector<int>> distinct(nrx);
   int DS = 1;
   for (int r = 0; r < nrx; ++r) {
-    const HostRxn& x = hm.rx[r];
+    const HostRxn& x = hm.rx[order[r]];
     lnA[r] = x.lnA; beta[r] = x.beta; EaR[r] = x.Ea / kR;
     RxnMeta& mt = meta[r];
     std::memset(&mt, 0, sizeof(mt));
@@ -219,7 +352,6 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   dm.DS = DS;
   // incidence and Jacobian entries per chunk of CH reactions, partitioned by
   // target species over the team's warps, with chunk-local reaction indices
-  const int CH = 32 * wpc;
   const int nchunks = (nrx + CH - 1) / CH;
   dm.CH = CH;
   dm.nchunks = nchunks;
@@ -227,31 +359,40 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   std::vector<uint32_t> inc, tri;
   std::vector<double> incc, tric;
   std::vector<int32_t> incp, trip;
+  auto net_nu = [&](int r) {
+    const HostRxn& x = hm.rx[order[r]];
+    std::map<int, int> nu;
+    for (int k : x.r) nu[k] -= 1;
+    for (int k : x.p) nu[k] += 1;
+    return nu;
+  };
   for (int c = 0; c < nchunks; ++c) {
+    std::map<int, int> mult, tmult;
+    for (int r = c * CH; r < std::min(nrx, (c + 1) * CH); ++r)
+      for (int k : shape[order[r]].ks) { mult[k] += 1; tmult[k] += shape[order[r]].ntri; }
+    const auto wof = assign_warps(mult, tmult, wpc, parity);
     std::vector<std::vector<Entry>> inc_w(wpc), tri_w(wpc);
     for (int r = c * CH; r < std::min(nrx, (c + 1) * CH); ++r) {
       const int rl = r - c * CH;
-      const HostRxn& x = hm.rx[r];
-      std::map<int, int> nu;
-      for (int k : x.r) nu[k] -= 1;
-      for (int k : x.p) nu[k] += 1;
-      for (auto& kv : nu) {
+      const HostRxn& x = hm.rx[order[r]];
+      for (auto& kv : net_nu(r)) {
         const int k = kv.first, v = kv.second;
         if (v == 0) continue;
         if (v < -7 || v > 7) { err = "stoichiometric coefficient out of range"; return false; }
-        inc_w[k % wpc].push_back({k, pack_inc(k, rl, v), double(v)});
+        const int w = wof.at(k);
+        inc_w[w].push_back({k, pack_inc(k, rl, v), double(v)});
         const auto& dl = distinct[r];
         for (int s2 = 0; s2 < int(dl.size()); ++s2) {
           const int j = dl[s2];
-          tri_w[k % wpc].push_back({(1 + k) * ld + 1 + j, pack_tri((1 + k) * ld + 1 + j, rl * DS + s2),
-                                    v * W[k] / W[j]});
+          tri_w[w].push_back({(1 + k) * ld + 1 + j, pack_tri((1 + k) * ld + 1 + j, rl * DS + s2),
+                              v * W[k] / W[j]});
         }
         if (meta[r].flags & RX_EFF)
           for (auto& e : x.eff) {
             const int j = e.first;
-            tri_w[k % wpc].push_back({(1 + k) * ld + 1 + j,
-                                      pack_tri((1 + k) * ld + 1 + j, rl * DS + meta[r].dslot_eff),
-                                      v * (e.second - 1.0) * W[k] / W[j]});
+            tri_w[w].push_back({(1 + k) * ld + 1 + j,
+                                pack_tri((1 + k) * ld + 1 + j, rl * DS + meta[r].dslot_eff),
+                                v * (e.second - 1.0) * W[k] / W[j]});
           }
       }
     }
@@ -264,6 +405,47 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   }
   incp.push_back(int32_t(inc.size() / 32));
   trip.push_back(int32_t(tri.size() / 32));
+  // whole-mechanism incidence rounds (rate evaluations without the Jacobian):
+  // a species in more than a balanced share of entries, ceil(n / (32 wpc)),
+  // alternates its entries over two accumulators; targets go to warps greedily
+  const int split_off = ((nsp + 1) + 1) & ~1;   // second accumulator = the v array
+  dm.split_off = split_off;
+  std::vector<uint32_t> inc_all;
+  std::vector<double> inc_allc;
+  std::vector<int32_t> incp_all;
+  {
+    std::vector<Entry> ents;
+    std::map<int, int> mult;
+    for (int r = 0; r < nrx; ++r)
+      for (auto& kv : net_nu(r)) if (kv.second != 0) mult[kv.first] += 1;
+    int n = 0;
+    for (auto& kv : mult) n += kv.second;
+    const int share = (n + 32 * wpc - 1) / (32 * wpc);
+    std::map<int, int> seen;
+    int nsplit = 0;
+    for (auto& kv : mult) nsplit += kv.second > share ? 1 : 0;
+    dm.nsplit = nsplit;
+    for (int r = 0; r < nrx; ++r)
+      for (auto& kv : net_nu(r)) {
+        const int k = kv.first, v = kv.second;
+        if (v == 0) continue;
+        const int part = mult[k] > share ? (seen[k]++ & 1) : 0;
+        const int t = part ? split_off + k : k;
+        ents.push_back({t, pack_inc(t, r, v), double(v)});
+      }
+    std::map<int, int> tm, tz;
+    for (auto& e : ents) tm[e.target] += 1;
+    for (auto& kv : tm) tz[kv.first] = 0;
+    const auto wof = assign_warps(tm, tz, wpc, false);
+    std::vector<std::vector<Entry>> per(wpc);
+    for (auto& e : ents) per[wof.at(e.target)].push_back(e);
+    for (int w = 0; w < wpc; ++w) {
+      incp_all.push_back(int32_t(inc_all.size() / 32));
+      build_rounds(per[w], pack_inc(nsp, 0, 0), inc_all, inc_allc);
+    }
+    incp_all.push_back(int32_t(inc_all.size() / 32));
+    if (split_off + nsp >= 4096) { err = "mechanism too large for 12-bit incidence targets"; return false; }
+  }
   // blob
   blob.clear();
   auto put = [&](const void* p, size_t bytes) {
@@ -291,6 +473,8 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   offs.push_back(put(aW.data(), aW.size() * 8));
   offs.push_back(put(incp.data(), incp.size() * 4));
   offs.push_back(put(trip.data(), trip.size() * 4));
+  offs.push_back(put(inc_all.data(), std::max<size_t>(inc_all.size(), 1) * 4));
+  offs.push_back(put(incp_all.data(), incp_all.size() * 4));
   // store offsets as fake pointers; relocated after upload
   auto P = [&](int i) { return reinterpret_cast<const double*>(offs[i]); };
   dm.W = P(0); dm.iW = P(1); dm.H0 = P(2); dm.cpa = P(3); dm.hcpb = P(4); dm.cpb = P(5);
@@ -306,6 +490,8 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   dm.aW = P(21);
   dm.incp = reinterpret_cast<const int32_t*>(offs[22]);
   dm.trip = reinterpret_cast<const int32_t*>(offs[23]);
+  dm.inc_all = reinterpret_cast<const uint32_t*>(offs[24]);
+  dm.incp_all = reinterpret_cast<const int32_t*>(offs[25]);
   return true;
 }
 
@@ -326,6 +512,8 @@ void relocate(DevMech& dm, void* base) {
   dm.aW = reloc(dm.aW, base);
   dm.incp = reloc(dm.incp, base);
   dm.trip = reloc(dm.trip, base);
+  dm.inc_all = reloc(dm.inc_all, base);
+  dm.incp_all = reloc(dm.incp_all, base);
 }
 
 int configure_launch(dlbchem_ctx* c) {
@@ -340,14 +528,14 @@ int configure_launch(dlbchem_ctx* c) {
   // teams per CTA that keep the most cells resident per SM (shared memory bound)
   int teams = 0, best_cells = 0;
   for (int t = 1; t <= max_teams; ++t) {
-    const size_t cta = team_bytes * t + 512 + 1024;   // + exp table + per-CTA reserve
+    const size_t cta = team_bytes * t + 640 + 1024;   // + exp and nu tables + per-CTA reserve
     if (cta - 1024 > max_block) break;
     const int cells = t * int(per_sm / cta);
     if (cells > best_cells) { best_cells = cells; teams = t; }
   }
   if (teams < 1) return fail(c, DLBCHEM_BAD_MECH, "mechanism too large: one cell's workspace exceeds shared memory");
   c->teams = teams;
-  c->smem_bytes = int(team_bytes * teams) + 64 * 8;   // + the CTA's exp table
+  c->smem_bytes = int(team_bytes * teams) + 80 * 8;   // + the CTA's exp and nu tables
   e = cudaFuncSetAttribute(dlb::rosenbrock_kernel_ptr(c->wpc), cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(dlb::gate_kernel_ptr(c->wpc), cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
@@ -459,7 +647,8 @@ int dlbchem_create(const char* mech_path, const dlbchem_options* opt, dlbchem_ct
   c->wpc = o.team_warps ? o.team_warps : (c->hm.nsp + 1 <= 32 ? 1 : (c->hm.nsp + 1 <= 64 ? 2 : 4));
   std::vector<unsigned char> blob;
   if (!build_tables(c->hm, c->wpc, blob, c->dm, why)) { delete c; return fail(nullptr, DLBCHEM_BAD_MECH, why); }
-  c->L = make_layout(c->hm.nsp, c->dm.CH, c->dm.N, c->dm.ld, c->dm.DS, o.precision == 1);
+  c->L = make_layout(c->hm.nsp, c->hm.nrx, c->dm.CH, c->dm.N, c->dm.ld, c->dm.DS, o.precision == 1);
+  if (c->L.vv - c->L.wdot != c->dm.split_off) { delete c; return fail(nullptr, DLBCHEM_BAD_MECH, "internal: split accumulator offset"); }
   for (auto& ev : c->ev)
     if (cudaEventCreate(&ev) != cudaSuccess) { ev = nullptr; dlbchem_destroy(c); return fail(nullptr, DLBCHEM_CUDA, "cudaEventCreate failed"); }
   if (cudaMalloc(&c->d_blob, blob.size()) != cudaSuccess || cudaMalloc(&c->d_counter, 64) != cudaSuccess) {

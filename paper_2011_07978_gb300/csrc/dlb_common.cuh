@@ -44,8 +44,10 @@ static_assert(sizeof(RxnMeta) == 32, "RxnMeta layout");
 
 enum : uint8_t { RX_REV = 1, RX_TB = 2, RX_EFF = 4 };
 
-// Incidence entry (species k, reaction r, coefficient nu), packed:
-//   k in bits 20..31, r in bits 4..19, nu + 8 in bits 0..3.
+// Incidence entry (target slot k, reaction r, coefficient nu), packed:
+//   k in bits 20..31, r in bits 4..19, nu + 8 in bits 0..3. The target is a
+//   species index, or in the whole-mechanism rounds split_off + species for
+//   the second accumulator of a frequent species.
 __host__ __device__ inline uint32_t pack_inc(int k, int r, int nu) {
   return (uint32_t(k) << 20) | (uint32_t(r) << 4) | uint32_t(nu + 8);
 }
@@ -71,6 +73,13 @@ struct DevMech {
   const uint32_t* tri;
   const double* tri_coef;
   const int32_t* trip;
+  // Rate evaluations without the Jacobian take all reactions at once: rounds
+  // [incp_all[w], incp_all[w+1]) of warp w over global reaction indices.
+  // Species in more reactions than a round-balanced share are split over two
+  // accumulators (wdot and wdot + split_off), summed after the rounds.
+  const uint32_t* inc_all;
+  const int32_t* incp_all;
+  int nsplit, split_off;
   const double* exptab;   // 2^(j/64), j = 0..63 (staged into shared memory per CTA)
   const double* aW;       // [4][nsp] atoms of element e per gram of species k (a_ek / W_k)
 };
@@ -88,7 +97,7 @@ struct WsLayout {
   int total;  // doubles per team (int and float arrays are counted in doubles)
 };
 
-__host__ inline WsLayout make_layout(int nsp, int CH, int N, int ld, int DS, bool mixed) {
+__host__ inline WsLayout make_layout(int nsp, int nrx, int CH, int N, int ld, int DS, bool mixed) {
   WsLayout L;
   int o = 0;
   auto take = [&](int n) { int r = o; o += (n + 1) & ~1; return r; };  // keep 16-byte alignment
@@ -111,7 +120,7 @@ __host__ inline WsLayout make_layout(int nsp, int CH, int N, int ld, int DS, boo
   L.sig = take(CH);
   L.dqdT = take(CH);
   L.dlt = take(CH);
-  L.D = take(CH * DS);
+  L.D = take(CH * DS > nrx ? CH * DS : nrx);   // D slots of a chunk, or every reaction's rate
   L.scal = take(32);
   L.perm = take((N + 1) / 2 + 1);
   const int nm = mixed ? 1 : 0;

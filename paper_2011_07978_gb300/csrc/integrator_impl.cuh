@@ -96,6 +96,7 @@ struct WS {
   int* perm32;
   double *rr, *dx, *isc;
   const double* exptab;   // 64 entries of 2^(j/64), shared by the CTA
+  const double* nutab;    // nutab[j] = j - 8: stoichiometric coefficients by their 4-bit code
 };
 
 __device__ __forceinline__ WS carve(double* base, const WsLayout& L) {
@@ -113,7 +114,7 @@ __device__ __forceinline__ WS carve(double* base, const WsLayout& L) {
 
 // Mixture scalars shared by one rate evaluation.
 struct Mix {
-  double T, iT, lnT, S, rho, irho;
+  double T, iT, lnT, S, rho, irho, Ctot;
 };
 
 // exp(x) by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989):
@@ -125,7 +126,7 @@ struct Mix {
 // About 10 FP64 operations against ~19 for the library exp; |x| >= 700 and
 // NaN go to the library exp.
 __device__ __forceinline__ double exp_tab(double x, const double* __restrict__ tab) {
-  if (!(fabs(x) < 700.0)) return exp(x);
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x4085E000) return exp(x);   // |x| >= 700 or NaN (700 = 0x4085E000 00000000)
   const double kShift = 6755399441055744.0;                 // 1.5 * 2^52
   const double t = fma(x, 92.33248261689366, kShift);       // x * 64 / ln2, rounded to an integer
   const int ki = __double2loint(t);
@@ -153,28 +154,103 @@ __device__ __forceinline__ double rcp_nr(double d) {
 }
 
 // ---------------------------------------------------------------------------
-// Rates. Species pass: concentrations c_k = rho Y_k / W_k, E_k = exp(-g_k/RT)
-// and 1/E_k (equilibrium constants as products of per-species factors:
-// 1/K_c = prod_reac E^nu' prod_prod (1/E)^nu'' (R_c T / p0)^dnu), molar h_k.
+// Rates. Species pass: concentrations c_k = rho Y_k / W_k, E_k =
+// exp(-g_k/RT) p0/(R_c T) (the standard-state concentration folded in, so
+// 1/K_c = prod_reac E^nu' prod_prod (1/E)^nu'') and 1/E_k, molar h_k.
 // Reaction pass: k_f = exp(ln A + b ln T - Ea/(R T)), q = [M](fwd - rev).
 // With JAC, also d q / d c for each distinct participant (D slots), the
 // homogeneity sum sigma = sum_j c_j dq/dc_j, dq/dT at fixed c, and the
 // third-body difference fwd - rev. Then the incidence rounds gather
 // wdot_k = sum_r nu_kr q_r (and v, dwdT, u).
+// Without JAC all reactions go at once: q into the D region, then the
+// whole-mechanism rounds. With JAC the reactions go one chunk of CH (= team
+// size) at a time: rate pass, then the chunk's incidence rounds and its
+// Jacobian rounds into M.
 // ---------------------------------------------------------------------------
+template <bool JAC>
+__device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mix& mx, int r, int rl, double* qdst) {
+  const RxnMeta mt = m.meta[r];
+  const double kf = exp_tab(fma(m.beta[r], mx.lnT, fma(-m.EaR[r], mx.iT, m.lnA[r])), w.exptab);
+  // expanded slots as fixed registers (unused slots hold 1)
+  const double a0 = w.c[mt.sp[0]];
+  const double a1 = mt.nr > 1 ? w.c[mt.sp[1]] : 1.0;
+  const double a2 = mt.nr > 2 ? w.c[mt.sp[2]] : 1.0;
+  const double pf = kf * (a0 * (a1 * a2));
+  double pr = 0.0, kr = 0.0, b0 = 1.0, b1 = 1.0, b2 = 1.0;
+  if (mt.flags & RX_REV) {
+    const double e1 = mt.nr > 1 ? w.E[mt.sp[1]] : 1.0;
+    const double e2 = mt.nr > 2 ? w.E[mt.sp[2]] : 1.0;
+    const double i1 = mt.np > 1 ? w.Einv[mt.sp[4]] : 1.0;
+    const double i2 = mt.np > 2 ? w.Einv[mt.sp[5]] : 1.0;
+    kr = kf * ((w.E[mt.sp[0]] * (e1 * e2)) * (w.Einv[mt.sp[3]] * (i1 * i2)));
+    b0 = w.c[mt.sp[3]];
+    b1 = mt.np > 1 ? w.c[mt.sp[4]] : 1.0;
+    b2 = mt.np > 2 ? w.c[mt.sp[5]] : 1.0;
+    pr = kr * (b0 * (b1 * b2));
+  }
+  double Mf = 1.0;
+  if (mt.flags & RX_TB) {
+    Mf = mx.Ctot;
+    for (int e = mt.eff_begin; e < mt.eff_end; ++e) Mf = fma(m.eff_dm1[e], w.c[m.eff_sp[e]], Mf);
+  }
+  qdst[rl] = Mf * (pf - pr);
+  if (JAC) {
+    double* D = w.D + rl * m.DS;
+    for (int s2 = 0; s2 < mt.nds; ++s2) D[s2] = 0.0;
+    // d/dc_j of the slot product = product of the other slots
+    const double kfM = kf * Mf;
+    D[mt.ds[0]] += kfM * (a1 * a2);
+    if (mt.nr > 1) D[mt.ds[1]] += kfM * (a0 * a2);
+    if (mt.nr > 2) D[mt.ds[2]] += kfM * (a0 * a1);
+    if (mt.flags & RX_REV) {
+      const double krM = kr * Mf;
+      D[mt.ds[3]] -= krM * (b1 * b2);
+      if (mt.np > 1) D[mt.ds[4]] -= krM * (b0 * b2);
+      if (mt.np > 2) D[mt.ds[5]] -= krM * (b0 * b1);
+    }
+    const int tb = (mt.flags & RX_TB) ? 1 : 0;
+    if (mt.flags & RX_EFF) D[mt.dslot_eff] = pf - pr;
+    w.sig[rl] = Mf * ((mt.nr + tb) * pf - (mt.np + tb) * pr);
+    const double dlnkf = fma(m.EaR[r], mx.iT * mx.iT, m.beta[r] * mx.iT);
+    double dq = pf * dlnkf;
+    if (mt.flags & RX_REV) {
+      double dH = w.hk[mt.sp[3]] - w.hk[mt.sp[0]];
+      if (mt.np > 1) dH += w.hk[mt.sp[4]];
+      if (mt.np > 2) dH += w.hk[mt.sp[5]];
+      if (mt.nr > 1) dH -= w.hk[mt.sp[1]];
+      if (mt.nr > 2) dH -= w.hk[mt.sp[2]];
+      const double dlnKc = dH * mx.iT * mx.iT * (1.0 / kR) - mt.dnu * mx.iT;
+      dq -= pr * (dlnkf - dlnKc);
+    }
+    w.dqdT[rl] = Mf * dq;
+    w.dlt[rl] = tb ? (pf - pr) : 0.0;
+  }
+}
+
 template <int WPC, bool JAC>
 __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm, const WS& w, const double* yv,
-                                        double P1, Mix& mx) {
+                                        double P1, double iP1, Mix& mx) {
   constexpr int TS = 32 * WPC;
   const int nsp = m.nsp, nrx = m.nrx;
   const double T = yv[0];
-  const double iT = 1.0 / T;
-  const double lnT = log(T);
   double s = 0.0;
   for (int k = tm.tid; k < nsp; k += TS) s = fma(yv[1 + k], m.iW[k], s);
+  double iT, lnT;
+  if (WPC == 1) {
+    iT = 1.0 / T;
+    lnT = log(T);
+  } else {
+    // one warp takes ln T, another 1/T; both are published with the barrier
+    // of the sum below (slots 28, 29 of the team scratch)
+    if (tm.warp == 0) { if (tm.lane == 0) w.scal[28] = log(T); }
+    else if (tm.warp == 1) { if (tm.lane == 0) w.scal[29] = 1.0 / T; }
+  }
   const double S = tm.sum(s);
-  const double rho = P1 * iT / S;
-  mx.T = T; mx.iT = iT; mx.lnT = lnT; mx.S = S; mx.rho = rho; mx.irho = (T * S) / P1;
+  if (WPC > 1) { lnT = w.scal[28]; iT = w.scal[29]; }
+  const double irho = (T * S) * iP1;          // 1/rho = R T S / p
+  const double rho = rcp_nr(irho);
+  mx.T = T; mx.iT = iT; mx.lnT = lnT; mx.S = S; mx.rho = rho; mx.irho = irho;
+  mx.Ctot = P1 * iT;                          // sum_k c_k (unit efficiencies)
   for (int k = tm.tid; k < nsp; k += TS) {
     w.c[k] = rho * yv[1 + k] * m.iW[k];
     const double e = exp_tab(fma(m.G2[k], lnT, fma(m.G3[k], T, -fma(m.G0[k], iT, m.G1[k]))), w.exptab);
@@ -183,109 +259,54 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
     w.hk[k] = fma(T, fma(m.hcpb[k], T, m.cpa[k]), m.H0[k]);
   }
   if (tm.tid == 0) w.c[nsp] = 0.0;
-  tm.sync();
-  const double Ctot = P1 * iT;          // sum_k c_k (unit efficiencies)
-  const double C0inv = (kRc / 1.0) * T; // R_c T / p0, p0 = 1 atm
-  const double C0 = 1.0 / C0inv;
-  for (int k = tm.tid; k <= nsp; k += TS) {
-    w.wdot[k] = 0.0;
-    if (JAC) { w.vv[k] = 0.0; w.dwdT[k] = 0.0; w.uu[k] = 0.0; }
-  }
-  // reactions one chunk of CH (= team size) at a time: rate pass, then the
-  // chunk's conflict-free incidence rounds (and Jacobian rounds into M)
-  for (int c = 0; c < m.nchunks; ++c) {
-    const int c0 = c * m.CH;
-    const int r = c0 + tm.tid;
-    if (r < nrx) {
-    const int rl = tm.tid;
-    const RxnMeta mt = m.meta[r];
-    const double kf = exp_tab(fma(m.beta[r], lnT, fma(-m.EaR[r], iT, m.lnA[r])), w.exptab);
-    // expanded slots as fixed registers (unused slots hold 1)
-    const double a0 = w.c[mt.sp[0]];
-    const double a1 = mt.nr > 1 ? w.c[mt.sp[1]] : 1.0;
-    const double a2 = mt.nr > 2 ? w.c[mt.sp[2]] : 1.0;
-    double pf = kf * a0;
-    if (mt.nr > 1) pf *= a1;
-    if (mt.nr > 2) pf *= a2;
-    double pr = 0.0, kr = 0.0, b0 = 1.0, b1 = 1.0, b2 = 1.0;
-    if (mt.flags & RX_REV) {
-      kr = kf * w.E[mt.sp[0]];
-      if (mt.nr > 1) kr *= w.E[mt.sp[1]];
-      if (mt.nr > 2) kr *= w.E[mt.sp[2]];
-      kr *= w.Einv[mt.sp[3]];
-      if (mt.np > 1) kr *= w.Einv[mt.sp[4]];
-      if (mt.np > 2) kr *= w.Einv[mt.sp[5]];
-      if (mt.dnu > 0) { kr *= C0inv; if (mt.dnu > 1) kr *= C0inv; if (mt.dnu > 2) kr *= C0inv; }
-      if (mt.dnu < 0) { kr *= C0; if (mt.dnu < -1) kr *= C0; if (mt.dnu < -2) kr *= C0; }
-      b0 = w.c[mt.sp[3]];
-      b1 = mt.np > 1 ? w.c[mt.sp[4]] : 1.0;
-      b2 = mt.np > 2 ? w.c[mt.sp[5]] : 1.0;
-      pr = kr * b0;
-      if (mt.np > 1) pr *= b1;
-      if (mt.np > 2) pr *= b2;
-    }
-    double Mf = 1.0;
-    if (mt.flags & RX_TB) {
-      Mf = Ctot;
-      for (int e = mt.eff_begin; e < mt.eff_end; ++e) Mf = fma(m.eff_dm1[e], w.c[m.eff_sp[e]], Mf);
-    }
-    w.q[rl] = Mf * (pf - pr);
-    if (JAC) {
-      double* D = w.D + rl * m.DS;
-      for (int s2 = 0; s2 < mt.nds; ++s2) D[s2] = 0.0;
-      // d/dc_j of the slot product = product of the other slots
-      const double kfM = kf * Mf;
-      D[mt.ds[0]] += kfM * (a1 * a2);
-      if (mt.nr > 1) D[mt.ds[1]] += kfM * (a0 * a2);
-      if (mt.nr > 2) D[mt.ds[2]] += kfM * (a0 * a1);
-      if (mt.flags & RX_REV) {
-        const double krM = kr * Mf;
-        D[mt.ds[3]] -= krM * (b1 * b2);
-        if (mt.np > 1) D[mt.ds[4]] -= krM * (b0 * b2);
-        if (mt.np > 2) D[mt.ds[5]] -= krM * (b0 * b1);
-      }
-      const int tb = (mt.flags & RX_TB) ? 1 : 0;
-      if (mt.flags & RX_EFF) D[mt.dslot_eff] = pf - pr;
-      w.sig[rl] = Mf * ((mt.nr + tb) * pf - (mt.np + tb) * pr);
-      const double dlnkf = fma(m.EaR[r], iT * iT, m.beta[r] * iT);
-      double dq = pf * dlnkf;
-      if (mt.flags & RX_REV) {
-        double dH = w.hk[mt.sp[3]] - w.hk[mt.sp[0]];
-        if (mt.np > 1) dH += w.hk[mt.sp[4]];
-        if (mt.np > 2) dH += w.hk[mt.sp[5]];
-        if (mt.nr > 1) dH -= w.hk[mt.sp[1]];
-        if (mt.nr > 2) dH -= w.hk[mt.sp[2]];
-        const double dlnKc = dH * iT * iT * (1.0 / kR) - mt.dnu * iT;
-        dq -= pr * (dlnkf - dlnKc);
-      }
-      w.dqdT[rl] = Mf * dq;
-      w.dlt[rl] = tb ? (pf - pr) : 0.0;
-    }
+  if (!JAC) {
+    for (int k = tm.tid; k <= nsp; k += TS) {
+      w.wdot[k] = 0.0;
+      if (m.nsplit) w.vv[k] = 0.0;
     }
     tm.sync();
-    const int ci = c * m.wpc + tm.warp;
-    const int r0 = m.incp[ci], r1 = m.incp[ci + 1];
-    for (int rd = r0; rd < r1; ++rd) {
-      const uint32_t e = m.inc[rd * 32 + tm.lane];
+    double* qa = w.D;
+    for (int r = tm.tid; r < nrx; r += TS) reaction<false>(m, w, mx, r, r, qa);
+    tm.sync();
+    for (int rd = m.incp_all[tm.warp], r1 = m.incp_all[tm.warp + 1]; rd < r1; ++rd) {
+      const uint32_t e = m.inc_all[rd * 32 + tm.lane];
       const int k = int(e >> 20), rr = int((e >> 4) & 0xffffu);
-      const double nu = double(int(e & 15u) - 8);
-      w.wdot[k] = fma(nu, w.q[rr], w.wdot[k]);
-      if (JAC) {
-        w.vv[k] = fma(nu, w.sig[rr], w.vv[k]);
-        w.dwdT[k] = fma(nu, w.dqdT[rr], w.dwdT[k]);
-        w.uu[k] = fma(nu, w.dlt[rr], w.uu[k]);
-      }
+      w.wdot[k] = fma(w.nutab[e & 15u], qa[rr], w.wdot[k]);
       __syncwarp();
     }
-    if (JAC) {
-      const int t0 = m.trip[ci], t1 = m.trip[ci + 1];
-      for (int rd = t0; rd < t1; ++rd) {
-        const uint32_t e = m.tri[rd * 32 + tm.lane];
-        const double cf = m.tri_coef[rd * 32 + tm.lane];
-        const int tgt = int(e >> 16), d = int(e & 0xffffu);
-        w.M[tgt] = fma(cf, w.D[d], w.M[tgt]);
-        __syncwarp();
-      }
+    tm.sync();
+    if (m.nsplit) {
+      for (int k = tm.tid; k < nsp; k += TS) w.wdot[k] += w.vv[k];
+      tm.sync();
+    }
+    return;
+  }
+  for (int k = tm.tid; k <= nsp; k += TS) {
+    w.wdot[k] = 0.0;
+    w.vv[k] = 0.0; w.dwdT[k] = 0.0; w.uu[k] = 0.0;
+  }
+  tm.sync();
+  for (int c = 0; c < m.nchunks; ++c) {
+    const int r = c * m.CH + tm.tid;
+    if (r < nrx) reaction<true>(m, w, mx, r, tm.tid, w.q);
+    tm.sync();
+    const int ci = c * m.wpc + tm.warp;
+    for (int rd = m.incp[ci], r1 = m.incp[ci + 1]; rd < r1; ++rd) {
+      const uint32_t e = m.inc[rd * 32 + tm.lane];
+      const int k = int(e >> 20), rr = int((e >> 4) & 0xffffu);
+      const double nu = w.nutab[e & 15u];
+      w.wdot[k] = fma(nu, w.q[rr], w.wdot[k]);
+      w.vv[k] = fma(nu, w.sig[rr], w.vv[k]);
+      w.dwdT[k] = fma(nu, w.dqdT[rr], w.dwdT[k]);
+      w.uu[k] = fma(nu, w.dlt[rr], w.uu[k]);
+      __syncwarp();
+    }
+    for (int rd = m.trip[ci], t1 = m.trip[ci + 1]; rd < t1; ++rd) {
+      const uint32_t e = m.tri[rd * 32 + tm.lane];
+      const double cf = m.tri_coef[rd * 32 + tm.lane];
+      const int tgt = int(e >> 16), d = int(e & 0xffffu);
+      w.M[tgt] = fma(cf, w.D[d], w.M[tgt]);
+      __syncwarp();
     }
     tm.sync();
   }
@@ -311,9 +332,9 @@ __device__ __forceinline__ void finish_f(const DevMech& m, const Team<WPC>& tm, 
 
 template <int WPC>
 __device__ __forceinline__ void eval_f(const DevMech& m, const Team<WPC>& tm, const WS& w, const double* yv,
-                                       double P1, bool iso, double* f) {
+                                       double P1, double iP1, bool iso, double* f) {
   Mix mx;
-  eval_rates<WPC, false>(m, tm, w, yv, P1, mx);
+  eval_rates<WPC, false>(m, tm, w, yv, P1, iP1, mx);
   double Q, cpm;
   finish_f<WPC>(m, tm, w, yv, mx, iso, f, Q, cpm);
 }
@@ -329,7 +350,7 @@ __device__ __forceinline__ void eval_f(const DevMech& m, const Team<WPC>& tm, co
 // rho(T, Y).
 // ---------------------------------------------------------------------------
 template <int WPC>
-__device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, const WS& w, double P1, bool iso,
+__device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, const WS& w, double P1, double iP1, bool iso,
                                       double ihg) {
   constexpr int TS = 32 * WPC;
   const int nsp = m.nsp, N = m.N, ld = m.ld;
@@ -337,7 +358,7 @@ __device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, 
   for (int i = tm.tid; i < ntot; i += TS) w.M[i] = 0.0;   // the Jacobian rounds accumulate into M
   tm.sync();
   Mix mx;
-  eval_rates<WPC, true>(m, tm, w, w.y0, P1, mx);
+  eval_rates<WPC, true>(m, tm, w, w.y0, P1, iP1, mx);
   double Q, cpm;
   finish_f<WPC>(m, tm, w, w.y0, mx, iso, w.f0, Q, cpm);
   // scalars for the T row / column
@@ -460,7 +481,7 @@ __device__ __forceinline__ bool lu_factor(const Team<WPC>& tm, R* M, int N, int 
     }
     tm.sync();
     const R d = M[k * ld + k];
-    if (d == R(0)) singular = true;
+    if (best == 0ull) singular = true;   // largest |M_ik| is zero
     if (tm.warp == 0) {           // one warp takes the reciprocal and the column
       const R inv = rcp_any(d);
       if (tm.lane == 0) invd[k] = inv;
@@ -624,7 +645,7 @@ __device__ __forceinline__ double wrms(const Team<WPC>& tm, const double* v, con
 // order-3 error exponent 1/4 and fallbacks scaled by dt. Uses ys, fs, u.
 template <int WPC>
 __device__ double initial_step(const DevMech& m, const Team<WPC>& tm, const WS& w, const IntegParams& P,
-                               double P1, bool iso) {
+                               double P1, double iP1, bool iso) {
   constexpr int TS = 32 * WPC;
   const int N = m.N;
   double* sc = w.u;
@@ -635,7 +656,7 @@ __device__ double initial_step(const DevMech& m, const Team<WPC>& tm, const WS& 
   h0 = fmin(h0, P.dt);
   for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(h0, w.f0[i], w.y0[i]);
   tm.sync();
-  eval_f<WPC>(m, tm, w, w.ys, P1, iso, w.fs);
+  eval_f<WPC>(m, tm, w, w.ys, P1, iP1, iso, w.fs);
   double* df = w.u + N;
   for (int i = tm.tid; i < N; i += TS) df[i] = w.fs[i] - w.f0[i];
   tm.sync();
@@ -665,9 +686,10 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
   bad = tm.any(bad);
   int status = CELL_OK, steps = 0;
   if (!bad) {
-    const double P1 = 1e-6 * p / kR;
-    eval_f<WPC>(m, tm, w, w.y0, P1, iso, w.f0);
-    double h = initial_step<WPC>(m, tm, w, P, P1, iso);
+    const double P1 = 1e-6 * p / kR;   // p / (R T) = P1 / T in mol/cm^3
+    const double iP1 = 1.0 / P1;
+    eval_f<WPC>(m, tm, w, w.y0, P1, iP1, iso, w.f0);
+    double h = initial_step<WPC>(m, tm, w, P, P1, iP1, iso);
     const double dt = P.dt;
     double t = 0.0;
     bool rejected_last = false;
@@ -681,7 +703,7 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
       if (h < P.hmin_frac * dt) { status = CELL_H_UNDERFLOW; break; }
       ++steps;
       const double ih = 1.0 / h;
-      assemble<WPC>(m, tm, w, P1, iso, ih * (1.0 / kGamma));
+      assemble<WPC>(m, tm, w, P1, iP1, iso, ih * (1.0 / kGamma));
       bool mixed = P.precision == 1;
       bool ok;
       if (mixed) {
@@ -704,14 +726,14 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
         // stage 2
         for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(kA21, u1[i], w.y0[i]);
         tm.sync();
-        eval_f<WPC>(m, tm, w, w.ys, P1, iso, w.fs);
+        eval_f<WPC>(m, tm, w, w.ys, P1, iP1, iso, w.fs);
         for (int i = tm.tid; i < N; i += TS) w.fs[i] = fma(kC21 * ih, u1[i], w.fs[i]);
         tm.sync();
         solve(w.fs, u2);
         // stage 3
         for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(kA31, u1[i], fma(kA32, u2[i], w.y0[i]));
         tm.sync();
-        eval_f<WPC>(m, tm, w, w.ys, P1, iso, w.fs);
+        eval_f<WPC>(m, tm, w, w.ys, P1, iP1, iso, w.fs);
         for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(ih, fma(kC31, u1[i], kC32 * u2[i]), w.fs[i]);
         tm.sync();
         solve(w.ys, u3);
@@ -780,10 +802,12 @@ __global__ void __launch_bounds__(128, WPC == 1 ? 4 : (WPC == 2 ? 3 : 2)) rosenb
   tm.parity = 0;
   double* tab = smem + size_t(teams) * a.L.total;
   for (int j = threadIdx.x; j < 64; j += blockDim.x) tab[j] = a.m.exptab[j];
+  for (int j = threadIdx.x; j < 16; j += blockDim.x) tab[64 + j] = double(j - 8);
   __syncthreads();
   double* base = smem + size_t(team) * a.L.total;
   WS w = carve(base, a.L);
   w.exptab = tab;
+  w.nutab = tab + 64;
   tm.red = w.scal;
   const int64_t nq = a.nqueue ? *a.nqueue : a.n;
   // one work-list entry -> (arrays, cell, dt)
@@ -842,9 +866,11 @@ __global__ void __launch_bounds__(128) gate_kernel(const GateArgs a) {
   tm.parity = 0;
   double* tab = smem + size_t(teams) * a.L.total;
   for (int j = threadIdx.x; j < 64; j += blockDim.x) tab[j] = a.m.exptab[j];
+  for (int j = threadIdx.x; j < 16; j += blockDim.x) tab[64 + j] = double(j - 8);
   __syncthreads();
   WS w = carve(smem + size_t(team) * a.L.total, a.L);
   w.exptab = tab;
+  w.nutab = tab + 64;
   tm.red = w.scal;
   const DevMech& m = a.m;
   const int N = m.N, nsp = m.nsp;
@@ -864,8 +890,9 @@ __global__ void __launch_bounds__(128) gate_kernel(const GateArgs a) {
     bad |= !(w.y0[0] > 0.0) || !(w.ys[0] > 0.0) || !(p > 0.0);
     if (tm.any(bad)) continue;
     const double P1 = 1e-6 * p / kR;
-    eval_f<WPC>(m, tm, w, w.y0, P1, a.P.isothermal != 0, w.f0);
-    eval_f<WPC>(m, tm, w, w.ys, P1, a.P.isothermal != 0, w.fs);
+    const double iP1 = 1.0 / P1;
+    eval_f<WPC>(m, tm, w, w.y0, P1, iP1, a.P.isothermal != 0, w.f0);
+    eval_f<WPC>(m, tm, w, w.ys, P1, iP1, a.P.isothermal != 0, w.fs);
     const double hdt = 0.5 * a.P.dt;
     double dY = 0.0, sumY = 0.0, e0 = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0, t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
     for (int i = tm.tid; i < N; i += TS) {

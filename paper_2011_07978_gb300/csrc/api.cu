@@ -660,6 +660,14 @@ int dlbchem_create(const char* mech_path, const dlbchem_options* opt, dlbchem_ct
   relocate(c->dm, c->d_blob);
   int rc = configure_launch(c);
   if (rc != DLBCHEM_OK) { std::string m = c->err; dlbchem_destroy(c); return fail(nullptr, rc, m); }
+  if (o.precision == 1) {
+    const size_t slots = size_t(c->num_sms) * c->blocks_per_sm * c->teams;
+    if (cudaMalloc(&c->d_m64, slots * c->dm.N * c->dm.N * sizeof(double)) != cudaSuccess) {
+      c->d_m64 = nullptr;
+      dlbchem_destroy(c);
+      return fail(nullptr, DLBCHEM_OOM, "device allocation of the mixed-precision matrix copies failed");
+    }
+  }
   *out = c;
   return DLBCHEM_OK;
 }
@@ -748,6 +756,7 @@ int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, con
   a.L = c->L;
   a.n = n; a.T = T; a.p = p; a.Y = Y; a.Tout = T_out; a.Yout = Y_out; a.steps = steps; a.status = status;
   a.fallbacks = c->d_counter + 2;
+  a.m64 = c->opt.precision == 1 ? c->d_m64 : nullptr;
   if (c->opt.precision == 1 && (e = cudaMemsetAsync(c->d_counter + 2, 0, 8, s)) != cudaSuccess)
     return cuda_fail(c, e, "cudaMemsetAsync");
   const bool listed = mapping || queue || surrogate || predictor;
@@ -755,7 +764,7 @@ int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, con
   a.nqueue = listed ? c->w_total : nullptr;
   const int threads = 32 * c->wpc * c->teams;
   int64_t grid = (n + c->teams - 1) / c->teams;
-  if (queue) {
+  if (queue || c->opt.precision == 1) {   // mixed precision indexes per-team scratch: persistent teams
     e = cudaMemsetAsync(c->d_counter, 0, 8, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
     a.queue = 1; a.counter = c->d_counter; a.chunk = c->opt.chunk;
@@ -917,6 +926,7 @@ void dlbchem_destroy(dlbchem_ctx* c) {
   if (c->d_blob) cudaFree(c->d_blob);
   if (c->d_counter) cudaFree(c->d_counter);
   if (c->d_ws) cudaFree(c->d_ws);
+  if (c->d_m64) cudaFree(c->d_m64);
   if (c->d_learn) cudaFree(c->d_learn);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);

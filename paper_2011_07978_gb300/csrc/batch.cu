@@ -147,6 +147,7 @@ cudaError_t enqueue_class(dlbchem_batch* b, dlbchem_batch::Class& c, cudaStream_
   }
   a.perm = c.list; a.nqueue = c.d_total; a.queue = 1; a.counter = c.counter; a.chunk = chunk;
   a.fallbacks = nullptr;
+  a.m64 = x->opt.precision == 1 ? x->d_m64 : nullptr;
   cudaError_t e = cudaSuccess;
   if (md_override) {   // tuning runs use host-built tables
     std::vector<int64_t> off(nm);

@@ -123,13 +123,29 @@ __host__ inline WsLayout make_layout(int nsp, int nrx, int CH, int N, int ld, in
   L.D = take(CH * DS > nrx ? CH * DS : nrx);   // D slots of a chunk, or every reaction's rate
   L.scal = take(32);
   L.perm = take((N + 1) / 2 + 1);
-  const int nm = mixed ? 1 : 0;
-  L.M32 = take(nm * ((N * ld + 1) / 2 + 1));
-  L.invd32 = take(nm * ((N + 1) / 2 + 1));
-  L.perm32 = take(nm * ((N + 1) / 2 + 1));
-  L.rr = take(nm * N);
-  L.dx = take(nm * N);
-  L.isc = take(nm * N);
+  L.M32 = L.invd32 = L.perm32 = L.rr = L.dx = L.isc = 0;
+  if (mixed) {
+    // FP32 factors over the first half of M (the FP64 matrix is kept in a
+    // global per-team scratch); pivots and refinement vectors over the
+    // Jacobian-only arrays dwdT .. dlt, dead from the factorisation to the
+    // next assembly (appended if they do not fit)
+    L.M32 = L.M;
+    int o2 = L.dwdT;
+    const int end2 = L.D;
+    auto take2 = [&](int n) { int r = o2; o2 += (n + 1) & ~1; return r; };
+    L.invd32 = take2((N + 1) / 2 + 1);
+    L.perm32 = take2((N + 1) / 2 + 1);
+    L.rr = take2(N);
+    L.dx = take2(N);
+    L.isc = take2(N);
+    if (o2 > end2) {
+      L.invd32 = take((N + 1) / 2 + 1);
+      L.perm32 = take((N + 1) / 2 + 1);
+      L.rr = take(N);
+      L.dx = take(N);
+      L.isc = take(N);
+    }
+  }
   L.total = o;
   return L;
 }
@@ -171,6 +187,9 @@ struct KernelArgs {
   int chunk;
   int queue;
   unsigned long long* fallbacks;   // steps whose FP32 refinement fell back to the FP64 LU
+  // mixed precision: per-team FP64 matrices (N*N doubles each, transposed),
+  // indexed by blockIdx.x * teams + team; launches are then persistent
+  double* m64;
   // batched launch (nmesh > 0): work-list entries are (mesh << kMeshShift) | cell
   // and each mesh brings its own arrays and dt; the single-mesh fields above
   // are then unused.

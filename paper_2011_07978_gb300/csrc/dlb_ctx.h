@@ -43,6 +43,7 @@ struct dlbchem_ctx {
   // workspace (grown on demand to the largest ncells seen)
   unsigned long long* d_counter = nullptr;   // queue counter (8 B) + reference index (8 B)
   void* d_ws = nullptr;
+  double* d_m64 = nullptr;   // mixed precision: per-team FP64 matrix copies (resident teams x N^2)
   int64_t ws_cap = 0;
   uint8_t* w_flag = nullptr;
   double* w_ref_state = nullptr;

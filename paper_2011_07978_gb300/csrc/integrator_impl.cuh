@@ -97,6 +97,7 @@ struct WS {
   double *rr, *dx, *isc;
   const double* exptab;   // 64 entries of 2^(j/64), shared by the CTA
   const double* nutab;    // nutab[j] = j - 8: stoichiometric coefficients by their 4-bit code
+  double* g;              // mixed precision: this team's FP64 matrix, transposed (global, L2-resident)
 };
 
 __device__ __forceinline__ WS carve(double* base, const WsLayout& L) {
@@ -597,28 +598,29 @@ __device__ __forceinline__ void lu_solve(const Team<WPC>& tm, const R* M, int N,
 }
 
 // Mixed precision: x = M^-1 b with the FP32 factors of M, refined in FP64.
-// Each round takes the FP64 residual r = b - M x against the unfactored M,
-// solves for the correction with the FP32 factors and adds it; it stops when
-// the correction is below 1e-6 of the error-norm weights sc (isc = 1/sc) and
-// gives up after three rounds. Returns false if it did not converge.
+// Each round takes the FP64 residual r = b - M x against the unfactored M
+// (here its transposed copy gT, gT[j*N + i] = M_ij, so a warp's loads of one
+// column are contiguous), solves for the correction with the FP32 factors
+// and adds it; it stops when the correction is below 1e-6 of the error-norm
+// weights sc (isc = 1/sc) and gives up after three rounds. Returns false if
+// it did not converge.
 template <int WPC>
-__device__ __forceinline__ bool solve_refined(const Team<WPC>& tm, const double* M, const float* M32, int N, int ld,
-                                              const float* invd32, const int* perm32, const double* b, double* x,
-                                              double* r, double* dx, const double* isc) {
+__device__ __forceinline__ bool solve_refined(const Team<WPC>& tm, const double* __restrict__ gT, const float* M32,
+                                              int N, int ld, const float* invd32, const int* perm32,
+                                              const double* b, double* x, double* r, double* dx, const double* isc) {
   constexpr int TS = 32 * WPC;
   lu_solve<WPC, float>(tm, M32, N, ld, invd32, perm32, b, x);
   for (int it = 0; it < 3; ++it) {
     for (int i = tm.tid; i < N; i += TS) {
-      const double* row = M + i * ld;
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
       int j = 0;
       for (; j + 3 < N; j += 4) {
-        s0 = fma(row[j], x[j], s0);
-        s1 = fma(row[j + 1], x[j + 1], s1);
-        s2 = fma(row[j + 2], x[j + 2], s2);
-        s3 = fma(row[j + 3], x[j + 3], s3);
+        s0 = fma(gT[j * N + i], x[j], s0);
+        s1 = fma(gT[(j + 1) * N + i], x[j + 1], s1);
+        s2 = fma(gT[(j + 2) * N + i], x[j + 2], s2);
+        s3 = fma(gT[(j + 3) * N + i], x[j + 3], s3);
       }
-      for (; j < N; ++j) s0 = fma(row[j], x[j], s0);
+      for (; j < N; ++j) s0 = fma(gT[j * N + i], x[j], s0);
       r[i] = b[i] - ((s0 + s1) + (s2 + s3));
     }
     tm.sync();
@@ -631,6 +633,36 @@ __device__ __forceinline__ bool solve_refined(const Team<WPC>& tm, const double*
     if (!tm.any(big)) return true;
   }
   return false;
+}
+
+// double -> float by truncating the significand (integer operations only;
+// the FP32 matrix is a preconditioner, so rounding toward zero is enough).
+// Magnitudes below the FP32 normal range flush to zero, above it saturate at
+// the largest float; NaN and infinity stay NaN and infinity.
+__device__ __forceinline__ float trunc_to_float(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = unsigned(b >> 32) & 0x80000000u;
+  const int ex = int((b >> 52) & 0x7ff);
+  const unsigned man = unsigned((b >> 29) & 0x7fffffu);
+  unsigned f;
+  if (ex == 0x7ff) f = 0x7f800000u | man | (man == 0u && (b & 0xfffffffffffffull) ? 1u : 0u);
+  else if (ex - 1023 + 127 >= 255) f = 0x7f7fffffu;
+  else if (ex - 1023 + 127 <= 0) f = 0u;
+  else f = (unsigned(ex - 1023 + 127) << 23) | man;
+  return __uint_as_float(sign | f);
+}
+
+// Walk the N x N elements e = t, t + TS, ... as (i, j) = (e % N, e / N)
+// with incremental indices (no division per element).
+template <int TS, class F>
+__device__ __forceinline__ void for_each_ij(int tid, int N, F&& f) {
+  const int di = TS % N, dj = TS / N;
+  int i = tid % N, j = tid / N;
+  for (int e = tid; e < N * N; e += TS) {
+    f(e, i, j);
+    i += di; j += dj;
+    if (i >= N) { i -= N; ++j; }
+  }
 }
 
 // weighted RMS norm sqrt(sum (v/sc)^2 / N) over a team vector
@@ -704,21 +736,30 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
       ++steps;
       const double ih = 1.0 / h;
       assemble<WPC>(m, tm, w, P1, iP1, iso, ih * (1.0 / kGamma));
-      bool mixed = P.precision == 1;
+      bool mixed = P.precision == 1 && w.g != nullptr;   // no scratch: FP64
       bool ok;
+      const int ld = m.ld;
+      // mixed: M goes, transposed, to the team's global copy, and its FP32
+      // truncation over M's first half is factorised in shared memory;
+      // restore() brings the FP64 matrix back for the FP64 fallback
+      auto restore = [&]() {
+        for_each_ij<TS>(tm.tid, N, [&](int e, int i, int j) { w.M[i * ld + j] = w.g[e]; });
+        tm.sync();
+      };
       if (mixed) {
-        const int nm = N * m.ld;
-        for (int i = tm.tid; i < nm; i += TS) w.M32[i] = float(w.M[i]);
+        for_each_ij<TS>(tm.tid, N, [&](int e, int i, int j) { w.g[j * N + i] = w.M[i * ld + j]; });
         for (int i = tm.tid; i < N; i += TS) w.isc[i] = rcp_nr(fma(P.rtol, fabs(w.y0[i]), P.atol));
         tm.sync();
-        ok = lu_factor<WPC, float>(tm, w.M32, N, m.ld, w.invd32, w.perm32);
-        if (!ok) mixed = false;
+        for_each_ij<TS>(tm.tid, N, [&](int e, int i, int j) { w.M32[i * ld + j] = trunc_to_float(w.g[j * N + i]); });
+        tm.sync();
+        ok = lu_factor<WPC, float>(tm, w.M32, N, ld, w.invd32, w.perm32);
+        if (!ok) { mixed = false; restore(); }
       }
-      if (!mixed) ok = lu_factor<WPC, double>(tm, w.M, N, m.ld, w.invd, w.perm);
+      if (!mixed) ok = lu_factor<WPC, double>(tm, w.M, N, ld, w.invd, w.perm);
       for (int attempt = 0; attempt < 2; ++attempt) {
         bool conv = true;
         auto solve = [&](const double* b, double* x) {
-          if (mixed) conv &= solve_refined<WPC>(tm, w.M, w.M32, N, m.ld, w.invd32, w.perm32, b, x, w.rr, w.dx, w.isc);
+          if (mixed) conv &= solve_refined<WPC>(tm, w.g, w.M32, N, ld, w.invd32, w.perm32, b, x, w.rr, w.dx, w.isc);
           else lu_solve<WPC, double>(tm, w.M, N, m.ld, w.invd, w.perm, b, x);
         };
         // stage 1
@@ -743,10 +784,11 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
         tm.sync();
         solve(w.ys, u4);
         if (!mixed || conv) break;
-        // refinement did not converge: redo the stages with the FP64 LU (M is intact)
+        // refinement did not converge: redo the stages with the FP64 LU of the kept matrix
         mixed = false;
         if (tm.tid == 0 && fallbacks) atomicAdd(fallbacks, 1ull);
-        ok = lu_factor<WPC, double>(tm, w.M, N, m.ld, w.invd, w.perm);
+        restore();
+        ok = lu_factor<WPC, double>(tm, w.M, N, ld, w.invd, w.perm);
       }
       // new state (ys) and error estimate
       double acc = 0.0;
@@ -808,6 +850,7 @@ __global__ void __launch_bounds__(128, WPC == 1 ? 4 : (WPC == 2 ? 3 : 2)) rosenb
   WS w = carve(base, a.L);
   w.exptab = tab;
   w.nutab = tab + 64;
+  w.g = a.m64 ? a.m64 + (size_t(blockIdx.x) * teams + team) * size_t(a.m.N) * a.m.N : nullptr;
   tm.red = w.scal;
   const int64_t nq = a.nqueue ? *a.nqueue : a.n;
   // one work-list entry -> (arrays, cell, dt)
@@ -826,20 +869,27 @@ __global__ void __launch_bounds__(128, WPC == 1 ? 4 : (WPC == 2 ? 3 : 2)) rosenb
     integrate_cell<WPC>(a.m, P, tm, w, cell, md.n, md.T, md.p, md.Y, md.Tout, md.Yout, md.steps, md.status,
                         a.fallbacks);
   };
-  if (!a.queue) {
-    const int64_t j = int64_t(blockIdx.x) * teams + team;
-    if (j < nq) run(a.perm ? int64_t(a.perm[j]) : j);
-    return;
-  }
+  // One call site of run() for both schedules: a second inlined copy of the
+  // integrator may contract a*b + c into FMAs differently, and plain and
+  // queued runs are meant to give bit-identical results.
   volatile int64_t* slot = reinterpret_cast<volatile int64_t*>(w.scal + 24);
+  bool once = !a.queue;
   for (;;) {
-    if (tm.tid == 0) *slot = int64_t(atomicAdd(a.counter, (unsigned long long)a.chunk));
-    tm.sync();
-    const int64_t first = *slot;
-    tm.sync();
+    int64_t first, last;
+    if (once) {
+      first = int64_t(blockIdx.x) * teams + team;
+      last = first + 1;
+    } else {
+      if (tm.tid == 0) *slot = int64_t(atomicAdd(a.counter, (unsigned long long)a.chunk));
+      tm.sync();
+      first = *slot;
+      tm.sync();
+      last = first + int64_t(a.chunk);
+    }
     if (first >= nq) break;
-    const int64_t last = min(first + int64_t(a.chunk), nq);
-    for (int64_t qi = first; qi < last; ++qi) run(int64_t(a.perm[qi]));
+    last = min(last, nq);
+    for (int64_t qi = first; qi < last; ++qi) run(a.perm ? int64_t(a.perm[qi]) : qi);
+    if (once) break;
   }
 }
 

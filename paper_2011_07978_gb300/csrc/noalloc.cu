@@ -111,6 +111,7 @@ extern "C" int dlbchem_integrate_static(dlbchem_ctx* c, int64_t n, double dt, co
   a.L = c->L;
   a.n = n; a.T = T; a.p = p; a.Y = Y; a.Tout = T_out; a.Yout = Y_out; a.steps = steps; a.status = status;
   a.perm = list; a.nqueue = total; a.queue = 1; a.counter = counter; a.chunk = c->opt.chunk;
+  a.m64 = c->opt.precision == 1 ? c->d_m64 : nullptr;   // allocated once, at creation
   int64_t grid = (n + c->teams - 1) / c->teams;
   if (grid > int64_t(c->num_sms) * c->blocks_per_sm) grid = int64_t(c->num_sms) * c->blocks_per_sm;
   e = dlb::launch_rosenbrock(c->wpc, unsigned(grid), 32 * c->wpc * c->teams, c->smem_bytes, s, a);

@@ -74,6 +74,19 @@ struct Team {
     for (int w = 1; w < WPC; ++w) s = fmax(s, buf[w]);
     return s;
   }
+  // Team maxima of two unsigned keys (every thread receives both).
+  __device__ __forceinline__ void umax2(unsigned& a, unsigned& b) const {
+    a = __reduce_max_sync(0xffffffffu, a);
+    b = __reduce_max_sync(0xffffffffu, b);
+    if (WPC == 1) return;
+    double* buf = red + parity * WPC;
+    parity ^= 1;
+    unsigned* ub = reinterpret_cast<unsigned*>(buf);
+    if (lane == 0) { ub[2 * warp] = a; ub[2 * warp + 1] = b; }
+    sync();
+#pragma unroll
+    for (int w = 0; w < WPC; ++w) { a = max(a, ub[2 * w]); b = max(b, ub[2 * w + 1]); }
+  }
   __device__ __forceinline__ int any(int x) const {
     x = __any_sync(0xffffffffu, x);
     if (WPC == 1) return x;
@@ -510,6 +523,80 @@ __device__ __forceinline__ bool lu_factor(const Team<WPC>& tm, R* M, int N, int 
   return !singular;
 }
 
+// One-warp FP32 LU of the mixed-precision path (N <= 128), in the factor
+// format of lu_factor: unit L below the diagonal, inverse pivots in invd,
+// each row of U scaled by its inverse pivot one step after it is used. The
+// flattened update above keeps every FP64 lane busy; in FP32 the update is
+// latency-bound instead, so here each lane owns one or two columns of the
+// trailing block, keeps its pivot-row entries in registers and walks the rows
+// (a row's multiplier is one broadcast load). The pivot is a largest |M_ik|
+// to within 2^-16 relative: the 32-bit key is |M_ik| with its 7 low bits
+// replaced by 127 - i, one warp max finds it and ties go to the lower row.
+// Returns false if the pivot is zero (or below the key's resolution).
+__device__ __forceinline__ bool lu32_warp(float* M, int N, int ld, float* invd, int* perm, int lane) {
+  for (int i = lane; i < N; i += 32) perm[i] = i;
+  __syncwarp();
+  bool singular = false;
+  for (int k = 0; k < N; ++k) {
+    if (k > 0) {
+      const float iv = invd[k - 1];
+      for (int j = k + lane; j < N; j += 32) M[(k - 1) * ld + j] *= iv;
+    }
+    unsigned best = 0u;
+    for (int i = k + lane; i < N; i += 32)
+      best = max(best, (__float_as_uint(M[i * ld + k]) & 0x7fffff80u) | unsigned(127 - i));
+    best = __reduce_max_sync(0xffffffffu, best);
+    const int bi = 127 - int(best & 127u);
+    if ((best >> 7) == 0u) singular = true;
+    if (bi != k) {
+      for (int j = lane; j < N; j += 32) {
+        const float a = M[k * ld + j];
+        M[k * ld + j] = M[bi * ld + j];
+        M[bi * ld + j] = a;
+      }
+      if (lane == 0) { const int t = perm[k]; perm[k] = perm[bi]; perm[bi] = t; }
+    }
+    __syncwarp();
+    const float inv = __frcp_rn(M[k * ld + k]);
+    if (lane == 0) invd[k] = inv;
+    for (int i = k + 1 + lane; i < N; i += 32) M[i * ld + k] *= inv;
+    __syncwarp();
+    const int j0 = k + 1 + lane, j1 = j0 + 32;
+    const bool c0 = j0 < N, c1 = j1 < N;
+    const float u0 = c0 ? M[k * ld + j0] : 0.f;
+    const float u1 = c1 ? M[k * ld + j1] : 0.f;
+    // rows four at a time, all loads before the stores: the compiler cannot
+    // tell that rows do not overlap, so this is what keeps four rows in flight
+    const int jj0 = c0 ? j0 : k, jj1 = c1 ? j1 : k;   // idle lanes read column k, write nothing
+    int i = k + 1;
+    for (; i + 3 < N; i += 4) {
+      float* r0 = M + i * ld;
+      float* r1 = r0 + ld;
+      float* r2 = r1 + ld;
+      float* r3 = r2 + ld;
+      const float a0 = r0[k], a1 = r1[k], a2 = r2[k], a3 = r3[k];
+      const float p0 = r0[jj0], p1 = r1[jj0], p2 = r2[jj0], p3 = r3[jj0];
+      const float q0 = r0[jj1], q1 = r1[jj1], q2 = r2[jj1], q3 = r3[jj1];
+      if (c0) {
+        r0[j0] = fmaf(-a0, u0, p0); r1[j0] = fmaf(-a1, u0, p1);
+        r2[j0] = fmaf(-a2, u0, p2); r3[j0] = fmaf(-a3, u0, p3);
+      }
+      if (c1) {
+        r0[j1] = fmaf(-a0, u1, q0); r1[j1] = fmaf(-a1, u1, q1);
+        r2[j1] = fmaf(-a2, u1, q2); r3[j1] = fmaf(-a3, u1, q3);
+      }
+    }
+    for (; i < N; ++i) {
+      float* row = M + i * ld;
+      const float a = row[k];
+      if (c0) row[j0] = fmaf(-a, u0, row[j0]);
+      if (c1) row[j1] = fmaf(-a, u1, row[j1]);
+    }
+    __syncwarp();
+  }
+  return !singular;
+}
+
 // Register sweep of one warp for N <= 32 NR: lane l holds rows l, l + 32, ...
 // in NR registers and each solved entry is broadcast by a shuffle. Columns
 // are walked in segments over which the set of slots that still hold
@@ -600,37 +687,58 @@ __device__ __forceinline__ void lu_solve(const Team<WPC>& tm, const R* M, int N,
 // Mixed precision: x = M^-1 b with the FP32 factors of M, refined in FP64.
 // Each round takes the FP64 residual r = b - M x against the unfactored M
 // (here its transposed copy gT, gT[j*N + i] = M_ij, so a warp's loads of one
-// column are contiguous), solves for the correction with the FP32 factors
-// and adds it; it stops when the correction is below 1e-6 of the error-norm
-// weights sc (isc = 1/sc) and gives up after three rounds. Returns false if
-// it did not converge.
+// column are contiguous), solves for the correction dx with the FP32 factors
+// and adds it. Every FP32 solve leaves about the same relative error rho, so
+// the error left after a correction is about |dx| rho / (1 - rho), with rho
+// estimated by |dx| / |x| after the first correction and by the ratio of
+// successive corrections after that (norms: max over i of |v_i| / sc_i,
+// isc = 1/sc). It stops when that estimate is below 1e-6 and gives up after
+// three rounds. Returns false if it did not converge.
 template <int WPC>
 __device__ __forceinline__ bool solve_refined(const Team<WPC>& tm, const double* __restrict__ gT, const float* M32,
                                               int N, int ld, const float* invd32, const int* perm32,
                                               const double* b, double* x, double* r, double* dx, const double* isc) {
   constexpr int TS = 32 * WPC;
   lu_solve<WPC, float>(tm, M32, N, ld, invd32, perm32, b, x);
+  double prev = 0.0;
   for (int it = 0; it < 3; ++it) {
     for (int i = tm.tid; i < N; i += TS) {
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
       int j = 0;
-      for (; j + 3 < N; j += 4) {
-        s0 = fma(gT[j * N + i], x[j], s0);
-        s1 = fma(gT[(j + 1) * N + i], x[j + 1], s1);
-        s2 = fma(gT[(j + 2) * N + i], x[j + 2], s2);
-        s3 = fma(gT[(j + 3) * N + i], x[j + 3], s3);
+      for (; j + 7 < N; j += 8) {   // eight loads in flight from L2 per round trip
+        const double g0 = gT[j * N + i], g1 = gT[(j + 1) * N + i], g2 = gT[(j + 2) * N + i], g3 = gT[(j + 3) * N + i];
+        const double g4 = gT[(j + 4) * N + i], g5 = gT[(j + 5) * N + i], g6 = gT[(j + 6) * N + i], g7 = gT[(j + 7) * N + i];
+        s0 = fma(g0, x[j], s0);
+        s1 = fma(g1, x[j + 1], s1);
+        s2 = fma(g2, x[j + 2], s2);
+        s3 = fma(g3, x[j + 3], s3);
+        s0 = fma(g4, x[j + 4], s0);
+        s1 = fma(g5, x[j + 5], s1);
+        s2 = fma(g6, x[j + 6], s2);
+        s3 = fma(g7, x[j + 7], s3);
       }
       for (; j < N; ++j) s0 = fma(gT[j * N + i], x[j], s0);
       r[i] = b[i] - ((s0 + s1) + (s2 + s3));
     }
     tm.sync();
     lu_solve<WPC, float>(tm, M32, N, ld, invd32, perm32, r, dx);
-    int big = 0;
+    // weighted maxima of the correction and of the new x through the high
+    // words of the non-negative doubles (monotone in the value)
+    unsigned hd = 0u, hx = 0u;
     for (int i = tm.tid; i < N; i += TS) {
-      x[i] += dx[i];
-      big |= !(fabs(dx[i]) * isc[i] <= 1e-6);
+      const double xi = x[i] + dx[i];
+      x[i] = xi;
+      hd = max(hd, unsigned(__double2hiint(fabs(dx[i]) * isc[i])));
+      hx = max(hx, unsigned(__double2hiint(fabs(xi) * isc[i])));
     }
-    if (!tm.any(big)) return true;
+    tm.umax2(hd, hx);
+    const double dmax = __hiloint2double(int(hd), -1);   // upper bound of max |dx_i| / sc_i
+    const double xmax = __hiloint2double(int(hx), 0);    // lower bound of max |x_i| / sc_i
+    if (!(hd < 0x7ff00000u)) return false;               // non-finite correction
+    if (hd == 0u) return true;
+    const double rho = it == 0 ? dmax / xmax : dmax / prev;
+    if (rho < 1.0 && dmax * rho <= 1e-6 * (1.0 - rho)) return true;
+    prev = dmax;
   }
   return false;
 }
@@ -752,7 +860,19 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
         tm.sync();
         for_each_ij<TS>(tm.tid, N, [&](int e, int i, int j) { w.M32[i * ld + j] = trunc_to_float(w.g[j * N + i]); });
         tm.sync();
-        ok = lu_factor<WPC, float>(tm, w.M32, N, ld, w.invd32, w.perm32);
+        // the FP32 factorisation is latency-bound: one warp, no cross-warp barriers
+        if (N > 64) {
+          ok = lu_factor<WPC, float>(tm, w.M32, N, ld, w.invd32, w.perm32);
+        } else if (WPC == 1) {
+          ok = lu32_warp(w.M32, N, ld, w.invd32, w.perm32, tm.lane);
+        } else {
+          if (tm.warp == 0) {
+            const bool ok1 = lu32_warp(w.M32, N, ld, w.invd32, w.perm32, tm.lane);
+            if (tm.lane == 0) w.scal[30] = ok1 ? 1.0 : 0.0;
+          }
+          tm.sync();
+          ok = w.scal[30] != 0.0;
+        }
         if (!ok) { mixed = false; restore(); }
       }
       if (!mixed) ok = lu_factor<WPC, double>(tm, w.M, N, ld, w.invd, w.perm);

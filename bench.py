@@ -41,15 +41,16 @@ METRIC = "chemistry cells/s per dt at stated T/Y error vs FP64 oracle; frac of F
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2.07 GHz x 2 FP64
 # FMA lanes per clock per SM x 2 flop (= the 1.25 TFLOP/s nominal figure).
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
-# dram__bytes_read.sum + dram__bytes_write.sum of one integrator launch from
-# ncu on the 2048-cell case (1.386 MB + 0 B), scaled by cells to the full
+# dram__bytes_read.sum + dram__bytes_write.sum of one FP64 integrator launch
+# from ncu on the 2048-cell case (1.683 MB + 0 B), scaled by cells to the full
 # 262,144-cell field; None whenever the kernel changes after the capture.
-INTEGRATOR_TRAFFIC_BYTES = None
+INTEGRATOR_TRAFFIC_BYTES = 1.6832e6 * 262144 / 2048
 
 
 def flops_per_step(m) -> float:
     """Algorithmic FP64 flops of one attempted Rosenbrock step (FMA = 2,
-    exp/log = 20, division = 8); the terms are listed in the design doc."""
+    exp/log = 20, division = 8): LU (2/3 N^3) and four solve pairs (8 N^2),
+    three rate evaluations, the Jacobian extras and assembly, stage vectors."""
     nsp, nrx = m.nsp, m.nrx
     N = nsp + 1
     nr, npd = m.nu_matrix()
@@ -180,6 +181,8 @@ def main():
     ap.add_argument("--ncells", type=int, default=NCELLS)
     ap.add_argument("--team-warps", type=int, default=0, choices=[0, 1, 2, 4],
                     help="warps per cell (0 = the library's automatic choice)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="mixed: FP32 LU of the iteration matrix with FP64 refinement")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -203,7 +206,7 @@ def main():
     sched = dlbchem.SCHED_QUEUE if args.schedule == "queue" else dlbchem.SCHED_PLAIN
     ctx = dlbchem.Context(states.mech_path(NSP, NRX, SEED), rtol=RTOL, atol=ATOL, schedule=sched,
                           mapping=args.mapping, map_Ttol=MAP_TOL, map_Ytol=MAP_TOL, timing=1,
-                          team_warps=args.team_warps)
+                          team_warps=args.team_warps, precision=1 if args.precision == "mixed" else 0)
     d = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
     Td, pd, Yd = d(T), d(p), d(Y)
     To, Yo = torch.empty_like(Td), torch.empty_like(Yd)
@@ -274,13 +277,16 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64 (LU in f32, f64 refinement)",
+        "data": "synthetic",
         "config": {"workload": f"bimodal {n} cells, 53 species / 325 reactions (seeded synthetic), p 20 bar, "
-                               f"dt 1e-5 s, rtol 1e-5, atol 1e-8, FP64", "schedule": args.schedule,
+                               f"dt 1e-5 s, rtol 1e-5, atol 1e-8, {'FP64' if args.precision == 'fp64' else 'mixed precision'}",
+                   "schedule": args.schedule, "precision": args.precision,
                    "mapping": bool(args.mapping), "mapping_tol": MAP_TOL, "cells_per_gpu": n,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": INTEGRATOR_TRAFFIC_BYTES,
+                     "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": INTEGRATOR_TRAFFIC_BYTES if args.precision == "fp64" else None,
                      "kernel": "rosenbrock_kernel", "flops_per_step": fstep,
                      "steps_per_launch": total_steps / args.steps, "launch_ms": integ_avg_ms,
                      "peak_source": "derived: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM x 2"},

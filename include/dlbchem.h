@@ -172,7 +172,7 @@ int dlbchem_integrate_static(dlbchem_ctx* ctx, int64_t ncells, double dt, const 
                              void* cuda_stream);
 
 /*
- * Batched uneven launch (SURVEY configuration of several meshes over several
+ * Batched uneven launch (several meshes of uneven sizes over several
  * mechanisms; the paper's balancing across processes, Sec. 2.2, becomes one
  * device queue per mechanism). Meshes that share a mechanism file form a
  * class; each class runs as ONE persistent integrator launch whose work list

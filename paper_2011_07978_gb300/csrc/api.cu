@@ -315,7 +315,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
     }
   }
   // reactions (device index r is file reaction order[r])
-  std::vector<double> lnA(nrx), beta(nrx), EaR(nrx);
+  std::vector<double> lnA(nrx), beta(nrx), EaR(nrx), dH0(nrx, 0.0), dHa(nrx, 0.0), dHb(nrx, 0.0);
   std::vector<RxnMeta> meta(nrx);
   std::vector<int32_t> eff_sp;
   std::vector<double> eff_dm1;
@@ -324,6 +324,8 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   for (int r = 0; r < nrx; ++r) {
     const HostRxn& x = hm.rx[order[r]];
     lnA[r] = x.lnA; beta[r] = x.beta; EaR[r] = x.Ea / kR;
+    for (int k : x.p) { dH0[r] += H0[k]; dHa[r] += cpa[k]; dHb[r] += hcpb[k]; }
+    for (int k : x.r) { dH0[r] -= H0[k]; dHa[r] -= cpa[k]; dHb[r] -= hcpb[k]; }
     RxnMeta& mt = meta[r];
     std::memset(&mt, 0, sizeof(mt));
     for (int i = 0; i < 6; ++i) mt.sp[i] = -1;
@@ -475,6 +477,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   offs.push_back(put(trip.data(), trip.size() * 4));
   offs.push_back(put(inc_all.data(), std::max<size_t>(inc_all.size(), 1) * 4));
   offs.push_back(put(incp_all.data(), incp_all.size() * 4));
+  for (auto* v : {&dH0, &dHa, &dHb}) offs.push_back(put(v->data(), v->size() * 8));
   // store offsets as fake pointers; relocated after upload
   auto P = [&](int i) { return reinterpret_cast<const double*>(offs[i]); };
   dm.W = P(0); dm.iW = P(1); dm.H0 = P(2); dm.cpa = P(3); dm.hcpb = P(4); dm.cpb = P(5);
@@ -492,6 +495,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   dm.trip = reinterpret_cast<const int32_t*>(offs[23]);
   dm.inc_all = reinterpret_cast<const uint32_t*>(offs[24]);
   dm.incp_all = reinterpret_cast<const int32_t*>(offs[25]);
+  dm.dH0 = P(26); dm.dHa = P(27); dm.dHb = P(28);
   return true;
 }
 
@@ -514,6 +518,7 @@ void relocate(DevMech& dm, void* base) {
   dm.trip = reloc(dm.trip, base);
   dm.inc_all = reloc(dm.inc_all, base);
   dm.incp_all = reloc(dm.incp_all, base);
+  dm.dH0 = reloc(dm.dH0, base); dm.dHa = reloc(dm.dHa, base); dm.dHb = reloc(dm.dHb, base);
 }
 
 int configure_launch(dlbchem_ctx* c) {

@@ -60,6 +60,8 @@ struct DevMech {
   const double *W, *iW, *H0, *cpa, *hcpb, *cpb, *G0, *G1, *G2, *G3, *bW;
   // reactions
   const double *lnA, *beta, *EaR;
+  // reaction enthalpy change dH(T) = dH0 + T (dHa + dHb T), sums over products minus reactants
+  const double *dH0, *dHa, *dHb;
   const RxnMeta* meta;
   const int32_t* eff_sp;
   const double* eff_dm1;
@@ -121,7 +123,7 @@ __host__ inline WsLayout make_layout(int nsp, int nrx, int CH, int N, int ld, in
   L.dqdT = take(CH);
   L.dlt = take(CH);
   L.D = take(CH * DS > nrx ? CH * DS : nrx);   // D slots of a chunk, or every reaction's rate
-  L.scal = take(32);
+  L.scal = take(48);
   L.perm = take((N + 1) / 2 + 1);
   L.M32 = L.invd32 = L.perm32 = L.rr = L.dx = L.isc = 0;
   if (mixed) {

@@ -74,6 +74,29 @@ struct Team {
     for (int w = 1; w < WPC; ++w) s = fmax(s, buf[w]);
     return s;
   }
+  // Sums of two values over the team with one butterfly: after the first
+  // exchange the two half-warps carry one partial sum each, so the warp does
+  // 5 FP64 adds instead of 10. Every thread receives both sums; the order of
+  // the adds is fixed. Cross-warp slots: team scratch 32 + [0, 4 WPC).
+  __device__ __forceinline__ void sum2(double& a, double& b) const {
+    const bool hi = (lane & 16) != 0;
+    double keep = hi ? b : a;
+    const double send = hi ? a : b;
+    keep += __shfl_xor_sync(0xffffffffu, send, 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+    a = __shfl_sync(0xffffffffu, keep, 0);
+    b = __shfl_sync(0xffffffffu, keep, 16);
+    if (WPC == 1) return;
+    double* buf = red + 32 + parity * 2 * WPC;
+    parity ^= 1;
+    if (lane == 0) { buf[2 * warp] = a; buf[2 * warp + 1] = b; }
+    sync();
+    a = buf[0];
+    b = buf[1];
+#pragma unroll
+    for (int w = 1; w < WPC; ++w) { a += buf[2 * w]; b += buf[2 * w + 1]; }
+  }
   // Team maxima of two unsigned keys (every thread receives both).
   __device__ __forceinline__ void umax2(unsigned& a, unsigned& b) const {
     a = __reduce_max_sync(0xffffffffu, a);
@@ -189,6 +212,24 @@ __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mi
   const double a0 = w.c[mt.sp[0]];
   const double a1 = mt.nr > 1 ? w.c[mt.sp[1]] : 1.0;
   const double a2 = mt.nr > 2 ? w.c[mt.sp[2]] : 1.0;
+  double Mf = 1.0;
+  if (mt.flags & RX_TB) {
+    Mf = mx.Ctot;
+    for (int e = mt.eff_begin; e < mt.eff_end; ++e) Mf = fma(m.eff_dm1[e], w.c[m.eff_sp[e]], Mf);
+  }
+  if (!JAC) {
+    // q = [M] k_f (prod c_reac - prod E_reac prod (c/E)_prod); Einv holds c_k / E_k here
+    double d = a0 * (a1 * a2);
+    if (mt.flags & RX_REV) {
+      const double e1 = mt.nr > 1 ? w.E[mt.sp[1]] : 1.0;
+      const double e2 = mt.nr > 2 ? w.E[mt.sp[2]] : 1.0;
+      const double g1 = mt.np > 1 ? w.Einv[mt.sp[4]] : 1.0;
+      const double g2 = mt.np > 2 ? w.Einv[mt.sp[5]] : 1.0;
+      d = fma(-(w.E[mt.sp[0]] * (e1 * e2)), w.Einv[mt.sp[3]] * (g1 * g2), d);
+    }
+    qdst[rl] = (Mf * kf) * d;
+    return;
+  }
   const double pf = kf * (a0 * (a1 * a2));
   double pr = 0.0, kr = 0.0, b0 = 1.0, b1 = 1.0, b2 = 1.0;
   if (mt.flags & RX_REV) {
@@ -202,43 +243,34 @@ __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mi
     b2 = mt.np > 2 ? w.c[mt.sp[5]] : 1.0;
     pr = kr * (b0 * (b1 * b2));
   }
-  double Mf = 1.0;
-  if (mt.flags & RX_TB) {
-    Mf = mx.Ctot;
-    for (int e = mt.eff_begin; e < mt.eff_end; ++e) Mf = fma(m.eff_dm1[e], w.c[m.eff_sp[e]], Mf);
-  }
   qdst[rl] = Mf * (pf - pr);
-  if (JAC) {
-    double* D = w.D + rl * m.DS;
-    for (int s2 = 0; s2 < mt.nds; ++s2) D[s2] = 0.0;
-    // d/dc_j of the slot product = product of the other slots
-    const double kfM = kf * Mf;
-    D[mt.ds[0]] += kfM * (a1 * a2);
-    if (mt.nr > 1) D[mt.ds[1]] += kfM * (a0 * a2);
-    if (mt.nr > 2) D[mt.ds[2]] += kfM * (a0 * a1);
-    if (mt.flags & RX_REV) {
-      const double krM = kr * Mf;
-      D[mt.ds[3]] -= krM * (b1 * b2);
-      if (mt.np > 1) D[mt.ds[4]] -= krM * (b0 * b2);
-      if (mt.np > 2) D[mt.ds[5]] -= krM * (b0 * b1);
-    }
-    const int tb = (mt.flags & RX_TB) ? 1 : 0;
-    if (mt.flags & RX_EFF) D[mt.dslot_eff] = pf - pr;
-    w.sig[rl] = Mf * ((mt.nr + tb) * pf - (mt.np + tb) * pr);
-    const double dlnkf = fma(m.EaR[r], mx.iT * mx.iT, m.beta[r] * mx.iT);
-    double dq = pf * dlnkf;
-    if (mt.flags & RX_REV) {
-      double dH = w.hk[mt.sp[3]] - w.hk[mt.sp[0]];
-      if (mt.np > 1) dH += w.hk[mt.sp[4]];
-      if (mt.np > 2) dH += w.hk[mt.sp[5]];
-      if (mt.nr > 1) dH -= w.hk[mt.sp[1]];
-      if (mt.nr > 2) dH -= w.hk[mt.sp[2]];
-      const double dlnKc = dH * mx.iT * mx.iT * (1.0 / kR) - mt.dnu * mx.iT;
-      dq -= pr * (dlnkf - dlnKc);
-    }
-    w.dqdT[rl] = Mf * dq;
-    w.dlt[rl] = tb ? (pf - pr) : 0.0;
+  double* D = w.D + rl * m.DS;
+  for (int s2 = 0; s2 < mt.nds; ++s2) D[s2] = 0.0;
+  // d/dc_j of the slot product = product of the other slots
+  const double kfM = kf * Mf;
+  D[mt.ds[0]] += kfM * (a1 * a2);
+  if (mt.nr > 1) D[mt.ds[1]] += kfM * (a0 * a2);
+  if (mt.nr > 2) D[mt.ds[2]] += kfM * (a0 * a1);
+  if (mt.flags & RX_REV) {
+    const double krM = kr * Mf;
+    D[mt.ds[3]] -= krM * (b1 * b2);
+    if (mt.np > 1) D[mt.ds[4]] -= krM * (b0 * b2);
+    if (mt.np > 2) D[mt.ds[5]] -= krM * (b0 * b1);
   }
+  const int tb = (mt.flags & RX_TB) ? 1 : 0;
+  if (mt.flags & RX_EFF) D[mt.dslot_eff] = pf - pr;
+  // small integers as doubles from the shared table (nutab[j] = j - 8), not by conversion
+  w.sig[rl] = Mf * (w.nutab[8 + mt.nr + tb] * pf - w.nutab[8 + mt.np + tb] * pr);
+  const double dlnkf = fma(m.EaR[r], mx.iT * mx.iT, m.beta[r] * mx.iT);
+  double dq = pf * dlnkf;
+  if (mt.flags & RX_REV) {
+    const double T = mx.T;
+    const double dH = fma(T, fma(m.dHb[r], T, m.dHa[r]), m.dH0[r]);   // sum nu h_k(T), products - reactants
+    const double dlnKc = dH * mx.iT * mx.iT * (1.0 / kR) - w.nutab[8 + mt.dnu] * mx.iT;
+    dq -= pr * (dlnkf - dlnKc);
+  }
+  w.dqdT[rl] = Mf * dq;
+  w.dlt[rl] = tb ? (pf - pr) : 0.0;
 }
 
 template <int WPC, bool JAC>
@@ -269,7 +301,7 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
     w.c[k] = rho * yv[1 + k] * m.iW[k];
     const double e = exp_tab(fma(m.G2[k], lnT, fma(m.G3[k], T, -fma(m.G0[k], iT, m.G1[k]))), w.exptab);
     w.E[k] = e;
-    w.Einv[k] = rcp_nr(e);
+    w.Einv[k] = JAC ? rcp_nr(e) : w.c[k] * rcp_nr(e);   // without the Jacobian: c_k / E_k
     w.hk[k] = fma(T, fma(m.hcpb[k], T, m.cpa[k]), m.H0[k]);
   }
   if (tm.tid == 0) w.c[nsp] = 0.0;
@@ -338,8 +370,9 @@ __device__ __forceinline__ void finish_f(const DevMech& m, const Team<WPC>& tm, 
     q = fma(w.hk[k], w.wdot[k], q);
     cp = fma(yv[1 + k] * m.iW[k], fma(m.cpb[k], mx.T, m.cpa[k]), cp);
   }
-  Q = tm.sum(q);
-  cpm = tm.sum(cp);
+  tm.sum2(q, cp);
+  Q = q;
+  cpm = cp;
   if (tm.tid == 0) f[0] = iso ? 0.0 : -Q * mx.irho / cpm;
   tm.sync();
 }
@@ -384,7 +417,9 @@ __device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, 
     const double cpk = fma(m.cpb[k], mx.T, m.cpa[k]);
     tt = fma(cpk, w.wdot[k], fma(w.hk[k], fma(-w.vv[k], mx.iT, w.dwdT[k]), tt));
   }
-  const double Hv = tm.sum(hv), Hu = tm.sum(hu), dcpm = tm.sum(dc), Tsum = tm.sum(tt);
+  tm.sum2(hv, hu);
+  tm.sum2(dc, tt);
+  const double Hv = hv, Hu = hu, dcpm = dc, Tsum = tt;
   const double irS = mx.irho / mx.S;
   const double icpm = 1.0 / cpm;
   // r_k into E, h_k/W_k into Einv (both free after the rate pass); T column

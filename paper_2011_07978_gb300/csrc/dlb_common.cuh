@@ -94,7 +94,7 @@ struct IntegParams {
 
 // Offsets (in doubles) of one team's workspace inside dynamic shared memory.
 struct WsLayout {
-  int M, y0, f0, ys, fs, u, c, E, Einv, hk, wdot, vv, dwdT, uu, invd, q, sig, dqdT, dlt, D, scal, perm;
+  int M, y0, f0, ys, fs, u, c, E, Einv, hk, wdot, vv, dwdT, uu, invd, q, dqdT, dlt, D, scal, perm;
   int M32, invd32, perm32, rr, dx, isc;   // mixed precision only (else 0-sized)
   int total;  // doubles per team (int and float arrays are counted in doubles)
 };
@@ -119,7 +119,6 @@ __host__ inline WsLayout make_layout(int nsp, int nrx, int CH, int N, int ld, in
   L.uu = take(nsp + 1);
   L.invd = take(N);
   L.q = take(CH);          // per-reaction arrays hold one chunk of CH reactions
-  L.sig = take(CH);
   L.dqdT = take(CH);
   L.dlt = take(CH);
   L.D = take(CH * DS > nrx ? CH * DS : nrx);   // D slots of a chunk, or every reaction's rate

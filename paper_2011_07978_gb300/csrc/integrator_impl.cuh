@@ -125,7 +125,7 @@ struct Team {
 };
 
 struct WS {
-  double *M, *y0, *f0, *ys, *fs, *u, *c, *E, *Einv, *hk, *wdot, *vv, *dwdT, *uu, *invd, *q, *sig, *dqdT, *dlt,
+  double *M, *y0, *f0, *ys, *fs, *u, *c, *E, *Einv, *hk, *wdot, *vv, *dwdT, *uu, *invd, *q, *dqdT, *dlt,
       *D, *scal;
   int* perm;
   float *M32, *invd32;
@@ -141,7 +141,7 @@ __device__ __forceinline__ WS carve(double* base, const WsLayout& L) {
   w.M = base + L.M; w.y0 = base + L.y0; w.f0 = base + L.f0; w.ys = base + L.ys; w.fs = base + L.fs;
   w.u = base + L.u; w.c = base + L.c; w.E = base + L.E; w.Einv = base + L.Einv; w.hk = base + L.hk;
   w.wdot = base + L.wdot; w.vv = base + L.vv; w.dwdT = base + L.dwdT; w.uu = base + L.uu;
-  w.invd = base + L.invd; w.q = base + L.q; w.sig = base + L.sig; w.dqdT = base + L.dqdT; w.dlt = base + L.dlt;
+  w.invd = base + L.invd; w.q = base + L.q; w.dqdT = base + L.dqdT; w.dlt = base + L.dlt;
   w.D = base + L.D; w.scal = base + L.scal; w.perm = reinterpret_cast<int*>(base + L.perm);
   w.M32 = reinterpret_cast<float*>(base + L.M32); w.invd32 = reinterpret_cast<float*>(base + L.invd32);
   w.perm32 = reinterpret_cast<int*>(base + L.perm32);
@@ -151,7 +151,7 @@ __device__ __forceinline__ WS carve(double* base, const WsLayout& L) {
 
 // Mixture scalars shared by one rate evaluation.
 struct Mix {
-  double T, iT, lnT, S, rho, irho, Ctot;
+  double T, iT, lnT, S, rho, irho, Ctot, irS;   // irS = 1/(rho S) = T / P1
 };
 
 // exp(x) by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989):
@@ -195,10 +195,11 @@ __device__ __forceinline__ double rcp_nr(double d) {
 // exp(-g_k/RT) p0/(R_c T) (the standard-state concentration folded in, so
 // 1/K_c = prod_reac E^nu' prod_prod (1/E)^nu'') and 1/E_k, molar h_k.
 // Reaction pass: k_f = exp(ln A + b ln T - Ea/(R T)), q = [M](fwd - rev).
-// With JAC, also d q / d c for each distinct participant (D slots), the
-// homogeneity sum sigma = sum_j c_j dq/dc_j, dq/dT at fixed c, and the
-// third-body difference fwd - rev. Then the incidence rounds gather
-// wdot_k = sum_r nu_kr q_r (and v, dwdT, u).
+// With JAC, also d q / d c for each distinct participant (D slots), and from
+// the homogeneity sum sigma = sum_j c_j dq/dc_j, dq/dT at fixed c and the
+// third-body difference fwd - rev the two combinations the assembly needs.
+// Then the incidence rounds gather wdot_k = sum_r nu_kr q_r (and with JAC
+// y_k = dwdot_k/dT - v_k/T and z_k = u_k - v_k/(rho S)).
 // Without JAC all reactions go at once: q into the D region, then the
 // whole-mechanism rounds. With JAC the reactions go one chunk of CH (= team
 // size) at a time: rate pass, then the chunk's incidence rounds and its
@@ -260,7 +261,7 @@ __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mi
   const int tb = (mt.flags & RX_TB) ? 1 : 0;
   if (mt.flags & RX_EFF) D[mt.dslot_eff] = pf - pr;
   // small integers as doubles from the shared table (nutab[j] = j - 8), not by conversion
-  w.sig[rl] = Mf * (w.nutab[8 + mt.nr + tb] * pf - w.nutab[8 + mt.np + tb] * pr);
+  const double sig = Mf * (w.nutab[8 + mt.nr + tb] * pf - w.nutab[8 + mt.np + tb] * pr);
   const double dlnkf = fma(m.EaR[r], mx.iT * mx.iT, m.beta[r] * mx.iT);
   double dq = pf * dlnkf;
   if (mt.flags & RX_REV) {
@@ -269,8 +270,10 @@ __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mi
     const double dlnKc = dH * mx.iT * mx.iT * (1.0 / kR) - w.nutab[8 + mt.dnu] * mx.iT;
     dq -= pr * (dlnkf - dlnKc);
   }
-  w.dqdT[rl] = Mf * dq;
-  w.dlt[rl] = tb ? (pf - pr) : 0.0;
+  // the assembly needs v only inside dwdot/dT - v/T and u - v/(rho S), so the
+  // gathers carry those two combinations (sigma = sum_j c_j dq/dc_j)
+  w.dqdT[rl] = fma(-sig, mx.iT, Mf * dq);
+  w.dlt[rl] = fma(-sig, mx.irS, tb ? (pf - pr) : 0.0);
 }
 
 template <int WPC, bool JAC>
@@ -297,6 +300,7 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
   const double rho = rcp_nr(irho);
   mx.T = T; mx.iT = iT; mx.lnT = lnT; mx.S = S; mx.rho = rho; mx.irho = irho;
   mx.Ctot = P1 * iT;                          // sum_k c_k (unit efficiencies)
+  mx.irS = T * iP1;
   for (int k = tm.tid; k < nsp; k += TS) {
     w.c[k] = rho * yv[1 + k] * m.iW[k];
     const double e = exp_tab(fma(m.G2[k], lnT, fma(m.G3[k], T, -fma(m.G0[k], iT, m.G1[k]))), w.exptab);
@@ -329,7 +333,7 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
   }
   for (int k = tm.tid; k <= nsp; k += TS) {
     w.wdot[k] = 0.0;
-    w.vv[k] = 0.0; w.dwdT[k] = 0.0; w.uu[k] = 0.0;
+    w.dwdT[k] = 0.0; w.uu[k] = 0.0;
   }
   tm.sync();
   for (int c = 0; c < m.nchunks; ++c) {
@@ -342,7 +346,6 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
       const int k = int(e >> 20), rr = int((e >> 4) & 0xffffu);
       const double nu = w.nutab[e & 15u];
       w.wdot[k] = fma(nu, w.q[rr], w.wdot[k]);
-      w.vv[k] = fma(nu, w.sig[rr], w.vv[k]);
       w.dwdT[k] = fma(nu, w.dqdT[rr], w.dwdT[k]);
       w.uu[k] = fma(nu, w.dlt[rr], w.uu[k]);
       __syncwarp();
@@ -409,33 +412,34 @@ __device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, 
   double Q, cpm;
   finish_f<WPC>(m, tm, w, w.y0, mx, iso, w.f0, Q, cpm);
   // scalars for the T row / column
-  double hv = 0.0, hu = 0.0, dc = 0.0, tt = 0.0;
+  // dwdT now holds y_k = dwdot_k/dT - v_k/T and uu holds z_k = u_k - v_k/(rho S)
+  double hz = 0.0, dc = 0.0, tt = 0.0;
   for (int k = tm.tid; k < nsp; k += TS) {
-    hv = fma(w.hk[k], w.vv[k], hv);
-    hu = fma(w.hk[k], w.uu[k], hu);
+    hz = fma(w.hk[k], w.uu[k], hz);
     dc = fma(w.y0[1 + k], m.bW[k], dc);
     const double cpk = fma(m.cpb[k], mx.T, m.cpa[k]);
-    tt = fma(cpk, w.wdot[k], fma(w.hk[k], fma(-w.vv[k], mx.iT, w.dwdT[k]), tt));
+    tt = fma(cpk, w.wdot[k], fma(w.hk[k], w.dwdT[k], tt));
   }
-  tm.sum2(hv, hu);
-  tm.sum2(dc, tt);
-  const double Hv = hv, Hu = hu, dcpm = dc, Tsum = tt;
-  const double irS = mx.irho / mx.S;
-  const double icpm = 1.0 / cpm;
-  // r_k into E, h_k/W_k into Einv (both free after the rate pass); T column
-  // M[1+k][0] = -J_kT, J_kT = W_k/rho (dwdT_k + (wdot_k - v_k)/T)
+  tm.sum2(hz, dc);
+  const double Tsum = tm.sum(tt);
+  const double Hz = hz, dcpm = dc;
+  const double irS = mx.irS;
+  const double icpm = rcp_nr(cpm);
+  // r_k = W_k (z_k + wdot_k/(rho S)) into E, h_k/W_k into Einv (both free after
+  // the rate pass); T column M[1+k][0] = -J_kT, J_kT = W_k/rho (y_k + wdot_k/T)
   for (int k = tm.tid; k < nsp; k += TS) {
-    w.E[k] = m.W[k] * fma(w.wdot[k] - w.vv[k], irS, w.uu[k]);
+    w.E[k] = m.W[k] * fma(w.wdot[k], irS, w.uu[k]);
     w.Einv[k] = w.hk[k] * m.iW[k];
-    w.M[(1 + k) * ld] = -m.W[k] * mx.irho * fma(w.wdot[k] - w.vv[k], mx.iT, w.dwdT[k]);
+    w.M[(1 + k) * ld] = -m.W[k] * mx.irho * fma(w.wdot[k], mx.iT, w.dwdT[k]);
   }
   tm.sync();
-  // T row: J_Tj = (1/cp) [ -sum_k (h_k/W_k) Shat_kj + (1/W_j)(-Hu + (Hv - Q)/(rho S) + Q cp_j/(rho cp)) ]
+  // T row: J_Tj = (1/cp) [ -sum_k (h_k/W_k) Shat_kj + (1/W_j)(-Hz - Q/(rho S) + Q cp_j/(rho cp)) ],
+  // Hz = sum_k h_k z_k = Hu - Hv/(rho S)
   for (int j = tm.tid; j < nsp; j += TS) {
     double hs = 0.0;
     for (int k = 0; k < nsp; ++k) hs = fma(w.Einv[k], w.M[(1 + k) * ld + 1 + j], hs);
     const double cpj = fma(m.cpb[j], mx.T, m.cpa[j]);
-    const double bracket = fma(Q * cpj, mx.irho * icpm, fma(Hv - Q, irS, -Hu));
+    const double bracket = fma(Q * cpj, mx.irho * icpm, -fma(Q, irS, Hz));
     const double JT = icpm * fma(m.iW[j], bracket, -hs);
     w.M[1 + j] = iso ? 0.0 : -JT;
   }

@@ -636,37 +636,55 @@ __device__ __forceinline__ bool lu32_warp(float* M, int N, int ld, float* invd, 
   return !singular;
 }
 
-// Register sweep of one warp for N <= 32 NR: lane l holds rows l, l + 32, ...
-// in NR registers and each solved entry is broadcast by a shuffle. Columns
-// are walked in segments over which the set of slots that still hold
-// unsolved rows is fixed at compile time, so every issued FP64 instruction
-// has work in it (a warp FP64 instruction costs the same with 1 or 32 active
-// lanes, and a fully predicated-off one still takes its issue slot). Loads of
-// rows past N are clamped to row N-1; those lanes compute values that are
-// never stored.
+// Register sweep of one warp for N <= 32 NR, each solved entry broadcast by a
+// shuffle. Columns are walked in segments over which the set of slots that
+// still hold unsolved rows is fixed at compile time, so every issued FP64
+// instruction has work in it (a warp FP64 instruction costs the same with 1
+// or 32 active lanes, and a fully predicated-off one still takes its issue
+// slot). The forward sweep aligns the slots to the last row (slot s holds
+// rows o + 32 s + lane, o = N - 32 NR <= 0), the backward sweep to the first
+// (rows 32 s + lane): the partly solved slot is then the one that empties
+// first in both directions (74 + 74 FP64 instructions at N = 54 instead of
+// 84 + 74). Rows outside [0, N) are clamped for loads and never stored.
 template <int NR, class R>
 __device__ __forceinline__ void sweep_solve(const R* M, int N, int ld, const R* invd, const int* perm,
                                             const double* b, double* x, int l) {
+  const int o = N - 32 * NR;
   R xs[NR];
   int ro[NR];
 #pragma unroll
   for (int s = 0; s < NR; ++s) {
-    const int i = 32 * s + l;
-    xs[s] = i < N ? R(b[perm[i]]) : R(0);
-    ro[s] = min(i, N - 1) * ld;
+    const int i = o + 32 * s + l;
+    xs[s] = i >= 0 ? R(b[perm[i]]) : R(0);
+    ro[s] = max(i, 0) * ld;
   }
-  // forward, unit lower L: column j updates rows r > j. Segment s0 holds the
-  // columns j in [32 s0 - 1, 32 s0 + 30]: slot s0 partly, slots above fully.
+  // forward, unit lower L: column j = jj + o updates rows r > j. Segment s0
+  // holds jj in [32 s0 - 1, 32 s0 + 30] (from -o for s0 = 0): slot s0 partly,
+  // slots above fully.
 #pragma unroll
   for (int s0 = 0; s0 < NR; ++s0) {
-    const int j0 = s0 == 0 ? 0 : 32 * s0 - 1;
-    const int j1 = min(32 * s0 + 31, N - 1);
-    for (int j = j0; j < j1; ++j) {
-      const R src = (s0 > 0 && j < 32 * s0) ? xs[s0 > 0 ? s0 - 1 : 0] : xs[s0];
-      const R xj = __shfl_sync(0xffffffffu, src, j & 31);
-      if (32 * s0 + l > j) xs[s0] = fma(-M[ro[s0] + j], xj, xs[s0]);
+    const int j0 = s0 == 0 ? -o : 32 * s0 - 1;
+    const int j1 = min(32 * s0 + 31, 32 * NR - 1);
+    for (int jj = j0; jj < j1; ++jj) {
+      const R src = (s0 > 0 && jj < 32 * s0) ? xs[s0 > 0 ? s0 - 1 : 0] : xs[s0];
+      const R xj = __shfl_sync(0xffffffffu, src, jj & 31);
+      const int j = jj + o;
+      if (32 * s0 + l > jj) xs[s0] = fma(-M[ro[s0] + j], xj, xs[s0]);
 #pragma unroll
       for (int s = s0 + 1; s < NR; ++s) xs[s] = fma(-M[ro[s] + j], xj, xs[s]);
+    }
+  }
+  // to the first-row alignment: row 32 t + l sits in forward slot t (lane
+  // l - o) or t + 1 (lane l - o - 32)
+  {
+    const int src = (l - o) & 31;
+    const bool up = l - o >= 32;
+#pragma unroll
+    for (int t = 0; t < NR; ++t) {   // in place: slot t reads only forward slots t and t + 1
+      const R v0 = __shfl_sync(0xffffffffu, xs[t], src);
+      const R v1 = __shfl_sync(0xffffffffu, t + 1 < NR ? xs[t + 1 < NR ? t + 1 : t] : R(0), src);
+      xs[t] = up ? v1 : v0;
+      ro[t] = min(32 * t + l, N - 1) * ld;
     }
   }
 #pragma unroll

@@ -42,9 +42,9 @@ METRIC = "chemistry cells/s per dt at stated T/Y error vs FP64 oracle; frac of F
 # FMA lanes per clock per SM x 2 flop (= the 1.25 TFLOP/s nominal figure).
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP64 integrator launch
-# from ncu on the 2048-cell case (1.683 MB + 0 B), scaled by cells to the full
+# from ncu on the 2048-cell case (1.419 MB + 0 B), scaled by cells to the full
 # 262,144-cell field; None whenever the kernel changes after the capture.
-INTEGRATOR_TRAFFIC_BYTES = 1.6832e6 * 262144 / 2048
+INTEGRATOR_TRAFFIC_BYTES = 1.4190e6 * 262144 / 2048
 
 
 def flops_per_step(m) -> float:

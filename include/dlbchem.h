@@ -87,9 +87,14 @@ typedef struct dlbchem_options {
   double map_Tmax;      /* > 0: only cells below this T qualify (0 = off) */
   int32_t team_warps;   /* warps per cell: 1, 2, 4, or 0 = automatic (1 up to 32 unknowns, 2 up to 64, else 4) */
   int32_t precision;    /* 0: FP64 LU of the iteration matrix (default); 1: FP32 LU with FP64
-                           iterative refinement (residuals against the FP64 matrix, at most 3
-                           rounds, step redone with the FP64 LU if they do not converge).
-                           State, rates, error norm and step control stay FP64. Fixed at create. */
+                           iterative refinement: residuals against the FP64 matrix, stopped when
+                           the estimated remaining error is below 1e-6 of the error weights, at
+                           most 3 rounds, the step redone with the FP64 LU if they do not
+                           converge. State, rates, error norm and step control stay FP64.
+                           Fixed at create, which then allocates one FP64 matrix copy per
+                           resident team (SMs x CTAs per SM x teams x N^2 doubles; 22 MB at 54
+                           unknowns on 152 SMs); integrations of such a context always launch
+                           persistent teams (the plain schedule keeps index order). */
   int32_t predictor;    /* 1: order the queue by the attached network's predicted step counts
                            (no previous call needed); steps[] is then only written */
   int32_t surrogate;    /* 1: try the attached network's increments first; cells that pass the
@@ -301,6 +306,20 @@ const char* dlbchem_last_error(const dlbchem_ctx* ctx);
 
 /* Release ctx and its device memory (synchronises its last stream). NULL ok. */
 void dlbchem_destroy(dlbchem_ctx* ctx);
+
+/*
+ * Host only, no GPU needed: build the mechanism tables for a team of
+ * team_warps (1, 2, 4) warps and check them against the mechanism file, the
+ * conditions the integrator's race-free gathers rely on (every incidence and
+ * Jacobian entry exactly once with its coefficient, no target twice in a round
+ * of 32, no target in two warps of one chunk, each target's entries in
+ * reaction order). On success out[0..9] = chunks, reactions per chunk, D slots
+ * per reaction, incidence rounds (all chunks and warps), Jacobian rounds,
+ * whole-mechanism incidence rounds of the busiest warp, species split over two
+ * accumulators, split offset, species, reactions. Returns OK, BAD_ARG or
+ * BAD_MECH (message from dlbchem_last_error(NULL)).
+ */
+int dlbchem_table_stats(const char* mech_path, int32_t team_warps, int64_t* out);
 
 #ifdef __cplusplus
 }

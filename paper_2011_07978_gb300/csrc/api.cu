@@ -265,7 +265,8 @@ bool valid_opts(const dlbchem_options* o, std::string& why) {
 }
 
 // Build all device tables of one mechanism into one contiguous blob.
-bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& blob, DevMech& dm, std::string& err) {
+bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& blob, DevMech& dm, std::string& err,
+                  std::vector<int>* order_out = nullptr) {
   const int nsp = hm.nsp, nrx = hm.nrx, N = nsp + 1, ld = N + 1;
   dm.nsp = nsp; dm.nrx = nrx; dm.N = N; dm.ld = ld; dm.wpc = wpc;
   if (N * ld + 2 >= 65536 || N > 256) { err = "mechanism too large (max 254 species)"; return false; }
@@ -314,6 +315,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
       if (cst < best) { best = cst; order = o; parity = par; }
     }
   }
+  if (order_out) *order_out = order;
   // reactions (device index r is file reaction order[r])
   std::vector<double> lnA(nrx), beta(nrx), EaR(nrx), dH0(nrx, 0.0), dHa(nrx, 0.0), dHb(nrx, 0.0);
   std::vector<RxnMeta> meta(nrx);
@@ -617,6 +619,138 @@ int ensure_ws(dlbchem_ctx* c, int64_t n) {
   c->w_hist = reinterpret_cast<int32_t*>(b + o_h);
   c->ws_cap = n;
   return DLBCHEM_OK;
+}
+
+// Check the round tables of a built mechanism against the mechanism itself
+// (host only). Incidence rounds, per chunk and warp and over the whole
+// mechanism: every nonzero net coefficient appears exactly once with its
+// reaction and value, no target twice in a round, no target in two warps of
+// one chunk, and each target's entries in increasing reaction order. Jacobian
+// rounds: every (species, distinct participant) pair of a reaction once with
+// coefficient nu W_k / W_j, same round and warp rules. Counts go to out[0..9].
+bool verify_tables(const dlb::HostMech& hm, int wpc, const std::vector<unsigned char>& blob, const DevMech& dm,
+                   const std::vector<int>& order, int64_t* out, std::string& err) {
+  auto at = [&](const void* off) { return blob.data() + reinterpret_cast<size_t>(off); };
+  const uint32_t* inc = reinterpret_cast<const uint32_t*>(at(dm.inc));
+  const int32_t* incp = reinterpret_cast<const int32_t*>(at(dm.incp));
+  const uint32_t* tri = reinterpret_cast<const uint32_t*>(at(dm.tri));
+  const double* tric = reinterpret_cast<const double*>(at(dm.tri_coef));
+  const int32_t* trip = reinterpret_cast<const int32_t*>(at(dm.trip));
+  const uint32_t* inca = reinterpret_cast<const uint32_t*>(at(dm.inc_all));
+  const int32_t* incpa = reinterpret_cast<const int32_t*>(at(dm.incp_all));
+  const RxnMeta* meta = reinterpret_cast<const RxnMeta*>(at(dm.meta));
+  const int nsp = hm.nsp, nrx = hm.nrx, CH = dm.CH, ld = dm.ld, DS = dm.DS;
+  const uint32_t inc_pad = pack_inc(nsp, 0, 0), tri_pad = pack_tri(dm.N * ld, 0);
+  auto net = [&](int r) {
+    std::map<int, int> nu;
+    for (int k : hm.rx[order[r]].r) nu[k] -= 1;
+    for (int k : hm.rx[order[r]].p) nu[k] += 1;
+    return nu;
+  };
+  // one list of rounds: distinct targets per round, entries collected per target in round order
+  auto scan = [&](const uint32_t* words, int r0, int r1, uint32_t pad, int shift, uint32_t mask,
+                  std::map<int, std::vector<int>>& by_target) {
+    for (int rd = r0; rd < r1; ++rd) {
+      std::vector<int> seen;
+      for (int l = 0; l < 32; ++l) {
+        const uint32_t e = words[size_t(rd) * 32 + l];
+        if (e == pad) continue;
+        const int t = int((e >> shift) & mask);
+        if (std::find(seen.begin(), seen.end(), t) != seen.end()) { err = "target twice in a round"; return false; }
+        seen.push_back(t);
+        by_target[t].push_back(rd * 32 + l);
+      }
+    }
+    return true;
+  };
+  int64_t inc_rounds = 0, tri_rounds = 0;
+  for (int c = 0; c < dm.nchunks; ++c) {
+    std::map<int, int> owner;        // species -> warp, incidence and Jacobian
+    std::map<std::pair<int, int>, int> want_inc;   // (k, rl) -> nu
+    std::map<std::pair<int, int>, double> want_tri;   // (M index, D index) -> coefficient
+    for (int r = c * CH; r < std::min(nrx, (c + 1) * CH); ++r) {
+      const int rl = r - c * CH;
+      const RxnMeta& mt = meta[r];
+      for (auto& kv : net(r)) {
+        if (kv.second == 0) continue;
+        want_inc[{kv.first, rl}] = kv.second;
+        std::vector<int> dl;
+        for (int k : hm.rx[order[r]].r) if (std::find(dl.begin(), dl.end(), k) == dl.end()) dl.push_back(k);
+        for (int k : hm.rx[order[r]].p) if (std::find(dl.begin(), dl.end(), k) == dl.end()) dl.push_back(k);
+        for (int s2 = 0; s2 < int(dl.size()); ++s2)
+          want_tri[{(1 + kv.first) * ld + 1 + dl[s2], rl * DS + s2}] = kv.second * hm.W[kv.first] / hm.W[dl[s2]];
+        if (mt.flags & RX_EFF)
+          for (auto& e : hm.rx[order[r]].eff)
+            want_tri[{(1 + kv.first) * ld + 1 + e.first, rl * DS + mt.dslot_eff}] =
+                kv.second * (e.second - 1.0) * hm.W[kv.first] / hm.W[e.first];
+      }
+    }
+    for (int w = 0; w < wpc; ++w) {
+      const int ci = c * wpc + w;
+      std::map<int, std::vector<int>> bi, bt;
+      if (!scan(inc, incp[ci], incp[ci + 1], inc_pad, 20, 0xfffu, bi)) return false;
+      if (!scan(tri, trip[ci], trip[ci + 1], tri_pad, 16, 0xffffu, bt)) return false;
+      inc_rounds += incp[ci + 1] - incp[ci];
+      tri_rounds += trip[ci + 1] - trip[ci];
+      for (auto& kv : bi) {
+        if (owner.count(kv.first) && owner[kv.first] != w) { err = "species in two warps of a chunk"; return false; }
+        owner[kv.first] = w;
+        int prev = -1;
+        for (int pos : kv.second) {
+          const uint32_t e = inc[pos];
+          const int rl = int((e >> 4) & 0xffffu), nu = int(e & 15u) - 8;
+          if (rl <= prev) { err = "incidence entries out of order"; return false; }
+          prev = rl;
+          auto it = want_inc.find({kv.first, rl});
+          if (it == want_inc.end() || it->second != nu) { err = "unexpected incidence entry"; return false; }
+          want_inc.erase(it);
+        }
+      }
+      for (auto& kv : bt) {
+        const int k = kv.first / ld - 1;
+        if (!owner.count(k) || owner[k] != w) { err = "Jacobian target outside its species' warp"; return false; }
+        for (int pos : kv.second) {
+          const int d = int(tri[pos] & 0xffffu);
+          auto it = want_tri.find({kv.first, d});
+          if (it == want_tri.end() || std::fabs(it->second - tric[pos]) > 1e-14 * std::fabs(it->second)) {
+            err = "unexpected Jacobian entry"; return false;
+          }
+          want_tri.erase(it);
+        }
+      }
+    }
+    if (!want_inc.empty() || !want_tri.empty()) { err = "entries missing from the chunk rounds"; return false; }
+  }
+  // whole-mechanism rounds
+  std::map<std::pair<int, int>, int> want;
+  for (int r = 0; r < nrx; ++r)
+    for (auto& kv : net(r)) if (kv.second != 0) want[{kv.first, r}] = kv.second;
+  std::map<int, int> towner;
+  int64_t all_max = 0;
+  for (int w = 0; w < wpc; ++w) {
+    std::map<int, std::vector<int>> bt;
+    if (!scan(inca, incpa[w], incpa[w + 1], inc_pad, 20, 0xfffu, bt)) return false;
+    all_max = std::max<int64_t>(all_max, incpa[w + 1] - incpa[w]);
+    for (auto& kv : bt) {
+      if (towner.count(kv.first)) { err = "target in two warps"; return false; }
+      towner[kv.first] = w;
+      const int k = kv.first >= dm.split_off ? kv.first - dm.split_off : kv.first;
+      int prev = -1;
+      for (int pos : kv.second) {
+        const uint32_t e = inca[pos];
+        const int r = int((e >> 4) & 0xffffu), nu = int(e & 15u) - 8;
+        if (r <= prev) { err = "whole-mechanism entries out of order"; return false; }
+        prev = r;
+        auto it = want.find({k, r});
+        if (it == want.end() || it->second != nu) { err = "unexpected whole-mechanism entry"; return false; }
+        want.erase(it);
+      }
+    }
+  }
+  if (!want.empty()) { err = "entries missing from the whole-mechanism rounds"; return false; }
+  out[0] = dm.nchunks; out[1] = CH; out[2] = DS; out[3] = inc_rounds; out[4] = tri_rounds;
+  out[5] = all_max; out[6] = dm.nsplit; out[7] = dm.split_off; out[8] = nsp; out[9] = nrx;
+  return true;
 }
 
 }  // namespace
@@ -924,6 +1058,21 @@ int dlbchem_last_timing(dlbchem_ctx* c, double out[8]) {
 }
 
 const char* dlbchem_last_error(const dlbchem_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+int dlbchem_table_stats(const char* mech_path, int32_t team_warps, int64_t* out) {
+  g_create_err.clear();
+  if (!mech_path || !out) return fail(nullptr, DLBCHEM_BAD_ARG, "NULL argument");
+  if (team_warps != 1 && team_warps != 2 && team_warps != 4) return fail(nullptr, DLBCHEM_BAD_ARG, "team_warps must be 1, 2 or 4");
+  dlb::HostMech hm;
+  std::string why;
+  if (!parse_mech(mech_path, hm, why)) return fail(nullptr, DLBCHEM_BAD_MECH, why);
+  std::vector<unsigned char> blob;
+  DevMech dm;
+  std::vector<int> order;
+  if (!build_tables(hm, team_warps, blob, dm, why, &order)) return fail(nullptr, DLBCHEM_BAD_MECH, why);
+  if (!verify_tables(hm, team_warps, blob, dm, order, out, why)) return fail(nullptr, DLBCHEM_BAD_MECH, "table check: " + why);
+  return DLBCHEM_OK;
+}
 
 void dlbchem_destroy(dlbchem_ctx* c) {
   if (!c) return;

@@ -48,6 +48,7 @@ def load() -> ctypes.CDLL:
     lib.dlbchem_integrate_host.argtypes = sig
     lib.dlbchem_integrate_static.argtypes = sig[:-2] + [_vp]
     lib.dlbchem_nspecies.argtypes = [_vp]
+    lib.dlbchem_table_stats.argtypes = [ctypes.c_char_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
     lib.dlbchem_nreactions.argtypes = [_vp]
     lib.dlbchem_last_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     lib.dlbchem_last_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
@@ -82,6 +83,19 @@ def load() -> ctypes.CDLL:
     lib.dlbchem_batch_destroy.argtypes = [_vp]
     _lib = lib
     return lib
+
+
+def table_stats(mech_path: str, team_warps: int) -> dict:
+    """Build and check a mechanism's round tables on the host (no GPU needed):
+    dlbchem_table_stats. Raises DlbchemError if a table check fails."""
+    lib = load()
+    out = (ctypes.c_int64 * 10)()
+    rc = lib.dlbchem_table_stats(str(mech_path).encode(), team_warps, out)
+    if rc != 0:
+        raise DlbchemError(rc, lib.dlbchem_last_error(None).decode())
+    keys = ["chunks", "chunk_size", "dslots", "inc_rounds", "tri_rounds", "all_rounds_max_warp", "nsplit",
+            "split_off", "nsp", "nrx"]
+    return dict(zip(keys, list(out)))
 
 
 def options_default() -> dlbchem_options:

@@ -141,6 +141,24 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest x over the ranks (the slowest rank sets the job's time);
+    x itself when there is one rank."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(cells_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job cells/s: every rank integrates its own field of cells_per_rank
+    (replicas, weak scaling) within the slowest rank's time per step."""
+    return world * cells_per_rank / (ms_per_step / 1e3)
+
+
 def reference_arm(args):
     """--impl reference: the FP64 oracle on the host cores (rank 0 only)."""
     world, rank, local = dist_setup()
@@ -240,13 +258,9 @@ def main():
             torch.distributed.barrier()
         wall = time.perf_counter() - t0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    dev_ms = float(np.sum(step_ms))
-    if world > 1:
-        tmax = torch.tensor([dev_ms], device=dev)
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        dev_ms = float(tmax.item())
+    dev_ms = max_over_ranks(float(np.sum(step_ms)), world, dev)
     ms_per_step = dev_ms / args.steps
-    value = world * n / (ms_per_step / 1e3)
+    value = job_throughput(n, world, ms_per_step)
 
     # roofline of the integrator kernel (algorithmic flops / its event-timed duration)
     fstep = flops_per_step(mech)

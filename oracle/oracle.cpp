@@ -18,6 +18,13 @@
 //  * Sec. 2.3: reference mapping (first qualifying cell solved, its solution
 //    mapped to the others).
 // Plain loops, row-major dense matrices, partial pivoting, no blocking or SIMD.
+//
+// Pinned (tests/test_oracle_pins.py, test_oracle_mapping.py) by the method's
+// order conditions and stability function, closed-form decays and
+// relaxations, equilibrium constants, detailed balance, linear invariants,
+// an independent stiff solver, finite-difference Jacobians and a library
+// linear solve. The end-to-end result of a multi-species mechanism has no
+// published value to compare with: parity unpinned beyond those pins.
 #include <algorithm>
 #include <atomic>
 #include <cmath>

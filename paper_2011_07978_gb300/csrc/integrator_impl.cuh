@@ -1077,7 +1077,7 @@ __global__ void __launch_bounds__(128, WPC == 1 ? 4 : (WPC == 2 ? 3 : 2)) rosenb
 // most g in every mass fraction and g*T in temperature, |sum Y' - 1| <= g, and
 // every element total changes by at most g relative. Accepted cells get
 // (T', Y'), status SURROGATE and steps 0; the others stay on the work list and
-// are integrated (the plain integrator is the fallback and the judge).
+// are integrated (the plain integrator is the fallback and the arbiter of its error).
 // ---------------------------------------------------------------------------
 template <int WPC>
 __global__ void __launch_bounds__(128) gate_kernel(const GateArgs a) {

@@ -7,13 +7,13 @@ import pytest
 from oracle import schedule
 
 # Sec. 3 configurations: (theta, x); the heavy problems are 20 % of all problems
-CONFIGS = {"C1": (1.0, 0.2), "C2": (0.8, 0.25), "C3": (0.4, 0.5), "C4": (0.2, 1.0)}
+SEC3_CASES = {"C1": (1.0, 0.2), "C2": (0.8, 0.25), "C3": (0.4, 0.5), "C4": (0.2, 1.0)}
 
 
-@pytest.mark.parametrize("name", list(CONFIGS))
+@pytest.mark.parametrize("name", list(SEC3_CASES))
 @pytest.mark.parametrize("xi", [2.0, 10.0, 50.0])
 def test_chi_max_is_max_over_mean_load(name, xi):
-    theta, x = CONFIGS[name]
+    theta, x = SEC3_CASES[name]
     costs = schedule.benchmark_loads(80, 200, theta, x, xi)
     loads = costs.sum(axis=1)
     assert x * theta == pytest.approx(0.2)
@@ -24,7 +24,7 @@ def test_printed_denominator_agrees_only_for_theta_one():
     """The printed form (theta xi + 1/x - 1) / (1/x) is the mean load for C1
     (theta = 1) and differs from it for C2 and C3."""
     xi = 10.0
-    for name, (theta, x) in CONFIGS.items():
+    for name, (theta, x) in SEC3_CASES.items():
         printed = (theta * xi + (1.0 - theta)) / ((theta * xi + (1.0 / x - 1.0)) / (1.0 / x))
         mine = schedule.chi_max(theta, xi, x)
         if theta == 1.0:
@@ -36,7 +36,7 @@ def test_printed_denominator_agrees_only_for_theta_one():
 def test_balanced_configuration_has_no_speedup():
     """C4 spreads the heavy problems evenly: chi_max = 1 and the queue cannot
     beat the unbalanced run (the paper's chi_su ~ 1 for C4)."""
-    theta, x = CONFIGS["C4"]
+    theta, x = SEC3_CASES["C4"]
     for xi in (2.0, 10.0, 50.0):
         assert schedule.chi_max(theta, xi, x) == pytest.approx(1.0, rel=1e-12)
         costs = schedule.benchmark_loads(40, 200, theta, x, xi)
@@ -47,7 +47,7 @@ def test_balanced_configuration_has_no_speedup():
 def test_longest_first_queue_reaches_the_bound(name):
     """With many problems per worker the longest-first queue lands on the mean
     load, so its speed-up over the unbalanced run is chi_max (within 1 %)."""
-    theta, x = CONFIGS[name]
+    theta, x = SEC3_CASES[name]
     xi = 10.0
     costs = schedule.benchmark_loads(40, 200, theta, x, xi)
     chi = schedule.unbalanced_makespan(costs) / schedule.lpt_makespan(costs, 40)

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -77,3 +78,30 @@ def test_create_rejects_bad_arguments_without_gpu(lib_path):
     assert lib.dlbchem_create(b"x", ctypes.byref(o), ctypes.byref(h)) == dlbchem.BAD_ARG
     assert lib.dlbchem_nspecies(None) == -1
     lib.dlbchem_destroy(None)
+
+
+def test_no_cpu_fallback_without_a_gpu(lib_path):
+    """Without a CUDA device a valid mechanism still fails to create a context
+    (DLBCHEM_CUDA): the library has no CPU path to fall back on."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2011_07978_gb300 import dlbchem
+    from synth import states
+    lib = dlbchem.load()
+    h = ctypes.c_void_p()
+    rc = lib.dlbchem_create(states.mech_path(10, 20, 0).encode(), None, ctypes.byref(h))
+    assert rc == dlbchem.CUDA and h.value is None
+    with pytest.raises(dlbchem.DlbchemError):
+        dlbchem.Context(states.mech_path(10, 20, 0))
+
+
+def test_missing_library_fails_at_import(tmp_path):
+    """If the .so is absent the binding raises instead of doing anything else."""
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2011_07978_gb300 import dlbchem\n"
+            "dlbchem.LIB_PATH = %r\n"
+            "try:\n    dlbchem.load()\nexcept ImportError as e:\n    print('raised', e)\n") % (
+        str(__import__('pathlib').Path(__file__).resolve().parents[1]), str(tmp_path / "absent.so"))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert "raised" in out.stdout and "no CPU fallback" in out.stdout, out.stdout + out.stderr

@@ -293,7 +293,7 @@ int dlbchem_last_worklist(dlbchem_ctx* ctx, int32_t* list_out, int64_t* m_out);
 
 /*
  * Diagnostic: evaluate the integrator's own exponential (Tang's table-driven
- * method) and reciprocal (Newton-Raphson from the hardware approximation)
+ * method) and reciprocal (one third-order correction of the hardware estimate)
  * next to CUDA's exp and IEEE division. x [n] device input; out [4n] device
  * output, per element: exp_own, exp_cuda, rcp_own, 1/x. Asynchronous on the
  * stream. Returns DLBCHEM_OK, BAD_ARG or CUDA.

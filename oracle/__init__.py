@@ -26,6 +26,14 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+def build_variant(dest: str, flags: list[str]) -> str:
+    """Compile the same oracle.cpp with extra compiler flags into dest (used by
+    the test that measures how much two legal builds of the same arithmetic
+    disagree, e.g. with and without FMA contraction)."""
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", *flags, SRC, "-o", dest])
+    return dest
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("max_steps", ctypes.c_int32),
                 ("isothermal", ctypes.c_int32), ("fixed_h", ctypes.c_double), ("hmin_frac", ctypes.c_double),
@@ -37,30 +45,39 @@ _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 
 
+def _bind(lib):
+    lib.orc_load.restype = ctypes.c_void_p
+    lib.orc_load.argtypes = [ctypes.c_char_p]
+    lib.orc_free.argtypes = [ctypes.c_void_p]
+    lib.orc_last_error.restype = ctypes.c_char_p
+    lib.orc_nspecies.argtypes = [ctypes.c_void_p]
+    lib.orc_nreactions.argtypes = [ctypes.c_void_p]
+    lib.orc_thermo.argtypes = [ctypes.c_void_p, ctypes.c_double] + [_dp] * 4
+    lib.orc_rates.argtypes = [ctypes.c_void_p, ctypes.c_double] + [_dp] * 5
+    lib.orc_rhs.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, ctypes.c_int]
+    lib.orc_jacobian.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, ctypes.c_int]
+    lib.orc_lu_solve.argtypes = [ctypes.c_int, _dp, _dp, _dp]
+    lib.orc_ros4_coeffs.argtypes = [_dp]
+    lib.orc_map_classify.restype = ctypes.c_int64
+    lib.orc_map_classify.argtypes = [ctypes.c_void_p, ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_uint8)]
+    lib.orc_integrate.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, _dp, _dp, _dp, _dp, _dp,
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(Opts), _dp]
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        lib.orc_load.restype = ctypes.c_void_p
-        lib.orc_load.argtypes = [ctypes.c_char_p]
-        lib.orc_free.argtypes = [ctypes.c_void_p]
-        lib.orc_last_error.restype = ctypes.c_char_p
-        lib.orc_nspecies.argtypes = [ctypes.c_void_p]
-        lib.orc_nreactions.argtypes = [ctypes.c_void_p]
-        lib.orc_thermo.argtypes = [ctypes.c_void_p, ctypes.c_double] + [_dp] * 4
-        lib.orc_rates.argtypes = [ctypes.c_void_p, ctypes.c_double] + [_dp] * 5
-        lib.orc_rhs.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, ctypes.c_int]
-        lib.orc_jacobian.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, ctypes.c_int]
-        lib.orc_lu_solve.argtypes = [ctypes.c_int, _dp, _dp, _dp]
-        lib.orc_ros4_coeffs.argtypes = [_dp]
-        lib.orc_map_classify.restype = ctypes.c_int64
-        lib.orc_map_classify.argtypes = [ctypes.c_void_p, ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
-                                         ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_uint8)]
-        lib.orc_integrate.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, _dp, _dp, _dp, _dp, _dp,
-                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
-                                      ctypes.POINTER(Opts), _dp]
-        _lib = lib
+        _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+def load_variant(path: str):
+    """A separately built copy of the oracle (see build_variant); pass it to
+    Oracle(..., lib=...)."""
+    return _bind(ctypes.CDLL(os.path.abspath(path)))
 
 
 def _p(a: np.ndarray):
@@ -87,8 +104,9 @@ def lu_solve(A: np.ndarray, b: np.ndarray) -> np.ndarray:
 class Oracle:
     """One loaded mechanism; all state vectors are y = (T, Y_1..Y_nsp)."""
 
-    def __init__(self, mech_path: str):
-        lib = _load()
+    def __init__(self, mech_path: str, lib=None):
+        lib = lib if lib is not None else _load()
+        self._lib = lib
         self._h = lib.orc_load(mech_path.encode())
         if not self._h:
             raise ValueError(lib.orc_last_error().decode())
@@ -96,32 +114,32 @@ class Oracle:
         self.nrx = lib.orc_nreactions(self._h)
 
     def __del__(self):
-        if getattr(self, "_h", None) and _lib is not None:
-            _lib.orc_free(self._h)
+        if getattr(self, "_h", None) and getattr(self, "_lib", None) is not None:
+            self._lib.orc_free(self._h)
             self._h = None
 
     def thermo(self, T: float):
         cp, h, s, g = (np.zeros(self.nsp) for _ in range(4))
-        _load().orc_thermo(self._h, T, _p(cp), _p(h), _p(s), _p(g))
+        self._lib.orc_thermo(self._h, T, _p(cp), _p(h), _p(s), _p(g))
         return cp, h, s, g
 
     def rates(self, p: float, y: np.ndarray):
         y = np.ascontiguousarray(y, dtype=np.float64)
         c = np.zeros(self.nsp)
         kf, kr, q = (np.zeros(self.nrx) for _ in range(3))
-        _load().orc_rates(self._h, p, _p(y), _p(c), _p(kf), _p(kr), _p(q))
+        self._lib.orc_rates(self._h, p, _p(y), _p(c), _p(kf), _p(kr), _p(q))
         return c, kf, kr, q
 
     def rhs(self, p: float, y: np.ndarray, isothermal: bool = False) -> np.ndarray:
         y = np.ascontiguousarray(y, dtype=np.float64)
         f = np.zeros(self.nsp + 1)
-        _load().orc_rhs(self._h, p, _p(y), _p(f), int(isothermal))
+        self._lib.orc_rhs(self._h, p, _p(y), _p(f), int(isothermal))
         return f
 
     def jacobian(self, p: float, y: np.ndarray, isothermal: bool = False) -> np.ndarray:
         y = np.ascontiguousarray(y, dtype=np.float64)
         J = np.zeros((self.nsp + 1, self.nsp + 1))
-        _load().orc_jacobian(self._h, p, _p(y), _p(J), int(isothermal))
+        self._lib.orc_jacobian(self._h, p, _p(y), _p(J), int(isothermal))
         return J
 
     def map_classify(self, T, Y, Yref, Ttol, Ytol, Tmax=0.0):
@@ -129,7 +147,7 @@ class Oracle:
         Y = np.ascontiguousarray(Y, dtype=np.float64)
         Yref = np.ascontiguousarray(Yref, dtype=np.float64)
         flag = np.zeros(T.size, dtype=np.uint8)
-        ref = _load().orc_map_classify(self._h, T.size, _p(T), _p(Y), _p(Yref), Ttol, Ytol, Tmax,
+        ref = self._lib.orc_map_classify(self._h, T.size, _p(T), _p(Y), _p(Yref), Ttol, Ytol, Tmax,
                                        flag.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
         return int(ref), flag
 
@@ -149,7 +167,7 @@ class Oracle:
         o = Opts(rtol, atol, max_steps, int(isothermal), fixed_h, hmin_frac,
                  nthreads if nthreads else (os.cpu_count() or 1), int(mapping), map_Ttol, map_Ytol, map_Tmax)
         yr = None if Yref is None else _p(np.ascontiguousarray(Yref, dtype=np.float64))
-        _load().orc_integrate(self._h, n, dt, _p(T), _p(p), _p(Y), _p(Tout), _p(Yout),
+        self._lib.orc_integrate(self._h, n, dt, _p(T), _p(p), _p(Y), _p(Tout), _p(Yout),
                               steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                               status.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(o), yr)
         return Tout, Yout, steps, status

@@ -4,11 +4,13 @@ The bar per cell: |T' - T'_oracle| <= 1e-5 T'_oracle and
 |Y' - Y'_oracle| <= 1e-9; statuses agree exactly; step counts agree within a
 few percent (bit-exact steps are not required).
 
-Where the adaptive step sequence is rounding-sensitive (the 10-species
-uniform case at rtol 1e-6: two builds of the oracle that differ only in FMA
-contraction disagree by up to 2.6e-8 in Y on 3.6 % of cells), an accept /
-reject decision taken at err ~ 1 can flip on either side and both results are
-valid integrations. There the Y bar must hold on >= 95 % of cells, and every
+Where the adaptive step sequence is rounding-sensitive, an accept / reject
+decision taken at err ~ 1 can flip on either side and both results are valid
+integrations. tests/test_oracle_rounding.py measures this with the oracle
+alone: two builds that differ only in FMA contraction disagree by more than
+1e-9 in Y on 3.6 % of the 10-species cells at rtol 1e-6 (by up to 2.6e-8),
+and on about 1-2 % of the bimodal field's cold cells at rtol 1e-5 (by up to
+2.1e-9). There the Y bar must hold on >= 95 % of cells, and every
 other cell must be valid: its error against a tight-tolerance oracle run
 (rtol 1e-10) may not exceed twice the oracle's own worst error at the same
 tolerance. The strict bar holds on every cell of the bimodal 53-species
@@ -47,7 +49,11 @@ def run_gpu(ctx, T, p, Y, dt, steps_in=None, Yref=None):
 def assert_parity(g, o, steps_tol=0.1, min_tight=1.0, tight_ref=None):
     """g, o: (T', Y', steps, status) from the GPU and the oracle.
     min_tight: fraction of cells that must meet the Y bar; the rest must be
-    valid against tight_ref = (T', Y') of a tight-tolerance oracle run."""
+    valid against tight_ref = (T', Y') of a tight-tolerance oracle run.
+    min_tight < 1 is used only where two legal builds of the oracle itself
+    disagree above 1e-9 on a fraction of cells (tests/test_oracle_rounding.py:
+    3.6 % of the 10-species cells at rtol 1e-6, 1-2 % of the bimodal cold
+    cells at rtol 1e-5); everywhere else the bar holds on every cell."""
     To, Yo, sg, stg = g
     Tr, Yr, so, sto = o
     np.testing.assert_array_equal(stg, sto)

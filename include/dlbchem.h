@@ -154,22 +154,25 @@ int dlbchem_integrate_host(dlbchem_ctx* ctx, int64_t ncells, double dt, const do
 /*
  * Queued integration that allocates nothing (the paper has no counterpart:
  * this serves callers, not the method). For flow solvers that reserve all
- * device memory up front and may not call cudaMalloc in their time loop, and
- * for code recording a CUDA graph in global capture mode, where cudaMalloc
- * is not allowed: dlbchem_integrate grows its scratch with cudaMalloc when a
- * larger field arrives, this call never does.
+ * device memory up front (their own pool, a fixed budget per GPU) and may not
+ * call cudaMalloc in their time loop, where it can fail once the pool owns
+ * the device and where it synchronises the whole device: dlbchem_integrate
+ * grows its scratch with cudaMalloc when a larger field arrives, this call
+ * never does.
  * Same arguments and results as dlbchem_integrate with the queue schedule,
  * cost keys from steps (sorted longest first when steps is non-NULL) and no
  * mapping, whatever ctx's options say about schedule and mapping; the other
- * options (tolerances, max_steps, isothermal, chunk) apply.
+ * options (tolerances, max_steps, isothermal, chunk, precision) apply.
  * Its scratch is one array of 5.3 MB compiled into the library, for up to
- * DLBCHEM_STATIC_MAX_CELLS cells; larger ncells returns BAD_ARG. Every GPU
- * that loads the library holds that array until the process exits. The
- * first call on a device looks up the array's device address (with that
- * device current; it must be ctx's device): make that first call before any
- * stream capture. All calls share the array and each call clears what it
+ * DLBCHEM_STATIC_MAX_CELLS cells; larger ncells returns BAD_ARG. CUDA loads
+ * that array lazily; dlbchem_create loads it on ctx's device, which holds it
+ * from then until the process exits (if that load failed, the first static
+ * call on the device loads it and reports a failure as CUDA). ctx's device
+ * must be current. All calls share the array and each call clears what it
  * needs, so calls that overlap on the GPU race and must be serialised by the
- * caller. Returns DLBCHEM_OK, BAD_ARG or CUDA.
+ * caller. After the call, dlbchem_last_stats describes it (no mapped cells)
+ * and dlbchem_last_worklist / dlbchem_last_timing report nothing.
+ * Returns DLBCHEM_OK, BAD_ARG or CUDA.
  */
 #define DLBCHEM_STATIC_MAX_CELLS 262144
 int dlbchem_integrate_static(dlbchem_ctx* ctx, int64_t ncells, double dt, const double* T, const double* p,

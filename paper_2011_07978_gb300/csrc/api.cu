@@ -799,6 +799,10 @@ int dlbchem_create(const char* mech_path, const dlbchem_options* opt, dlbchem_ct
   relocate(c->dm, c->d_blob);
   int rc = configure_launch(c);
   if (rc != DLBCHEM_OK) { std::string m = c->err; dlbchem_destroy(c); return fail(nullptr, rc, m); }
+  // load the fixed scratch of dlbchem_integrate_static on this device now,
+  // so that callers who reserve their memory after creating the context
+  // find it in place (a failure here is retried by the first static call)
+  (void)dlb::static_scratch_prepare(c->device);
   if (o.precision == 1) {
     const size_t slots = size_t(c->num_sms) * c->blocks_per_sm * c->teams;
     if (cudaMalloc(&c->d_m64, slots * c->dm.N * c->dm.N * sizeof(double)) != cudaSuccess) {

@@ -251,6 +251,7 @@ int mlp_shape(const dlbchem_mlp* m, int* n_in, int* n_out);
 cudaError_t launch_count_scan(int64_t n, const uint8_t* flag, int32_t* block_count, int32_t* block_off,
                               int64_t* total, cudaStream_t s);
 cudaError_t launch_lnsteps_keys(int64_t n, const float* lnsteps, int32_t* keys, cudaStream_t s);
+cudaError_t static_scratch_prepare(int dev);
 cudaError_t launch_map_scatter(int64_t n, int nsp, const uint8_t* mapped, const unsigned long long* ref,
                                const double* ref_state, const double* T, const double* Y, double* Tout,
                                double* Yout, int32_t* steps, int32_t* status, cudaStream_t s);

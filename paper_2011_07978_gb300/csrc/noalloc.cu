@@ -4,17 +4,19 @@
 // Who needs it: a flow solver that reserves all of its device memory when it
 // starts (its own pool, a fixed budget per GPU) and must not call cudaMalloc
 // inside its time loop, both because cudaMalloc can fail once the pool owns
-// the device and because it synchronises the whole device; and code that is
-// recording a CUDA graph in global capture mode, where cudaMalloc is not
-// permitted. dlbchem_integrate grows its work list and sort buffers with
-// cudaMalloc the first time it sees a larger field; this entry point instead
-// takes that scratch from one fixed array compiled into the library.
+// the device and because it synchronises the whole device.
+// dlbchem_integrate grows its work list and sort buffers with cudaMalloc the
+// first time it sees a larger field; this entry point instead takes that
+// scratch from one fixed array compiled into the library.
 //
 // The array holds the queue counter, the work list, the sort keys, their
 // ping-pong copies and the radix histograms for up to kStaticMaxCells cells
-// (5.3 MB). Every GPU that loads the library keeps it until the process
-// exits. All calls share it: calls that overlap on the GPU (two streams, two
-// threads) race on it and must be serialised by the caller.
+// (5.3 MB). It lives in this file's own module, which CUDA loads lazily: the
+// module (and with it the array's device memory) is loaded on a device when
+// its address is first looked up, and dlbchem_create does that on the
+// context's device. From then on that device holds the array until the
+// process exits. All calls share it: calls that overlap on the GPU (two
+// streams, two threads) race on it and must be serialised by the caller.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -44,8 +46,9 @@ static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
 // Device address of g_static_scratch per device ordinal. In host code the
 // symbol name is only a host-side stand-in, so the address is fetched with
-// cudaGetSymbolAddress, with the device current, the first time a device is
-// used.
+// cudaGetSymbolAddress, with the device current, once per device (from
+// dlbchem_create; a device whose look-up failed there is tried again by the
+// first static call on it).
 std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 void* g_addr[kMaxDevices] = {};
@@ -68,6 +71,16 @@ int fail(dlbchem_ctx* c, int code, const std::string& msg) {
 }
 
 }  // namespace
+
+namespace dlb {
+// Loads the scratch array's module on the current device (called by
+// dlbchem_create with the context's device current).
+cudaError_t static_scratch_prepare(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  unsigned char* base = nullptr;
+  return scratch_for_device(dev, &base);
+}
+}  // namespace dlb
 
 extern "C" int dlbchem_integrate_static(dlbchem_ctx* c, int64_t n, double dt, const double* T, const double* p,
                                         const double* Y, double* T_out, double* Y_out, int32_t* steps,
@@ -112,9 +125,26 @@ extern "C" int dlbchem_integrate_static(dlbchem_ctx* c, int64_t n, double dt, co
   a.n = n; a.T = T; a.p = p; a.Y = Y; a.Tout = T_out; a.Yout = Y_out; a.steps = steps; a.status = status;
   a.perm = list; a.nqueue = total; a.queue = 1; a.counter = counter; a.chunk = c->opt.chunk;
   a.m64 = c->opt.precision == 1 ? c->d_m64 : nullptr;   // allocated once, at creation
+  // mixed precision: count the steps whose refinement fell back to the FP64
+  // LU in the context's own counter (allocated at creation)
+  if (c->opt.precision == 1) {
+    a.fallbacks = c->d_counter + 2;
+    e = cudaMemsetAsync(c->d_counter + 2, 0, 8, s);
+    if (e != cudaSuccess) return fail(c, DLBCHEM_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  }
   int64_t grid = (n + c->teams - 1) / c->teams;
   if (grid > int64_t(c->num_sms) * c->blocks_per_sm) grid = int64_t(c->num_sms) * c->blocks_per_sm;
   e = dlb::launch_rosenbrock(c->wpc, unsigned(grid), 32 * c->wpc * c->teams, c->smem_bytes, s, a);
   if (e != cudaSuccess) return fail(c, DLBCHEM_CUDA, std::string("integrator launch: ") + cudaGetErrorString(e));
+  // what dlbchem_last_stats reports for this call (nothing mapped, no work
+  // list kept in the context, no timing)
+  c->last_n = n;
+  c->last_mapping = 0;
+  c->last_listed = 0;
+  c->timed_last = false;
+  for (int i = 0; i < 10; ++i) c->stats[i] = 0;
+  c->stats[0] = n; c->stats[2] = -1; c->stats[3] = 32 * c->wpc; c->stats[4] = c->teams;
+  c->stats[5] = grid; c->stats[6] = c->smem_bytes; c->stats[7] = 1 + (steps ? 12 : 0) + 1;
+  c->stats[9] = c->opt.precision;
   return DLBCHEM_OK;
 }

@@ -1,8 +1,10 @@
 """dlbchem_integrate_static, the queued integration for callers that may not
-allocate device memory (a solver with a fixed, pre-reserved memory budget,
-or one recording a CUDA graph), checked against dlbchem_integrate with the
-same queue schedule on two calls in a row. Kept last in collection order so
-that a failure here never hides another test; it also passes on its own."""
+allocate device memory while they run (a flow solver that reserved its whole
+memory budget at start-up), checked against dlbchem_integrate with the same
+queue schedule on two calls in a row, in FP64 and in mixed precision, and
+checked to leave the device's free memory unchanged. Kept last in collection
+order so that a failure here never hides another test; it also passes on its
+own in a fresh process."""
 import numpy as np
 import pytest
 
@@ -20,19 +22,20 @@ def _lib():
     return dlbchem
 
 
-def _field(n):
-    T, p, Y, cls = states.bimodal_states(53, 325, n, 11)
+def _field(n, seed=11):
+    T, p, Y, cls = states.bimodal_states(53, 325, n, seed)
     d = lambda a: torch.tensor(np.ascontiguousarray(a), device=DEV)
     return d(T), d(p), d(Y)
 
 
-def test_static_scratch_matches_dlbchem_integrate_twice():
+@pytest.mark.parametrize("precision", [0, 1])
+def test_static_scratch_matches_dlbchem_integrate_twice(precision):
     d = _lib()
     mech = states.mech_path(53, 325, 0)
     n = 3000
     T, p, Y = _field(n)
-    ctx_ref = d.Context(mech, rtol=1e-5, atol=1e-8, schedule=d.SCHED_QUEUE)
-    ctx = d.Context(mech, rtol=1e-5, atol=1e-8)
+    ctx_ref = d.Context(mech, rtol=1e-5, atol=1e-8, schedule=d.SCHED_QUEUE, precision=precision)
+    ctx = d.Context(mech, rtol=1e-5, atol=1e-8, precision=precision)
     steps_ref = torch.zeros(n, dtype=torch.int32, device=DEV)
     steps = torch.zeros(n, dtype=torch.int32, device=DEV)
     for call in range(2):       # second call sorts by the first call's step counts
@@ -48,6 +51,30 @@ def test_static_scratch_matches_dlbchem_integrate_twice():
         np.testing.assert_array_equal(st.cpu().numpy(), st_ref.cpu().numpy())
         np.testing.assert_array_equal(steps.cpu().numpy(), steps_ref.cpu().numpy())
         assert (st.cpu().numpy() == 0).all()
+        stats = ctx.last_stats()
+        assert stats["integrated"] == n and stats["mapped"] == 0 and stats["precision"] == precision
+        if precision == 1:
+            assert stats["fp64_fallbacks"] == ctx_ref.last_stats()["fp64_fallbacks"]
+
+
+def test_static_call_leaves_free_device_memory_unchanged():
+    """After one call (which loads the scheduling kernels), a call on a
+    larger field than before changes nothing in cudaMemGetInfo."""
+    d = _lib()
+    mech = states.mech_path(53, 325, 0)
+    ctx = d.Context(mech, rtol=1e-5, atol=1e-8)
+    small, big = _field(500, 12), _field(4000, 13)
+    outs = [(torch.empty_like(f[0]), torch.empty_like(f[2]), torch.zeros(f[0].numel(), dtype=torch.int32, device=DEV))
+            for f in (small, big)]
+    (Ts, ps, Ys), (Tb, pb, Yb) = small, big
+    ctx.integrate_static(Ts, ps, Ys, 1e-5, outs[0][0], outs[0][1], steps=outs[0][2])
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(DEV)
+    ctx.integrate_static(Tb, pb, Yb, 1e-5, outs[1][0], outs[1][1], steps=outs[1][2])
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(DEV)
+    assert free1 == free0, (free0, free1)
+    assert torch.isfinite(outs[1][0]).all()
 
 
 def test_static_scratch_rejects_fields_above_its_limit():

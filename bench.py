@@ -37,6 +37,7 @@ NSP, NRX, SEED = 53, 325, 0
 NCELLS = 262144
 DT, RTOL, ATOL = 1e-5, 1e-5, 1e-8
 MAP_TOL = 1e-4
+HEADLINE_MAPPING = 1   # 1: one reference cell per field; 2: one reference per state bucket
 METRIC = "chemistry cells/s per dt at stated T/Y error vs FP64 oracle; frac of FP64 roofline"
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2.07 GHz x 2 FP64
 # FMA lanes per clock per SM x 2 flop (= the 1.25 TFLOP/s nominal figure).
@@ -45,24 +46,29 @@ FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
 # from ncu on the 2048-cell case (1.419 MB + 0 B), scaled by cells to the full
 # 262,144-cell field; None whenever the kernel changes after the capture.
 INTEGRATOR_TRAFFIC_BYTES = 1.4190e6 * 262144 / 2048
+N_F = 3   # function evaluations per Rosenbrock step (stage 4 reuses stage 3's)
+PAPER_CONTEXT = ("paper (DLBFoam, arXiv 2011.07978): load balancing + reference mapping speed the CPU "
+                 "chemistry step up by about 10x (Spray A, 256 MPI ranks on 2x64-core AMD EPYC Rome nodes, "
+                 "FP64; chi_su 9.87 LB+RM, 2.57 LB only); context, not a target")
 
 
 def flops_per_step(m) -> float:
-    """Algorithmic FP64 flops of one attempted Rosenbrock step (FMA = 2,
-    exp/log = 20, division = 8): LU (2/3 N^3) and four solve pairs (8 N^2),
-    three rate evaluations, the Jacobian extras and assembly, stage vectors."""
+    """Algorithmic FP64 flops of one attempted step of the 4-stage Rosenbrock
+    method: (2/3) N^3 for the LU of the iteration matrix, 8 N^2 for its four
+    pairs of triangular solves, n_f (25 R + 15 N_sp) for the n_f = 3 rate and
+    right-hand-side evaluations, 90 R + 3 N^2 for the analytic Jacobian and
+    the assembly of the iteration matrix. exp and log are not flops here;
+    transcendentals_per_step counts them."""
     nsp, nrx = m.nsp, m.nrx
     N = nsp + 1
-    nr, npd = m.nu_matrix()
-    nu = npd - nr
-    n_inc = int((nu != 0).sum())
-    distinct = ((nr + npd) > 0).sum(axis=0)
-    n_tri = int(((nu != 0).sum(axis=0) * distinct).sum())
-    lu_solve = (2.0 / 3.0) * N**3 + 8.0 * N**2
-    rates = 3 * (nsp * 48 + nrx * 40 + 2 * n_inc)
-    jac = nrx * 28 + 6 * n_inc + 2 * n_tri + 4 * nsp * nsp
-    vec = 40 * N
-    return lu_solve + rates + jac + vec
+    return (2.0 / 3.0) * N**3 + 8.0 * N**2 + N_F * (25 * nrx + 15 * nsp) + 90 * nrx + 3 * N**2
+
+
+def transcendentals_per_step(m) -> dict:
+    """exp and log per attempted step, counted apart from the flops: a forward
+    rate constant per reaction and evaluation plus a reverse one per
+    reaction and evaluation and one for the Jacobian, a log per species."""
+    return {"exp": (2 * N_F + 1) * m.nrx, "log": m.nsp}
 
 
 class ClockSampler:
@@ -187,6 +193,78 @@ def reference_arm(args):
     return 0
 
 
+def conservation(mech, T, Y, To, Yo):
+    """Largest changes of the linear invariants over the field (on the GPU,
+    outside the timed region): |sum_k Y'_k - sum_k Y_k| per cell, and the
+    relative change of each element's total sum_k a_ek Y_k / W_k."""
+    import torch
+    aW = torch.tensor(mech.atoms.T / mech.W[None, :], dtype=torch.float64, device=Y.device)   # [4, nsp]
+    e0 = aW @ Y
+    e1 = aW @ Yo
+    rel = ((e1 - e0).abs() / e0.abs().clamp_min(1e-300))[e0 > 0]
+    return {"mass_defect_max": float((Yo.sum(0) - Y.sum(0)).abs().max()),
+            "sum_Y_minus_1_max": float((Yo.sum(0) - 1.0).abs().max()),
+            "element_defect_max_rel": float(rel.max()) if rel.numel() else 0.0}
+
+
+def time_form(dlbchem, mech_path, fstep, Td, pd, Yd, To, Yo, stream, *, schedule, mapping, precision, warm=1):
+    """One comparison form on the full field: warm-up calls (the first gives
+    the queue's cost keys), then one call timed with CUDA events."""
+    import torch
+    n = Td.numel()
+    ctx = dlbchem.Context(mech_path, rtol=RTOL, atol=ATOL, schedule=schedule, mapping=mapping,
+                          map_Ttol=MAP_TOL, map_Ytol=MAP_TOL, timing=1, precision=precision)
+    steps = torch.zeros(n, dtype=torch.int32, device=Td.device)
+    status = torch.zeros(n, dtype=torch.int32, device=Td.device)
+    for _ in range(warm):
+        ctx.integrate(Td, pd, Yd, DT, T_out=To, Y_out=Yo, steps=steps, status=status, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.integrate(Td, pd, Yd, DT, T_out=To, Y_out=Yo, steps=steps, status=status, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    integ = ctx.last_timing()["integrator_ms"]
+    st = ctx.last_stats()
+    total = int(steps.sum().item())
+    ach = fstep * total / (integ / 1e3) / 1e12
+    return {"cells_per_s": n / (ms / 1e3), "ms": ms, "integrator_ms": integ, "attempted_steps": total,
+            "roofline_frac": ach / FP64_PEAK_TFLOPS, "achieved_tflops": ach, "integrated": st["integrated"],
+            "mapped": st["mapped"], "failed": int((status < 0).sum().item()),
+            "fp64_fallbacks": st["fp64_fallbacks"] if precision else None}
+
+
+def fp64_probe(dlbchem, dev, stream):
+    """Measured FP64 FMA throughput (TFLOP/s) of this GPU, best of 3 launches."""
+    import torch
+    out = torch.empty(152 * 8 * 256, dtype=torch.float64, device=dev)
+    dlbchem.fp64_fma_probe(2000, out, stream)
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = dlbchem.fp64_fma_probe(20000, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best
+
+
+def class_errors(cls, To_h, Yo_h, idx, res, sel_mask):
+    """max / p99 of |dT|/T and |dY| per cell class on the sampled cells."""
+    dT = np.abs(To_h[idx] - res[0]) / res[0]
+    dY = np.abs(Yo_h[:, idx] - res[1]).max(axis=0)
+    err = {}
+    for c, name in ((0, "cold"), (1, "burnt"), (2, "front")):
+        sel = (cls[idx] == c) & sel_mask
+        if sel.any():
+            err[name] = {"max_rel_T": float(dT[sel].max()), "p99_rel_T": float(np.percentile(dT[sel], 99)),
+                         "max_abs_Y": float(dY[sel].max()), "p99_abs_Y": float(np.percentile(dY[sel], 99)),
+                         "cells": int(sel.sum())}
+    return err
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -194,8 +272,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dlbchem", choices=["dlbchem", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-arms", action="store_true", help="skip the comparison forms (plain, mixed, ...)")
     ap.add_argument("--schedule", default="queue", choices=["queue", "plain"])
-    ap.add_argument("--mapping", type=int, default=1)
+    ap.add_argument("--mapping", type=int, default=HEADLINE_MAPPING, choices=[0, 1, 2],
+                    help="0 none, 1 one reference cell, 2 one reference per state bucket")
     ap.add_argument("--ncells", type=int, default=NCELLS)
     ap.add_argument("--team-warps", type=int, default=0, choices=[0, 1, 2, 4],
                     help="warps per cell (0 = the library's automatic choice)")
@@ -220,11 +300,13 @@ def main():
 
     n = args.ncells
     T, p, Y, cls = states.bimodal_states(NSP, NRX, n, SEED + rank)
-    mech = read_mech(states.mech_path(NSP, NRX, SEED))
+    mech_path = states.mech_path(NSP, NRX, SEED)
+    mech = read_mech(mech_path)
     sched = dlbchem.SCHED_QUEUE if args.schedule == "queue" else dlbchem.SCHED_PLAIN
-    ctx = dlbchem.Context(states.mech_path(NSP, NRX, SEED), rtol=RTOL, atol=ATOL, schedule=sched,
+    prec = 1 if args.precision == "mixed" else 0
+    ctx = dlbchem.Context(mech_path, rtol=RTOL, atol=ATOL, schedule=sched,
                           mapping=args.mapping, map_Ttol=MAP_TOL, map_Ytol=MAP_TOL, timing=1,
-                          team_warps=args.team_warps, precision=1 if args.precision == "mixed" else 0)
+                          team_warps=args.team_warps, precision=prec)
     d = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
     Td, pd, Yd = d(T), d(p), d(Y)
     To, Yo = torch.empty_like(Td), torch.empty_like(Yd)
@@ -269,6 +351,8 @@ def main():
     achieved = flops_launch / (integ_avg_ms / 1e3) / 1e12
     stats = ctx.last_stats()
     status_h = status.cpu().numpy()
+    cons = conservation(mech, Td, Yd, To, Yo)
+    peak_measured = fp64_probe(dlbchem, dev, stream)
 
     # e2e: same step through the host-buffer entry point, copies inside the timed region
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -287,7 +371,9 @@ def main():
     e2e_value = world * n / float(np.mean(e2e_walls))
     h2d = Th.nbytes + ph.nbytes + Yh.nbytes + sth.nbytes
     d2h = Toh.nbytes + Yoh.nbytes + sth.nbytes + stath.nbytes
+    To_h, Yo_h = To.cpu().numpy(), Yo.cpu().numpy()
 
+    map_names = {0: "none", 1: "one reference cell", 2: "one reference per state bucket"}
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -296,38 +382,68 @@ def main():
         "config": {"workload": f"bimodal {n} cells, 53 species / 325 reactions (seeded synthetic), p 20 bar, "
                                f"dt 1e-5 s, rtol 1e-5, atol 1e-8, {'FP64' if args.precision == 'fp64' else 'mixed precision'}",
                    "schedule": args.schedule, "precision": args.precision,
-                   "mapping": bool(args.mapping), "mapping_tol": MAP_TOL, "cells_per_gpu": n,
+                   "mapping": map_names[args.mapping], "mapping_tol": MAP_TOL, "cells_per_gpu": n,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": INTEGRATOR_TRAFFIC_BYTES if args.precision == "fp64" else None,
                      "kernel": "rosenbrock_kernel", "flops_per_step": fstep,
+                     "flops_formula": "(2/3)N^3 + 8N^2 + 3(25R + 15Nsp) + 90R + 3N^2, N = Nsp + 1",
+                     "transcendentals_per_step": transcendentals_per_step(mech),
                      "steps_per_launch": total_steps / args.steps, "launch_ms": integ_avg_ms,
-                     "peak_source": "derived: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM x 2"},
+                     "peak_source": "derived: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk/SM x 2",
+                     "peak_measured": peak_measured, "frac_of_measured": achieved / peak_measured,
+                     "peak_measured_source": "dlbchem_fp64_fma_probe in this run (8 FMA chains per thread, "
+                                             "152 x 8 blocks of 256 threads), best of 3"},
         "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "clocks": clk.summary(),
         "gpu_launches": int(launches),
         "cells": {"integrated": stats["integrated"], "mapped": stats["mapped"],
                   "failed": int((status_h < 0).sum())},
+        "conservation": cons,
         "wall_s_timed": wall,
+        "paper_context": PAPER_CONTEXT,
     }
+    if not args.no_arms:
+        arms = {}
+        scratch_T, scratch_Y = torch.empty_like(Td), torch.empty_like(Yd)
+        forms = [("plain_fp64", dict(schedule=dlbchem.SCHED_PLAIN, mapping=0, precision=0, warm=1)),
+                 ("queue_one_reference_fp64", dict(schedule=dlbchem.SCHED_QUEUE, mapping=1, precision=0, warm=2)),
+                 ("queue_buckets_fp64", dict(schedule=dlbchem.SCHED_QUEUE, mapping=2, precision=0, warm=2)),
+                 ("queue_buckets_mixed", dict(schedule=dlbchem.SCHED_QUEUE, mapping=2, precision=1, warm=2))]
+        for name, kw in forms:
+            same = (kw["schedule"] == sched and kw["mapping"] == args.mapping and kw["precision"] == prec)
+            if same or (kw["mapping"] == 2 and HEADLINE_MAPPING != 2):
+                continue
+            arms[name] = time_form(dlbchem, mech_path, fstep, Td, pd, Yd, scratch_T, scratch_Y, stream, **kw)
+        line["forms"] = arms
     if rank == 0 and not args.no_cpu_baseline:
+        import oracle
         idx, res, cwall, cores = cpu_oracle_sample(T, p, Y, 1024, 0, mapping=False)
-        # error of this field's GPU result on the sampled cells vs the oracle (unmapped cells)
-        To_h, Yo_h = To.cpu().numpy(), Yo.cpu().numpy()
-        integrated = status_h[idx] == 0
-        dT = np.abs(To_h[idx] - res[0]) / res[0]
-        dY = np.abs(Yo_h[:, idx] - res[1]).max(axis=0)
-        err = {}
-        for c, name in ((0, "cold"), (1, "burnt"), (2, "front")):
-            sel = (cls[idx] == c) & integrated
-            if sel.any():
-                err[name] = {"max_rel_T": float(dT[sel].max()), "p99_rel_T": float(np.percentile(dT[sel], 99)),
-                             "max_abs_Y": float(dY[sel].max()), "p99_abs_Y": float(np.percentile(dY[sel], 99)),
-                             "cells": int(sel.sum())}
-        line["error_vs_oracle"] = err
+        # error of this field's GPU result vs the oracle: integrated cells on the
+        # random sample; mapped cells (a sample per class) against the oracle
+        # integrating them instead of mapping them (the mapping approximation)
+        line["error_vs_oracle"] = class_errors(cls, To_h, Yo_h, idx, res, status_h[idx] == 0)
+        mapped = np.flatnonzero(status_h == 1)
+        if mapped.size:
+            rng = np.random.default_rng(7)
+            pick = np.sort(np.concatenate([rng.choice(mapped[cls[mapped] == c], size=min(256, int((cls[mapped] == c).sum())),
+                                                      replace=False) for c in (0, 1, 2) if (cls[mapped] == c).any()]))
+            orc = oracle.Oracle(mech_path)
+            resm = orc.integrate(T[pick], p[pick], np.ascontiguousarray(Y[:, pick]), DT, rtol=RTOL, atol=ATOL,
+                                 nthreads=cores)
+            line["mapped_error_vs_unmapped_oracle"] = class_errors(cls, To_h, Yo_h, pick, resm,
+                                                                   np.ones(pick.size, bool))
+        # single-threaded oracle on a stratified sample (cold, burnt, front)
+        one = states.stratified_sample(cls, 16, 3)
+        t1 = time.perf_counter()
+        oracle.Oracle(mech_path).integrate(T[one], p[one], np.ascontiguousarray(Y[:, one]), DT, rtol=RTOL,
+                                           atol=ATOL, nthreads=1)
+        w1 = time.perf_counter() - t1
         line["cpu_baseline"] = {"value": idx.size / cwall, "unit": "cells/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{idx.size} random cells of the field, no mapping, {cwall:.1f} s wall"}
+                                "sample": f"{idx.size} random cells of the field, no mapping, {cwall:.1f} s wall",
+                                "single_thread": {"value": one.size / w1, "unit": "cells/s",
+                                                  "sample": f"{one.size} cells, 16 per class, {w1:.1f} s wall"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -303,6 +303,17 @@ int dlbchem_last_worklist(dlbchem_ctx* ctx, int32_t* list_out, int64_t* m_out);
  */
 int dlbchem_check_math(dlbchem_ctx* ctx, int64_t n, const double* x, double* out, void* cuda_stream);
 
+/*
+ * Measurement aid (not a step of the method): FP64 FMA throughput probe, the
+ * measured denominator of the integrator's FP64 roofline fraction. Launches
+ * nout / 256 blocks of 256 threads; every thread runs `iters` rounds of eight
+ * independent FP64 FMA chains and writes one value to out[nout] (device,
+ * nout a positive multiple of 256). *flops receives the launch's FP64 flop
+ * count (2 per FMA); time the launch with events on the same stream.
+ * Asynchronous. Returns DLBCHEM_OK, BAD_ARG or CUDA.
+ */
+int dlbchem_fp64_fma_probe(int64_t iters, double* out, int64_t nout, int64_t* flops, void* cuda_stream);
+
 /* Message of the last failed call on ctx, or of the last failed create when
  * ctx is NULL. Never NULL; "" when there was no error. Owned by the library. */
 const char* dlbchem_last_error(const dlbchem_ctx* ctx);

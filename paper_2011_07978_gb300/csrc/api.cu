@@ -1033,6 +1033,14 @@ int dlbchem_check_math(dlbchem_ctx* c, int64_t n, const double* x, double* out, 
   return e == cudaSuccess ? DLBCHEM_OK : cuda_fail(c, e, "check_math launch");
 }
 
+int dlbchem_fp64_fma_probe(int64_t iters, double* out, int64_t nout, int64_t* flops, void* stream) {
+  if (iters < 1 || !out || nout < 256 || nout % 256 != 0 || nout / 256 > (int64_t(1) << 31) - 1)
+    return DLBCHEM_BAD_ARG;
+  if (flops) *flops = 2 * 8 * iters * nout;
+  cudaError_t e = dlb::launch_fp64_fma_probe(iters, out, nout, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? DLBCHEM_OK : DLBCHEM_CUDA;
+}
+
 int dlbchem_last_worklist(dlbchem_ctx* c, int32_t* list_out, int64_t* m_out) {
   if (!c || !list_out || !m_out) return DLBCHEM_BAD_ARG;
   *m_out = -1;

@@ -230,6 +230,7 @@ const void* rosenbrock_kernel_ptr_w4();
 cudaError_t launch_rosenbrock(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
 const void* rosenbrock_kernel_ptr(int wpc);
 cudaError_t launch_check_math(int64_t n, const double* x, const double* tab, double* out, cudaStream_t s);
+cudaError_t launch_fp64_fma_probe(int64_t iters, double* out, int64_t nout, cudaStream_t s);
 cudaError_t launch_map_classify(int64_t n, int nsp, const double* T, const double* Y, const double* Yref,
                                 double Ttol, double Ytol, double Tmax, uint8_t* qual, unsigned long long* ref,
                                 double* ref_state, int32_t* block_count, int32_t* block_off, int64_t* total,

@@ -22,6 +22,25 @@ __global__ void check_math_kernel(int64_t n, const double* __restrict__ x, const
   out[4 * i + 3] = 1.0 / x[i];
 }
 
+// FP64 FMA throughput probe: eight independent chains per thread, bounded
+// values (a <- a m + c with |m| < 1), one result per thread kept live.
+__global__ void __launch_bounds__(256) fp64_fma_probe_kernel(int64_t iters, double* __restrict__ out) {
+  const int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  double a0 = 1e-3 * threadIdx.x, a1 = a0 + 1.0, a2 = a0 + 2.0, a3 = a0 + 3.0;
+  double a4 = a0 + 4.0, a5 = a0 + 5.0, a6 = a0 + 6.0, a7 = a0 + 7.0;
+  const double m = 0.9999999, c = 1e-7 * (1 + (blockIdx.x & 7));
+  for (int64_t i = 0; i < iters; ++i) {
+    a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+    a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
+  }
+  out[t] = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+}
+
+cudaError_t launch_fp64_fma_probe(int64_t iters, double* out, int64_t nout, cudaStream_t s) {
+  fp64_fma_probe_kernel<<<unsigned(nout / 256), 256, 0, s>>>(iters, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check_math(int64_t n, const double* x, const double* tab, double* out, cudaStream_t s) {
   check_math_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(n, x, tab, out);
   return cudaGetLastError();

@@ -54,6 +54,7 @@ def load() -> ctypes.CDLL:
     lib.dlbchem_last_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
     lib.dlbchem_last_worklist.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int64)]
     lib.dlbchem_check_math.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp]
+    lib.dlbchem_fp64_fma_probe.argtypes = [ctypes.c_int64, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _vp]
     lib.dlbchem_last_error.argtypes = [_vp]
     lib.dlbchem_last_error.restype = ctypes.c_char_p
     lib.dlbchem_destroy.argtypes = [_vp]
@@ -96,6 +97,20 @@ def table_stats(mech_path: str, team_warps: int) -> dict:
     keys = ["chunks", "chunk_size", "dslots", "inc_rounds", "tri_rounds", "all_rounds_max_warp", "nsplit",
             "split_off", "nsp", "nrx"]
     return dict(zip(keys, list(out)))
+
+
+def fp64_fma_probe(iters: int, out, stream=None) -> int:
+    """dlbchem_fp64_fma_probe on a CUDA float64 tensor `out` (numel a multiple
+    of 256); returns the launch's FP64 flop count."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(out.device)
+    flops = ctypes.c_int64(0)
+    rc = load().dlbchem_fp64_fma_probe(int(iters), _ptr(out), out.numel(), ctypes.byref(flops),
+                                       ctypes.c_void_p(stream.cuda_stream))
+    if rc != OK:
+        raise DlbchemError(rc, "dlbchem_fp64_fma_probe failed")
+    return int(flops.value)
 
 
 def options_default() -> dlbchem_options:

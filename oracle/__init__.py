@@ -61,6 +61,9 @@ def _bind(lib):
     lib.orc_map_classify.restype = ctypes.c_int64
     lib.orc_map_classify.argtypes = [ctypes.c_void_p, ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_uint8)]
+    lib.orc_map_buckets.restype = ctypes.c_int64
+    lib.orc_map_buckets.argtypes = [ctypes.c_void_p, ctypes.c_int64, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_int64)]
     lib.orc_integrate.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, _dp, _dp, _dp, _dp, _dp,
                                   ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(Opts), _dp]
@@ -151,10 +154,23 @@ class Oracle:
                                        flag.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
         return int(ref), flag
 
+    def map_buckets(self, T, Y, Ttol, Ytol, Tmax=0.0):
+        """One reference per state bucket: (ref[n] int64, -1 for unmapped
+        cells; flag[n] uint8, 1 for mapped cells)."""
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        Y = np.ascontiguousarray(Y, dtype=np.float64)
+        flag = np.zeros(T.size, dtype=np.uint8)
+        ref = np.zeros(T.size, dtype=np.int64)
+        self._lib.orc_map_buckets(self._h, T.size, _p(T), _p(Y), Ttol, Ytol, Tmax,
+                                  flag.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                  ref.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+        return ref, flag
+
     def integrate(self, T, p, Y, dt, rtol=1e-6, atol=1e-10, max_steps=100000, isothermal=False,
                   fixed_h=0.0, hmin_frac=1e-20, nthreads=None, mapping=False, map_Ttol=1e-4,
                   map_Ytol=1e-4, map_Tmax=0.0, Yref=None):
-        """Integrate cells over dt. T[n], p[n], Y[nsp, n] -> (T', Y', steps, status)."""
+        """Integrate cells over dt. T[n], p[n], Y[nsp, n] -> (T', Y', steps, status).
+        mapping: 0/False none, 1/True one reference cell, 2 one reference per state bucket."""
         T = np.ascontiguousarray(T, dtype=np.float64)
         p = np.ascontiguousarray(np.broadcast_to(p, T.shape), dtype=np.float64)
         Y = np.ascontiguousarray(Y, dtype=np.float64)

@@ -32,6 +32,7 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <map>
 #include <string>
 #include <thread>
 #include <vector>
@@ -495,6 +496,63 @@ void parallel_for(int64_t n, int nthreads, F&& body) {
   for (auto& x : th) x.join();
 }
 
+// Reference mapping with one reference per state bucket (Sec. 2.3 generalised
+// from one reference cell to many, as multi-zone models bin cells by state).
+// A cell is eligible when its state is finite, T > 0, T < Tmax (if Tmax > 0)
+// and both tolerances are positive. Its bucket key is
+//   kT  = the IEEE-754 bits of T shifted right by s, s = the largest integer
+//         with 2^(s-52) <= Ttol (T on a relative grid finer than Ttol), and
+//   q_k = floor(Y_k * (1/Ytol)) for every species (Y on a grid of width Ytol),
+// with every |Y_k / Ytol| below 2^62 (else the cell is not eligible). The
+// reference of a bucket is its lowest-index eligible cell (the paper's "first
+// reference cell found"), and a cell of the bucket is mapped to it when it is
+// not the reference and meets the criterion of Sec. 2.3 against it:
+// max_k |Y_k - Yr_k| < Ytol and |T - Tr| < Ttol * Tr. ref[i] is the reference
+// of a mapped cell and -1 otherwise; flag[i] = 1 for mapped cells. Returns the
+// number of mapped cells.
+int bucket_shift(double Ttol) {
+  int e = 0;
+  std::frexp(Ttol, &e);       // Ttol = m 2^e, m in [0.5, 1)
+  return std::min(62, std::max(0, 51 + e));
+}
+
+int64_t map_buckets(const Mech& m, int64_t n, const double* T, const double* Y, double Ttol, double Ytol,
+                    double Tmax, uint8_t* flag, int64_t* ref) {
+  for (int64_t i = 0; i < n; ++i) { flag[i] = 0; ref[i] = -1; }
+  if (!(Ttol > 0) || !(Ytol > 0)) return 0;
+  const int s = bucket_shift(Ttol);
+  const double c = 1.0 / Ytol;
+  std::map<std::vector<int64_t>, int64_t> first;   // bucket key -> lowest index
+  std::vector<std::vector<int64_t>> key(n);
+  for (int64_t i = 0; i < n; ++i) {
+    bool ok = std::isfinite(T[i]) && T[i] > 0 && (Tmax <= 0 || T[i] < Tmax);
+    std::vector<int64_t> k(m.nsp + 1);
+    if (ok) {
+      uint64_t bits;
+      std::memcpy(&bits, &T[i], 8);
+      k[0] = int64_t(bits >> s);
+      for (int j = 0; j < m.nsp && ok; ++j) {
+        const double v = Y[(size_t)j * n + i] * c;
+        ok = std::isfinite(v) && std::fabs(v) < 4611686018427387904.0;   // 2^62
+        if (ok) k[1 + j] = (int64_t)std::floor(v);
+      }
+    }
+    if (!ok) continue;
+    key[i] = k;
+    first.emplace(k, i);   // keeps the first (lowest) index of each bucket
+  }
+  int64_t mapped = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (key[i].empty()) continue;
+    const int64_t r = first.at(key[i]);
+    if (r == i) continue;
+    double d = 0;
+    for (int j = 0; j < m.nsp; ++j) d = std::max(d, std::fabs(Y[(size_t)j * n + i] - Y[(size_t)j * n + r]));
+    if (d < Ytol && std::fabs(T[i] - T[r]) < Ttol * T[r]) { flag[i] = 1; ref[i] = r; ++mapped; }
+  }
+  return mapped;
+}
+
 struct Handle {
   Mech m;
 };
@@ -584,11 +642,14 @@ int orc_integrate(void* hd, int64_t n, double dt, const double* T, const double*
   const Mech& m = static_cast<Handle*>(hd)->m;
   const int N = m.nsp + 1;
   std::vector<uint8_t> flag(n, 0);
+  std::vector<int64_t> refs(n, -1);
   int64_t ref = -1;
-  if (o->mapping && n > 0) {
+  if (o->mapping == 1 && n > 0) {
     std::vector<double> y0(m.nsp);
     for (int k = 0; k < m.nsp; ++k) y0[k] = Y[(size_t)k * n + 0];
     ref = orc_map_classify(hd, n, T, Y, Yref ? Yref : y0.data(), o->map_Ttol, o->map_Ytol, o->map_Tmax, flag.data());
+  } else if (o->mapping == 2 && n > 0) {
+    map_buckets(m, n, T, Y, o->map_Ttol, o->map_Ytol, o->map_Tmax, flag.data(), refs.data());
   }
   std::vector<double> out((size_t)N * n);
   std::vector<int32_t> st(n), sp(n);
@@ -602,11 +663,21 @@ int orc_integrate(void* hd, int64_t n, double dt, const double* T, const double*
   });
   for (int64_t i = 0; i < n; ++i) {
     if (!flag[i]) continue;
-    // mapped: copy the reference cell's increments (keeps sum Y = 1)
-    out[i] = T[i] + (out[ref] - T[ref]);
-    for (int k = 0; k < m.nsp; ++k)
-      out[(size_t)(1 + k) * n + i] = Y[(size_t)k * n + i] + (out[(size_t)(1 + k) * n + ref] - Y[(size_t)k * n + ref]);
-    st[i] = st[ref] < 0 ? st[ref] : ST_MAPPED;
+    if (o->mapping == 1) {
+      // mapped: copy the reference cell's increments (keeps sum Y = 1)
+      out[i] = T[i] + (out[ref] - T[ref]);
+      for (int k = 0; k < m.nsp; ++k)
+        out[(size_t)(1 + k) * n + i] = Y[(size_t)k * n + i] + (out[(size_t)(1 + k) * n + ref] - Y[(size_t)k * n + ref]);
+      st[i] = st[ref] < 0 ? st[ref] : ST_MAPPED;
+    } else {
+      // one reference per bucket: the same increment, written as the
+      // reference's result plus the cell's offset from the reference's input
+      const int64_t r = refs[i];
+      out[i] = out[r] + (T[i] - T[r]);
+      for (int k = 0; k < m.nsp; ++k)
+        out[(size_t)(1 + k) * n + i] = out[(size_t)(1 + k) * n + r] + (Y[(size_t)k * n + i] - Y[(size_t)k * n + r]);
+      st[i] = st[r] < 0 ? st[r] : ST_MAPPED;
+    }
     sp[i] = 0;
   }
   for (int64_t i = 0; i < n; ++i) {
@@ -616,6 +687,13 @@ int orc_integrate(void* hd, int64_t n, double dt, const double* T, const double*
     if (status) status[i] = st[i];
   }
   return 0;
+}
+
+// One reference per state bucket (map_buckets above). Returns the number of
+// mapped cells; ref[i] is the reference of a mapped cell, else -1.
+int64_t orc_map_buckets(void* hd, int64_t n, const double* T, const double* Y, double Ttol, double Ytol,
+                        double Tmax, uint8_t* flag, int64_t* ref) {
+  return map_buckets(static_cast<Handle*>(hd)->m, n, T, Y, Ttol, Ytol, Tmax, flag, ref);
 }
 
 }  // extern "C"

@@ -80,7 +80,15 @@ typedef struct dlbchem_options {
   double hmin_frac;     /* H_UNDERFLOW when h < hmin_frac * dt (1e-20) */
   int32_t schedule;     /* DLBCHEM_SCHED_PLAIN or DLBCHEM_SCHED_QUEUE */
   int32_t chunk;        /* cells per queue pull (1) */
-  int32_t mapping;      /* 1: reference mapping on */
+  int32_t mapping;      /* 0: off; 1: one reference cell (the lowest-index cell within
+                           tolerance of Yref, Sec. 2.3); 2: one reference per state bucket
+                           (Sec. 2.3 generalised): the bucket key is (the IEEE bits of T
+                           shifted right by s, s the largest with 2^(s-52) <= map_Ttol;
+                           floor(Y_k / map_Ytol) per species), the reference is the bucket's
+                           lowest-index eligible cell (finite state, T > 0, T < map_Tmax if
+                           set), and a cell maps when the keys agree and it meets the Sec. 2.3
+                           criterion against it. Mapped cells get T' = T'_r + (T - T_r),
+                           Y' = Y'_r + (Y - Y_r): the reference's increment. */
   int32_t timing;       /* 1: record CUDA events around each kernel (see dlbchem_last_timing) */
   double map_Ttol;      /* relative temperature tolerance (1e-4) */
   double map_Ytol;      /* absolute composition tolerance (1e-4) */
@@ -131,7 +139,8 @@ int dlbchem_set_options(dlbchem_ctx* ctx, const dlbchem_options* opt);
  *          (accepted + rejected; 0 for mapped cells).
  *   status [ncells] int32, nullable: per-cell DLBCHEM_CELL_* codes.
  *   Yref   [nsp] device pointer, nullable: the reference composition of the
- *          mapping criterion; NULL uses cell 0's composition.
+ *          mapping criterion with mapping 1; NULL uses cell 0's composition.
+ *          Ignored with mapping 2.
  * ncells == 0 is a no-op. Mapping and the queue follow ctx's options.
  * Returns DLBCHEM_OK, BAD_ARG (NULL pointer, dt <= 0 or not finite, ncells
  * < 0), CUDA or OOM (workspace growth failed).
@@ -264,8 +273,9 @@ int dlbchem_nreactions(const dlbchem_ctx* ctx);
 
 /*
  * Statistics of the last completed call on ctx (synchronises its stream).
- *   out[0] cells integrated, out[1] cells mapped, out[2] reference cell
- *   index (-1 if none), out[3] team size in threads, out[4] teams per CTA,
+ *   out[0] cells integrated, out[1] cells mapped (or taken from the
+ *   surrogate), out[2] reference cell index with mapping 1 (-1 if none or
+ *   with mapping 2; see dlbchem_last_mapping), out[3] team size in threads, out[4] teams per CTA,
  *   out[5] CTAs launched by the integrator, out[6] dynamic shared memory
  *   bytes per CTA, out[7] kernel launches in the call, out[8] steps whose
  *   FP32 refinement fell back to the FP64 LU, out[9] precision mode.
@@ -293,6 +303,16 @@ int dlbchem_last_timing(dlbchem_ctx* ctx, double out[8]);
  * Returns DLBCHEM_OK, BAD_ARG or CUDA.
  */
 int dlbchem_last_worklist(dlbchem_ctx* ctx, int32_t* list_out, int64_t* m_out);
+
+/*
+ * Which cells the last call mapped, and to which reference (Sec. 2.3): writes
+ * ref_out[i] = the reference cell of mapped cell i, -1 for every other cell,
+ * into ref_out, a DEVICE array of at least ncells int32, and ncells into
+ * *n_out (host). Only valid after a call with mapping 1 or 2; otherwise
+ * *n_out = -1. Runs on and synchronises the stream of the last call.
+ * Returns DLBCHEM_OK, BAD_ARG or CUDA.
+ */
+int dlbchem_last_mapping(dlbchem_ctx* ctx, int32_t* ref_out, int64_t* n_out);
 
 /*
  * Diagnostic: evaluate the integrator's own exponential (Tang's table-driven

@@ -258,6 +258,7 @@ bool valid_opts(const dlbchem_options* o, std::string& why) {
   if (o->schedule != DLBCHEM_SCHED_PLAIN && o->schedule != DLBCHEM_SCHED_QUEUE) { why = "unknown schedule"; return false; }
   if (o->chunk < 1) { why = "chunk must be >= 1"; return false; }
   if (!(o->map_Ttol >= 0) || !(o->map_Ytol >= 0) || !(o->map_Tmax >= 0)) { why = "mapping tolerances must be >= 0"; return false; }
+  if (o->mapping < 0 || o->mapping > 2) { why = "mapping must be 0, 1 or 2"; return false; }
   if (o->team_warps != 0 && o->team_warps != 1 && o->team_warps != 2 && o->team_warps != 4) { why = "team_warps must be 0, 1, 2 or 4"; return false; }
   if (o->precision != 0 && o->precision != 1) { why = "precision must be 0 or 1"; return false; }
   if (!(o->gate >= 0)) { why = "gate must be >= 0"; return false; }
@@ -605,6 +606,12 @@ int ensure_ws(dlbchem_ctx* c, int64_t n) {
   const size_t o_k = off; off += al(size_t(n) * 4);
   const size_t o_ka = off; off += al(size_t(n) * 4);
   const size_t o_h = off; off += al(size_t(nb) * 256 * 4);
+  int64_t cap = 1024;
+  while (cap < 2 * n) cap *= 2;
+  const size_t o_tk = off; off += al(size_t(cap) * 8);
+  const size_t o_tm = off; off += al(size_t(cap) * 4);
+  const size_t o_sl = off; off += al(size_t(n) * 4);
+  const size_t o_ri = off; off += al(size_t(n) * 4);
   if (cudaMalloc(&c->d_ws, off) != cudaSuccess) { c->d_ws = nullptr; return fail(c, DLBCHEM_OOM, "workspace allocation failed"); }
   char* b = static_cast<char*>(c->d_ws);
   c->w_flag = reinterpret_cast<uint8_t*>(b + o_flag);
@@ -617,6 +624,11 @@ int ensure_ws(dlbchem_ctx* c, int64_t n) {
   c->w_keys = reinterpret_cast<uint32_t*>(b + o_k);
   c->w_keys_alt = reinterpret_cast<uint32_t*>(b + o_ka);
   c->w_hist = reinterpret_cast<int32_t*>(b + o_h);
+  c->w_tkey = reinterpret_cast<unsigned long long*>(b + o_tk);
+  c->w_tmin = reinterpret_cast<int32_t*>(b + o_tm);
+  c->w_slot = reinterpret_cast<int32_t*>(b + o_sl);
+  c->w_refidx = reinterpret_cast<int32_t*>(b + o_ri);
+  c->tcap = cap;
   c->ws_cap = n;
   return DLBCHEM_OK;
 }
@@ -860,10 +872,18 @@ int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, con
     e = dlb::mlp_predict(c->mlp, n, c->hm.nsp, T, p, Y, dt, c->l_X, c->l_out, c->l_lnsteps, c->l_dT, c->l_dY, s);
   if (predictor && e == cudaSuccess) e = dlb::launch_lnsteps_keys(n, c->l_lnsteps, c->l_keys, s);
   const int32_t* keys_in = predictor ? c->l_keys : steps;
-  if (mapping) {
+  const bool buckets = c->opt.mapping == 2;
+  if (mapping && !buckets) {
     if (e == cudaSuccess)
       e = dlb::launch_map_classify(n, c->hm.nsp, T, Y, Yref, c->opt.map_Ttol, c->opt.map_Ytol, c->opt.map_Tmax,
                                    c->w_flag, d_ref, c->w_ref_state, c->w_bcount, c->w_boff, c->w_total, s);
+  } else if (buckets) {
+    // one reference per state bucket; mapped cells' outputs receive their
+    // offsets from the reference's input here
+    if (e == cudaSuccess)
+      e = dlb::launch_bucket_map(n, c->hm.nsp, T, Y, T_out, Y_out, c->opt.map_Ttol, c->opt.map_Ytol,
+                                 c->opt.map_Tmax, c->w_tkey, c->w_tmin, c->tcap, c->w_slot, c->w_flag, c->w_refidx,
+                                 c->w_bcount, c->w_boff, c->w_total, s);
   } else if (surrogate && e == cudaSuccess) {
     e = cudaMemsetAsync(c->w_flag, 0, size_t(n), s);
   }
@@ -919,19 +939,21 @@ int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, con
   if (e != cudaSuccess) return cuda_fail(c, e, "integrator launch");
   // stage 4: mapped cells take the reference cell's increment
   rec(5);
-  if (mapping && e == cudaSuccess)
+  if (mapping && !buckets && e == cudaSuccess)
     e = dlb::launch_map_scatter(n, c->hm.nsp, c->w_flag, d_ref, c->w_ref_state, T, Y, T_out, Y_out, steps, status, s);
+  if (buckets && e == cudaSuccess)
+    e = dlb::launch_bucket_scatter(n, c->hm.nsp, c->w_flag, c->w_refidx, T_out, Y_out, steps, status, s);
   rec(6);
   if (e != cudaSuccess) return cuda_fail(c, e, "mapping scatter");
   c->timed_last = timing;
   c->last_n = n;
-  c->last_mapping = mapping || surrogate;
+  c->last_mapping = mapping ? c->opt.mapping : (surrogate ? 3 : 0);
   c->last_listed = listed;
   c->stats[0] = n; c->stats[1] = 0; c->stats[2] = -1; c->stats[3] = 32 * c->wpc; c->stats[4] = c->teams;
   // kernels launched by this call: classify (init, classify, flag, scan, compact) or the list init,
   // four sort passes of three kernels, the integrator, the scatter
   c->stats[5] = grid; c->stats[6] = c->smem_bytes;
-  c->stats[7] = (learned ? 9 : 0) + (predictor ? 1 : 0) + (mapping ? 4 : 0) + (surrogate ? 3 : 0) +
+  c->stats[7] = (learned ? 9 : 0) + (predictor ? 1 : 0) + (mapping ? (buckets ? 3 : 4) : 0) + (surrogate ? 3 : 0) +
                 ((mapping || surrogate) ? 1 : ((queue || predictor) ? 1 : 0)) + ((queue && keys_in) ? 12 : 0) + 1 +
                 (mapping ? 1 : 0);
   return DLBCHEM_OK;
@@ -1011,11 +1033,11 @@ int dlbchem_last_stats(dlbchem_ctx* c, int64_t out[10]) {
     int64_t m = 0;
     unsigned long long r = 0;
     if ((e = cudaMemcpy(&m, c->w_total, 8, cudaMemcpyDeviceToHost)) != cudaSuccess ||
-        (e = cudaMemcpy(&r, c->d_counter + 1, 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        (c->last_mapping == 1 && (e = cudaMemcpy(&r, c->d_counter + 1, 8, cudaMemcpyDeviceToHost)) != cudaSuccess))
       return cuda_fail(c, e, "cudaMemcpy");
     c->stats[0] = m;
     c->stats[1] = c->last_n - m;
-    c->stats[2] = int64_t(r) < c->last_n ? int64_t(r) : -1;
+    c->stats[2] = (c->last_mapping == 1 && int64_t(r) < c->last_n) ? int64_t(r) : -1;
   }
   if (c->opt.precision == 1 && c->last_n > 0) {
     unsigned long long fb = 0;
@@ -1023,6 +1045,18 @@ int dlbchem_last_stats(dlbchem_ctx* c, int64_t out[10]) {
     c->stats[8] = int64_t(fb);
   }
   for (int i = 0; i < 10; ++i) out[i] = c->stats[i];
+  return DLBCHEM_OK;
+}
+
+int dlbchem_last_mapping(dlbchem_ctx* c, int32_t* ref_out, int64_t* n_out) {
+  if (!c || !ref_out || !n_out) return DLBCHEM_BAD_ARG;
+  *n_out = -1;
+  if ((c->last_mapping != 1 && c->last_mapping != 2) || c->last_n <= 0) return DLBCHEM_OK;
+  cudaError_t e = dlb::launch_mapping_refs(c->last_n, c->w_flag, c->w_refidx,
+                                           c->last_mapping == 1 ? c->d_counter + 1 : nullptr, ref_out, c->last_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->last_stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "mapping references");
+  *n_out = c->last_n;
   return DLBCHEM_OK;
 }
 

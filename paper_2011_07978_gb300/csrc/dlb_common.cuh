@@ -253,6 +253,15 @@ cudaError_t launch_count_scan(int64_t n, const uint8_t* flag, int32_t* block_cou
                               int64_t* total, cudaStream_t s);
 cudaError_t launch_lnsteps_keys(int64_t n, const float* lnsteps, int32_t* keys, cudaStream_t s);
 cudaError_t static_scratch_prepare(int dev);
+int bucket_shift(double Ttol);
+cudaError_t launch_bucket_map(int64_t n, int nsp, const double* T, const double* Y, double* Tout, double* Yout,
+                              double Ttol, double Ytol, double Tmax, unsigned long long* tkey, int32_t* tmin,
+                              int64_t cap, int32_t* slot, uint8_t* flag, int32_t* refidx, int32_t* block_count,
+                              int32_t* block_off, int64_t* total, cudaStream_t s);
+cudaError_t launch_bucket_scatter(int64_t n, int nsp, const uint8_t* flag, const int32_t* refidx, double* Tout,
+                                  double* Yout, int32_t* steps, int32_t* status, cudaStream_t s);
+cudaError_t launch_mapping_refs(int64_t n, const uint8_t* flag, const int32_t* refidx,
+                                const unsigned long long* single_ref, int32_t* out, cudaStream_t s);
 cudaError_t launch_map_scatter(int64_t n, int nsp, const uint8_t* mapped, const unsigned long long* ref,
                                const double* ref_state, const double* T, const double* Y, double* Tout,
                                double* Yout, int32_t* steps, int32_t* status, cudaStream_t s);

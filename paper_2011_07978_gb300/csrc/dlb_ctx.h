@@ -50,10 +50,15 @@ struct dlbchem_ctx {
   int32_t *w_bcount = nullptr, *w_boff = nullptr, *w_list = nullptr, *w_list_alt = nullptr, *w_hist = nullptr;
   uint32_t *w_keys = nullptr, *w_keys_alt = nullptr;
   int64_t* w_total = nullptr;
+  // one reference per state bucket: hash table (keys, lowest index per slot),
+  // per-cell slot and reference index
+  unsigned long long* w_tkey = nullptr;
+  int32_t *w_tmin = nullptr, *w_slot = nullptr, *w_refidx = nullptr;
+  int64_t tcap = 0;
   cudaEvent_t ev[8] = {};
   bool timed_last = false;
   int64_t last_n = 0;
-  int last_mapping = 0;
+  int last_mapping = 0;   // 0 none, 1 one reference, 2 buckets, 3 surrogate gate only
   int last_listed = 0;
   // host-buffer staging
   double* d_stage = nullptr;

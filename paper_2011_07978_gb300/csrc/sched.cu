@@ -11,9 +11,20 @@
 //    Algorithm 1) with a stable LSD radix sort, so the persistent integrator
 //    pulls the most expensive cells first.
 //  * scatter: mapped cells receive the reference cell's increments.
+//  * buckets (Sec. 2.3 generalised to one reference per state bucket): a
+//    cell's bucket key is (T's IEEE bits >> s, floor(Y_k / Ytol) per
+//    species), with s the largest integer with 2^(s-52) <= Ttol; cells hash
+//    their key into an open-addressing table whose slots keep the lowest
+//    cell index (the bucket's reference); a cell maps to its bucket's
+//    reference when the keys agree exactly and it meets the Sec. 2.3
+//    criterion against it. Before the integrator runs, a mapped cell's
+//    output arrays hold its offset from the reference's input, and the
+//    scatter adds the reference's result to it.
 // Every kernel here is HBM- or latency-bound and tiny next to the integrator.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 
 #include "dlb_common.cuh"
@@ -217,6 +228,129 @@ __global__ void map_scatter_kernel(int64_t n, int nsp, const uint8_t* __restrict
   }
 }
 
+// ---- one reference per state bucket -----------------------------------------
+
+// splitmix64 finaliser (Steele, Lea and Flood, OOPSLA 2014): mixes the key
+// words into the table hash.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+constexpr double kTwo62 = 4611686018427387904.0;
+
+// Eligibility and hash of cell i's bucket key; false when not eligible
+// (non-finite state, T <= 0, T >= Tmax when Tmax > 0, |Y_k / Ytol| >= 2^62).
+__device__ __forceinline__ bool bucket_hash(int64_t i, int64_t n, int nsp, const double* __restrict__ T,
+                                            const double* __restrict__ Y, int s, double c, double Tmax,
+                                            unsigned long long& h) {
+  const double t = T[i];
+  if (!(isfinite(t) && t > 0.0 && (Tmax <= 0.0 || t < Tmax))) return false;
+  unsigned long long x = mix64((unsigned long long)__double_as_longlong(t) >> s);
+  for (int k = 0; k < nsp; ++k) {
+    const double v = __dmul_rn(Y[int64_t(k) * n + i], c);
+    if (!(fabs(v) < kTwo62)) return false;
+    x = mix64(x ^ (unsigned long long)__double2ll_rd(v) ^ (0x9e3779b97f4a7c15ull * unsigned(k + 1)));
+  }
+  h = x | 1ull;   // 0 marks an empty table slot
+  return true;
+}
+
+// Insert every eligible cell's key; each slot keeps the lowest cell index.
+// Linear probing over at most the whole table (capacity >= 2 n, never full).
+__global__ void bucket_insert_kernel(int64_t n, int nsp, const double* __restrict__ T, const double* __restrict__ Y,
+                                     int s, double c, double Tmax, unsigned long long* __restrict__ tkey,
+                                     int32_t* __restrict__ tmin, unsigned mask, int32_t* __restrict__ slot) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  unsigned long long h;
+  int32_t out = -1;
+  if (bucket_hash(i, n, nsp, T, Y, s, c, Tmax, h)) {
+    unsigned pos = unsigned(h) & mask;
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+      const unsigned long long old = atomicCAS(&tkey[pos], 0ull, h);
+      if (old == 0ull || old == h) {
+        atomicMin(&tmin[pos], int32_t(i));
+        out = int32_t(pos);
+        break;
+      }
+      pos = (pos + 1u) & mask;
+    }
+  }
+  slot[i] = out;
+}
+
+// A cell maps to its slot's lowest index r when r != i, the keys agree
+// exactly (no hash collision) and max_k |Y_k - Y_r,k| < Ytol,
+// |T - T_r| < Ttol T_r. Mapped cells get flag 1, ref = r and, in the output
+// arrays, their offset from r's input (T - T_r, Y - Y_r). A reference is
+// never mapped (it is the lowest index of its own slot, and a cell enters one
+// slot only), so no thread writes a value another thread reads, also when
+// the outputs alias the inputs. Per block: the number of unmapped cells.
+__global__ void bucket_classify_kernel(int64_t n, int nsp, const double* T, const double* Y,
+                                       double* Tout, double* Yout, int s, double c, double Ttol, double Ytol,
+                                       const int32_t* __restrict__ tmin, const int32_t* __restrict__ slot,
+                                       uint8_t* __restrict__ flag, int32_t* __restrict__ refidx,
+                                       int32_t* __restrict__ block_count) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  bool mapped = false;
+  int32_t r = -1;
+  if (i < n) {
+    const int32_t sl = slot[i];
+    if (sl >= 0) {
+      r = tmin[sl];
+      if (r != i) {
+        const double ti = T[i], tr = T[r];
+        bool same = ((unsigned long long)__double_as_longlong(ti) >> s) ==
+                    ((unsigned long long)__double_as_longlong(tr) >> s);
+        double d = 0.0;
+        for (int k = 0; k < nsp; ++k) {
+          const double yi = Y[int64_t(k) * n + i], yr = Y[int64_t(k) * n + r];
+          same = same && __double2ll_rd(__dmul_rn(yi, c)) == __double2ll_rd(__dmul_rn(yr, c));
+          d = fmax(d, fabs(yi - yr));
+        }
+        mapped = same && d < Ytol && fabs(ti - tr) < Ttol * tr;
+      }
+    }
+    if (mapped) {
+      refidx[i] = r;
+      Tout[i] = T[i] - T[r];
+      for (int k = 0; k < nsp; ++k) Yout[int64_t(k) * n + i] = Y[int64_t(k) * n + i] - Y[int64_t(k) * n + r];
+    }
+    flag[i] = mapped ? 1 : 0;
+  }
+  const int cnt = __syncthreads_count(i < n && !mapped);
+  if (threadIdx.x == 0) block_count[blockIdx.x] = cnt;
+}
+
+// Mapped cells: T' = T'_r + (T - T_r), Y' = Y'_r + (Y - Y_r) (the offsets are
+// already in the outputs); steps 0; status MAPPED, or the reference's failure.
+__global__ void bucket_scatter_kernel(int64_t n, int nsp, const uint8_t* __restrict__ flag,
+                                      const int32_t* __restrict__ refidx, double* Tout, double* Yout,
+                                      int32_t* __restrict__ steps, int32_t* status) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= n || flag[i] != 1) return;
+  const int64_t r = refidx[i];
+  Tout[i] = Tout[r] + Tout[i];
+  for (int k = 0; k < nsp; ++k) Yout[int64_t(k) * n + i] = Yout[int64_t(k) * n + r] + Yout[int64_t(k) * n + i];
+  if (steps) steps[i] = 0;
+  if (status) {
+    const int32_t sr = status[r];
+    status[i] = sr < 0 ? sr : CELL_MAPPED;
+  }
+}
+
+// Per cell: the reference index of a mapped cell, -1 otherwise (both modes).
+__global__ void mapping_refs_kernel(int64_t n, const uint8_t* __restrict__ flag, const int32_t* __restrict__ refidx,
+                                    const unsigned long long* __restrict__ single_ref, int32_t* __restrict__ out) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  out[i] = flag[i] == 1 ? (single_ref ? int32_t(*single_ref) : refidx[i]) : -1;
+}
+
 // ---- host-side orchestration ------------------------------------------------
 
 int64_t tiles_of(int64_t m) { return (m + kSchedThreads - 1) / kSchedThreads; }
@@ -291,6 +425,48 @@ cudaError_t launch_map_scatter(int64_t n, int nsp, const uint8_t* mapped, const 
                                double* Yout, int32_t* steps, int32_t* status, cudaStream_t s) {
   map_scatter_kernel<<<unsigned(tiles_of(n)), kSchedThreads, 0, s>>>(n, nsp, mapped, ref, ref_state, T, Y, Tout, Yout,
                                                                      steps, status);
+  return cudaGetLastError();
+}
+
+int bucket_shift(double Ttol) {
+  int e = 0;
+  std::frexp(Ttol, &e);   // Ttol = m 2^e, m in [0.5, 1): 2^(s-52) <= Ttol for s = 51 + e
+  return std::min(62, std::max(0, 51 + e));
+}
+
+cudaError_t launch_bucket_map(int64_t n, int nsp, const double* T, const double* Y, double* Tout, double* Yout,
+                              double Ttol, double Ytol, double Tmax, unsigned long long* tkey, int32_t* tmin,
+                              int64_t cap, int32_t* slot, uint8_t* flag, int32_t* refidx, int32_t* block_count,
+                              int32_t* block_off, int64_t* total, cudaStream_t s) {
+  const unsigned nb = unsigned(tiles_of(n));
+  cudaError_t e;
+  if (!(Ttol > 0.0) || !(Ytol > 0.0)) {   // nothing maps: every cell on the work list
+    if ((e = cudaMemsetAsync(flag, 0, size_t(n), s)) != cudaSuccess) return e;
+    count_kernel<<<nb, kSchedThreads, 0, s>>>(n, flag, block_count);
+    scan_counts_kernel<<<1, kSchedThreads, 0, s>>>(int(nb), block_count, block_off, total);
+    return cudaGetLastError();
+  }
+  const int sh = bucket_shift(Ttol);
+  const double c = 1.0 / Ytol;
+  if ((e = cudaMemsetAsync(tkey, 0, size_t(cap) * 8, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(tmin, 0x7f, size_t(cap) * 4, s)) != cudaSuccess) return e;   // 0x7f7f7f7f > any index
+  bucket_insert_kernel<<<nb, kSchedThreads, 0, s>>>(n, nsp, T, Y, sh, c, Tmax, tkey, tmin, unsigned(cap - 1), slot);
+  bucket_classify_kernel<<<nb, kSchedThreads, 0, s>>>(n, nsp, T, Y, Tout, Yout, sh, c, Ttol, Ytol, tmin, slot, flag,
+                                                      refidx, block_count);
+  scan_counts_kernel<<<1, kSchedThreads, 0, s>>>(int(nb), block_count, block_off, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_scatter(int64_t n, int nsp, const uint8_t* flag, const int32_t* refidx, double* Tout,
+                                  double* Yout, int32_t* steps, int32_t* status, cudaStream_t s) {
+  bucket_scatter_kernel<<<unsigned(tiles_of(n)), kSchedThreads, 0, s>>>(n, nsp, flag, refidx, Tout, Yout, steps,
+                                                                        status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mapping_refs(int64_t n, const uint8_t* flag, const int32_t* refidx,
+                                const unsigned long long* single_ref, int32_t* out, cudaStream_t s) {
+  mapping_refs_kernel<<<unsigned(tiles_of(n)), kSchedThreads, 0, s>>>(n, flag, refidx, single_ref, out);
   return cudaGetLastError();
 }
 

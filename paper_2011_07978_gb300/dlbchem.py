@@ -53,6 +53,7 @@ def load() -> ctypes.CDLL:
     lib.dlbchem_last_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     lib.dlbchem_last_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
     lib.dlbchem_last_worklist.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.dlbchem_last_mapping.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int64)]
     lib.dlbchem_check_math.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp]
     lib.dlbchem_fp64_fma_probe.argtypes = [ctypes.c_int64, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _vp]
     lib.dlbchem_last_error.argtypes = [_vp]
@@ -233,6 +234,13 @@ class Context:
         """Copy the last work list into the int32 CUDA tensor `out`; returns its length."""
         m = ctypes.c_int64()
         self._check(load().dlbchem_last_worklist(self._h, _ptr(out), ctypes.byref(m)))
+        return m.value
+
+    def last_mapping(self, out):
+        """dlbchem_last_mapping into the int32 CUDA tensor `out`: the reference of
+        each mapped cell, -1 elsewhere. Returns ncells, or -1 without mapping."""
+        m = ctypes.c_int64()
+        self._check(load().dlbchem_last_mapping(self._h, _ptr(out), ctypes.byref(m)))
         return m.value
 
     def attach_mlp(self, mlp):

@@ -199,35 +199,49 @@ def test_larger_mechanisms(kind):
     assert_parity(g, o)
 
 
-def test_bimodal_full_size_sampled_parity():
+@pytest.mark.parametrize("mapping", [1, 2])
+def test_bimodal_full_size_sampled_parity(mapping):
     """The 262,144-cell, 53-species bimodal workload in the launch
     configuration bench.py times (cost-sorted queue keyed by a warm-up call's
-    steps, reference mapping at 1e-4). 4096 cells of every class, integrated
-    by the oracle one by one: statuses equal, T within 1e-5 relative on every
-    cell, Y within 1e-9 on at least 99 % and every other cell valid against a
-    tight-tolerance solution; every mapped cell carries the reference cell's
-    increment bit for bit."""
+    steps, reference mapping at 1e-4: one reference cell, or one per state
+    bucket). 4096 cells of every class, integrated by the oracle one by one:
+    statuses equal, T within 1e-5 relative on every cell, Y within 1e-9 on at
+    least 99 % and every other cell valid against a tight-tolerance solution
+    (two legal oracle builds already disagree above 1e-9 on 1-2 % of cold
+    cells); every mapped cell carries its reference's increment bit for bit,
+    and the mapped set and references equal the oracle's."""
     d = dlb()
     mech = states.mech_path(53, 325, 0)
     n = 262144
     T, p, Y, cls = states.bimodal_states(53, 325, n, 0)
-    ctx = d.Context(mech, rtol=1e-5, atol=1e-8, schedule=d.SCHED_QUEUE, mapping=1, map_Ttol=1e-4, map_Ytol=1e-4)
+    ctx = d.Context(mech, rtol=1e-5, atol=1e-8, schedule=d.SCHED_QUEUE, mapping=mapping, map_Ttol=1e-4,
+                    map_Ytol=1e-4)
     warm = run_gpu(ctx, T, p, Y, 1e-5)
     g = run_gpu(ctx, T, p, Y, 1e-5, steps_in=warm[2])
-    ref = ctx.last_stats()["ref"]
+    refs_t = torch.empty(n, dtype=torch.int32, device=DEV)
+    assert ctx.last_mapping(refs_t) == n
+    refs = refs_t.cpu().numpy().astype(np.int64)
     mapped = g[3] == d.CELL_MAPPED
-    assert ((g[3] == 0) | mapped).all() and mapped.sum() > 0 and ref >= 0
-    np.testing.assert_array_equal(g[0][mapped], T[mapped] + (g[0][ref] - T[ref]))
-    np.testing.assert_array_equal(g[1][:, mapped], Y[:, mapped] + (g[1][:, ref] - Y[:, ref])[:, None])
+    np.testing.assert_array_equal(mapped, refs >= 0)
+    orc = oracle.Oracle(mech)
+    if mapping == 1:
+        ref = ctx.last_stats()["ref"]
+        assert (refs[mapped] == ref).all()
+        np.testing.assert_array_equal(g[0][mapped], T[mapped] + (g[0][ref] - T[ref]))
+        np.testing.assert_array_equal(g[1][:, mapped], Y[:, mapped] + (g[1][:, ref] - Y[:, ref])[:, None])
+    else:
+        oref, oflag = orc.map_buckets(T, Y, 1e-4, 1e-4)
+        np.testing.assert_array_equal(refs, oref)
+        r = refs[mapped]
+        np.testing.assert_array_equal(g[0][mapped], g[0][r] + (T[mapped] - T[r]))
+        np.testing.assert_array_equal(g[1][:, mapped], g[1][:, r] + (Y[:, mapped] - Y[:, r]))
+        assert mapped[cls == states.COLD].mean() > 0.99 and mapped[cls == states.BURNT].mean() > 0.9
+        assert not mapped[cls == states.FRONT].any()
+    assert ((g[3] == 0) | mapped).all() and mapped.sum() > 0
     idx = states.stratified_sample(cls, 4096, 0)
     idx = idx[~mapped[idx]]
-    orc = oracle.Oracle(mech)
     o = orc.integrate(T[idx], p[idx], Y[:, idx], 1e-5, rtol=1e-5, atol=1e-8)
     gs = tuple(a[..., idx] for a in g)
-    # At this sample size a fraction of a percent of cells have a rounding-sensitive
-    # step sequence (measured: 99.7 % within 1e-9, the rest below 3e-9). Those cells
-    # must be as close to a tight-tolerance solution as the oracle's own error at
-    # rtol 1e-5 (max over them and 512 random sampled cells, times two).
     dY = np.abs(gs[1] - o[1]).max(axis=0)
     rng = np.random.default_rng(5)
     sub = np.union1d(np.flatnonzero(dY > 1e-9), rng.choice(idx.size, size=min(512, idx.size), replace=False))
@@ -240,6 +254,12 @@ def test_bimodal_full_size_sampled_parity():
     assert (np.abs(gs[0] - o[0]) / o[0]).max() <= 1e-5
     assert (dY <= 1e-9).mean() >= 0.99, ((dY <= 1e-9).mean(), dY.max())
     assert np.mean(np.abs(gs[2].astype(float) - o[2]) / np.maximum(o[2], 1)) <= 0.1
+    # the mapping approximation itself: mapped cells against the oracle integrating them
+    pick = np.sort(np.random.default_rng(6).choice(np.flatnonzero(mapped), size=min(512, int(mapped.sum())),
+                                                   replace=False))
+    om = orc.integrate(T[pick], p[pick], Y[:, pick], 1e-5, rtol=1e-5, atol=1e-8)
+    print(f"mapping {mapping}: {int(mapped.sum())} cells mapped; on {pick.size} of them vs the unmapped oracle "
+          f"max |dT|/T {np.max(np.abs(g[0][pick] - om[0]) / om[0]):.2e}, max |dY| {np.abs(g[1][:, pick] - om[1]).max():.2e}")
     # whole-field properties that hold at any size
     np.testing.assert_allclose(g[1].sum(0), 1.0, atol=1e-12)
     assert np.isfinite(g[0]).all() and (g[0] > 0).all()
@@ -268,6 +288,45 @@ def test_mapping_matches_oracle_and_zero_tolerance_is_identity():
     np.testing.assert_array_equal(g[2][flag.astype(bool)], 0)
     # zero tolerances: identical to the plain unmapped run, bit for bit
     ctx0 = d.Context(mech, rtol=1e-5, atol=1e-8, mapping=1, map_Ttol=0.0, map_Ytol=0.0)
+    g0 = run_gpu(ctx0, T, p, Y, 1e-5)
+    plain = run_gpu(d.Context(mech, rtol=1e-5, atol=1e-8), T, p, Y, 1e-5)
+    assert ctx0.last_stats()["mapped"] == 0
+    for a, b in zip(g0, plain):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_bucket_mapping_matches_oracle_and_zero_tolerance_is_identity():
+    """One reference per state bucket: the same references as the oracle (bit
+    for bit), mapped cells equal T'_r + (T - T_r), parity with the oracle's
+    mapped run; in place (outputs aliasing inputs) gives the same bits; zero
+    tolerances map nothing and equal the unmapped run."""
+    d = dlb()
+    mech = states.mech_path(53, 325, 0)
+    T, p, Y, cls = _bimodal(3000, 3)
+    ctx = d.Context(mech, rtol=1e-5, atol=1e-8, mapping=2, map_Ttol=1e-4, map_Ytol=1e-4, schedule=d.SCHED_QUEUE)
+    g = run_gpu(ctx, T, p, Y, 1e-5)
+    refs_t = torch.empty(T.size, dtype=torch.int32, device=DEV)
+    assert ctx.last_mapping(refs_t) == T.size
+    refs = refs_t.cpu().numpy().astype(np.int64)
+    orc = oracle.Oracle(mech)
+    oref, oflag = orc.map_buckets(T, Y, 1e-4, 1e-4)
+    np.testing.assert_array_equal(refs, oref)
+    m = oflag.astype(bool)
+    assert ctx.last_stats()["mapped"] == int(m.sum()) > 1000
+    np.testing.assert_array_equal(g[3] == d.CELL_MAPPED, m)
+    np.testing.assert_array_equal(g[0][m], g[0][refs[m]] + (T[m] - T[refs[m]]))
+    np.testing.assert_array_equal(g[1][:, m], g[1][:, refs[m]] + (Y[:, m] - Y[:, refs[m]]))
+    o = orc.integrate(T, p, Y, 1e-5, rtol=1e-5, atol=1e-8, mapping=2, map_Ttol=1e-4, map_Ytol=1e-4)
+    assert_parity(g, o)
+    # in place: T_out / Y_out are the input tensors
+    Td, pd, Yd = (torch.tensor(np.ascontiguousarray(a), device=DEV) for a in (T, p, Y))
+    st = torch.zeros(T.size, dtype=torch.int32, device=DEV)
+    ctx.integrate(Td, pd, Yd, 1e-5, T_out=Td, Y_out=Yd, status=st)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Td.cpu().numpy(), g[0])
+    np.testing.assert_array_equal(Yd.cpu().numpy(), g[1])
+    # zero tolerances: identical to the unmapped run, bit for bit
+    ctx0 = d.Context(mech, rtol=1e-5, atol=1e-8, mapping=2, map_Ttol=0.0, map_Ytol=0.0)
     g0 = run_gpu(ctx0, T, p, Y, 1e-5)
     plain = run_gpu(d.Context(mech, rtol=1e-5, atol=1e-8), T, p, Y, 1e-5)
     assert ctx0.last_stats()["mapped"] == 0

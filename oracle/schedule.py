@@ -55,3 +55,66 @@ def lpt_makespan(costs, workers: int) -> float:
     for c in sorted(np.ravel(costs), reverse=True):
         heapq.heappush(loads, heapq.heappop(loads) + float(c))
     return max(loads)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 of the paper (stage 2 of the balancer): pair the least loaded
+# process (a receiver) with the most loaded one (a sender), move the load
+# min(mean - L_receiver, L_sender - mean) between them as a number of
+# problems whose cost adds up to it, and advance past whichever of the two
+# reached the mean. Transfers below 0.01 of the mean load are dropped.
+# Readings where the paper is silent: the sender gives away problems from
+# the end of its list (those it would solve last), as many as bring their
+# cost sum closest to the load to move; "|L_i - mean| ~ 0" is a relative
+# tolerance of 1e-12; a dropped transfer still updates the bookkeeping.
+# ---------------------------------------------------------------------------
+
+def balance_operations(costs, threshold: float = 0.01):
+    """costs: one sequence of per-problem costs (t_cpu of the previous step)
+    per process. Returns (operations, mean load): operations is a list of
+    (sender, receiver, number of problems, moved cost)."""
+    loads = np.array([float(np.sum(c)) for c in costs])
+    nproc = loads.size
+    mean = loads.sum() / nproc
+    order = np.argsort(loads, kind="stable")     # ranks by ascending load
+    L = loads[order].copy()
+    remaining = [list(np.asarray(c, dtype=float)) for c in costs]
+    ops = []
+    i, j = 0, nproc - 1
+    while i < j:
+        dL = min(mean - L[i], L[j] - mean)
+        receiver, sender = int(order[i]), int(order[j])
+        if dL >= threshold * mean and dL > 0:
+            pool = remaining[sender]
+            tail = np.cumsum(pool[::-1])          # cost of sending the last 1, 2, ... problems
+            k = int(np.argmin(np.abs(tail - dL))) + 1 if tail.size else 0
+            if k > 0:
+                moved = float(tail[k - 1])
+                del pool[len(pool) - k:]
+                ops.append((sender, receiver, k, moved))
+        L[i] += dL
+        L[j] -= dL
+        if abs(L[i] - mean) <= 1e-12 * mean:
+            i += 1
+        else:
+            j -= 1
+    return ops, mean
+
+
+def balanced_loads(costs, ops) -> np.ndarray:
+    """Per-process load after the operations (a process solves what it kept
+    and what it received)."""
+    loads = np.array([float(np.sum(c)) for c in costs])
+    for s, r, k, moved in ops:
+        loads[s] -= moved
+        loads[r] += moved
+    return loads
+
+
+def chi_su_model(nproc: int, nprob: int, theta: float, x: float, xi: float) -> float:
+    """Speed-up of Algorithm 1 on a Sec. 3 configuration (communication not
+    counted): slowest process without balancing over slowest process after
+    the operations."""
+    costs = benchmark_loads(nproc, nprob, theta, x, xi)
+    ops, _ = balance_operations(list(costs))
+    return unbalanced_makespan(costs) / float(balanced_loads(list(costs), ops).max())

@@ -166,3 +166,62 @@ def test_surrogate_gate_and_fallback(trained):
     err = np.abs(Yo[:, acc] - Yo0[:, acc]).max(axis=0) if acc.any() else np.zeros(0)
     print(f"surrogate accepted {acc.sum()} of {n} cells; max |dY| vs integrator on accepted "
           f"{err.max() if err.size else 0:.2e}")
+
+
+def test_gate_accept_branch_with_a_host_built_network():
+    """Drives the gate's accept branch with a network built on the host: all
+    weights and biases zero and output normalisation mu = 0, sd = 1, so it
+    proposes exactly a zero increment (T' = T, Y' = Y). On nearly inert cold
+    cells the trapezoid defect dt/2 (f(y) + f(y')) = dt f(y) is below the gate,
+    so they are accepted; hot cells are not. Accepted cells meet the gate
+    against the oracle's right-hand side, and their error against the
+    oracle's integration (the whole increment they skip) is stated and at most
+    twice the gate; the other cells are integrated exactly as without the
+    surrogate."""
+    d = lib()
+    mech = states.mech_path(10, 20, 0)
+    n = 3000
+    T, p, Y = states.uniform_states(10, n, 5)
+    T[: n // 2] = np.random.default_rng(1).uniform(300, 380, n // 2)
+    dt = 1e-6
+    net = d.MLP(13, 256, 12)
+    net.set_params(torch.zeros(net.nparams, dtype=torch.float32, device=DEV))
+    net.set_norm(np.zeros(13), np.ones(13), np.zeros(12), np.ones(12))
+    dd = lambda a: torch.tensor(np.ascontiguousarray(a), device=DEV)
+    gate = 1e-4
+    ctx = d.Context(mech, rtol=1e-6, atol=1e-10, surrogate=1, gate=gate)
+    ctx.attach_mlp(net)
+    st = torch.zeros(n, dtype=torch.int32, device=DEV)
+    ss = torch.zeros(n, dtype=torch.int32, device=DEV)
+    To, Yo = ctx.integrate(dd(T), dd(p), dd(Y), dt, steps=st, status=ss)
+    plain = d.Context(mech, rtol=1e-6, atol=1e-10)
+    To0, Yo0 = plain.integrate(dd(T), dd(p), dd(Y), dt)
+    torch.cuda.synchronize()
+    ss, st = ss.cpu().numpy(), st.cpu().numpy()
+    To, Yo, To0, Yo0 = To.cpu().numpy(), Yo.cpu().numpy(), To0.cpu().numpy(), Yo0.cpu().numpy()
+    acc = ss == d.CELL_SURROGATE
+    assert acc.sum() > 0.2 * n and not acc[T > 1500].any()
+    assert ((ss == 0) | acc).all() and (st[acc] == 0).all()
+    np.testing.assert_array_equal(To[acc], T[acc])
+    np.testing.assert_array_equal(Yo[:, acc], Y[:, acc])
+    np.testing.assert_array_equal(To[~acc], To0[~acc])
+    np.testing.assert_array_equal(Yo[:, ~acc], Yo0[:, ~acc])
+    orc = oracle.Oracle(mech)
+    for i in np.flatnonzero(acc):
+        y0 = np.concatenate([[T[i]], Y[:, i]])
+        f0 = orc.rhs(p[i], y0)
+        defect = -dt * f0           # y' = y0: the trapezoid defect is -dt/2 (f0 + f0)
+        assert abs(defect[0]) <= gate * T[i] * (1 + 1e-6) and np.abs(defect[1:]).max() <= gate * (1 + 1e-6)
+    # and the cells the gate turned down really miss it (a zero increment
+    # keeps sum Y and the element totals, so only the defect can fail)
+    for i in np.flatnonzero(~acc)[:200]:
+        y0 = np.concatenate([[T[i]], Y[:, i]])
+        f0 = orc.rhs(p[i], y0)
+        assert abs(dt * f0[0]) > gate * T[i] * (1 - 1e-6) or np.abs(dt * f0[1:]).max() > gate * (1 - 1e-6)
+    sel = np.flatnonzero(acc)
+    o = orc.integrate(T[sel], p[sel], Y[:, sel], dt, rtol=1e-6, atol=1e-10)
+    err_T = np.abs(To[sel] - o[0]) / o[0]
+    err_Y = np.abs(Yo[:, sel] - o[1]).max(axis=0)
+    print(f"zero-increment surrogate accepted {sel.size} of {n} cells; vs the oracle's integration "
+          f"max |dT|/T {err_T.max():.2e}, max |dY| {err_Y.max():.2e}")
+    assert err_Y.max() <= 2 * gate and err_T.max() <= 2 * gate

@@ -452,8 +452,9 @@ def test_mixed_precision_bimodal_sample():
 def test_batched_graph_matches_single_calls():
     """Three uneven meshes over two mechanisms (53/325 twice with different
     dt, 100/1000 once) in one captured graph, autotuned: every cell equals a
-    single dlbchem_integrate call with the same team size bit for bit, and a
-    second replay reproduces the first."""
+    single dlbchem_integrate call with the same team size bit for bit, a
+    second replay reproduces the first, and 256 sampled cells of every mesh
+    meet the parity bar against the oracle."""
     d = dlb()
     m53, m100 = states.mech_path(53, 325, 0), states.mech_path(100, 1000, 1)
     spec = [(m53, 53, 1500, 1e-6, 21), (m100, 100, 96, 1e-6, 22), (m53, 53, 2500, 1e-5, 23)]
@@ -482,7 +483,17 @@ def test_batched_graph_matches_single_calls():
         assert (a["ss"] == 0).all()
         tw = info[0 if mech == m53 else 1]["team_warps"]
         ctx = d.Context(mech, rtol=1e-6, atol=1e-10, team_warps=tw)
-        g = run_gpu(ctx, a["T"].cpu().numpy(), a["p"].cpu().numpy(), a["Y"].cpu().numpy(), dt)
+        T0, p0, Y0 = a["T"].cpu().numpy(), a["p"].cpu().numpy(), a["Y"].cpu().numpy()
+        g = run_gpu(ctx, T0, p0, Y0, dt)
         np.testing.assert_array_equal(a["To"].cpu().numpy(), g[0])
         np.testing.assert_array_equal(a["Yo"].cpu().numpy(), g[1])
+        # the batched results against the oracle on a sample of every mesh
+        # (rtol 1e-6: the rounding-sensitive bar with a tight-tolerance check)
+        idx = np.sort(np.random.default_rng(n).choice(n, size=min(256, n), replace=False))
+        orc = oracle.Oracle(mech)
+        o = orc.integrate(T0[idx], p0[idx], Y0[:, idx], dt, rtol=1e-6, atol=1e-10)
+        tight = orc.integrate(T0[idx], p0[idx], Y0[:, idx], dt, rtol=1e-10, atol=1e-16)
+        gb = (a["To"].cpu().numpy()[idx], a["Yo"].cpu().numpy()[:, idx], a["st"].cpu().numpy()[idx],
+              a["ss"].cpu().numpy()[idx])
+        assert_parity(gb, o, min_tight=0.95, tight_ref=tight[:2])
     b.close()

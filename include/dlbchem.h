@@ -106,7 +106,10 @@ typedef struct dlbchem_options {
   int32_t predictor;    /* 1: order the queue by the attached network's predicted step counts
                            (no previous call needed); steps[] is then only written */
   int32_t surrogate;    /* 1: try the attached network's increments first; cells that pass the
-                           gate get status DLBCHEM_CELL_SURROGATE, the others are integrated */
+                           gate get status DLBCHEM_CELL_SURROGATE, the others are integrated;
+                           2: the same with the proposal y + dt f(y) + the network's output (an
+                           explicit Euler step corrected by a network trained on the residual
+                           increment - dt f(y), see dlbchem_rhs) */
   double gate;          /* surrogate gate tolerance (default 1e-4): trapezoid defect per mass
                            fraction (relative for T), |sum Y' - 1| and relative element change */
 } dlbchem_options;
@@ -322,6 +325,18 @@ int dlbchem_last_mapping(dlbchem_ctx* ctx, int32_t* ref_out, int64_t* n_out);
  * stream. Returns DLBCHEM_OK, BAD_ARG or CUDA.
  */
 int dlbchem_check_math(dlbchem_ctx* ctx, int64_t n, const double* x, double* out, void* cuda_stream);
+
+/*
+ * Right-hand side of every cell's ODE (Sec. 1: the thermochemical state
+ * evolves by dPhi/dt = f(Phi); here f = (dT/dt, dY_k/dt) of a constant-
+ * pressure ideal gas with the mechanism's rates, isothermal per ctx's
+ * options). T, p [ncells], Y [nsp][ncells] device inputs; fT [ncells],
+ * fY [nsp][ncells] device outputs (K/s, 1/s). Cells with a non-finite state,
+ * T <= 0 or p <= 0 get NaN. Asynchronous on the stream.
+ * Returns DLBCHEM_OK, BAD_ARG or CUDA.
+ */
+int dlbchem_rhs(dlbchem_ctx* ctx, int64_t ncells, const double* T, const double* p, const double* Y, double* fT,
+                double* fY, void* cuda_stream);
 
 /*
  * Measurement aid (not a step of the method): FP64 FMA throughput probe, the

@@ -261,6 +261,7 @@ bool valid_opts(const dlbchem_options* o, std::string& why) {
   if (o->mapping < 0 || o->mapping > 2) { why = "mapping must be 0, 1 or 2"; return false; }
   if (o->team_warps != 0 && o->team_warps != 1 && o->team_warps != 2 && o->team_warps != 4) { why = "team_warps must be 0, 1, 2 or 4"; return false; }
   if (o->precision != 0 && o->precision != 1) { why = "precision must be 0 or 1"; return false; }
+  if (o->surrogate < 0 || o->surrogate > 2) { why = "surrogate must be 0, 1 or 2"; return false; }
   if (!(o->gate >= 0)) { why = "gate must be >= 0"; return false; }
   return true;
 }
@@ -319,6 +320,10 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   if (order_out) *order_out = order;
   // reactions (device index r is file reaction order[r])
   std::vector<double> lnA(nrx), beta(nrx), EaR(nrx), dH0(nrx, 0.0), dHa(nrx, 0.0), dHb(nrx, 0.0);
+  // d ln k_r / dT = d ln k_f / dT - d ln K_c / dT with K_c's standard state
+  // folded in: Ea/(R T^2) + beta/T - dH(T)/(R T^2) + dnu/T, dH(T) = dH0 +
+  // dHa T + dHb T^2, collected as B2/T^2 + B1/T + B0
+  std::vector<double> kB0(nrx, 0.0), kB1(nrx, 0.0), kB2(nrx, 0.0);
   std::vector<RxnMeta> meta(nrx);
   std::vector<int32_t> eff_sp;
   std::vector<double> eff_dm1;
@@ -329,6 +334,9 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
     lnA[r] = x.lnA; beta[r] = x.beta; EaR[r] = x.Ea / kR;
     for (int k : x.p) { dH0[r] += H0[k]; dHa[r] += cpa[k]; dHb[r] += hcpb[k]; }
     for (int k : x.r) { dH0[r] -= H0[k]; dHa[r] -= cpa[k]; dHb[r] -= hcpb[k]; }
+    kB2[r] = EaR[r] - dH0[r] / kR;
+    kB1[r] = x.beta + double(int(x.p.size()) - int(x.r.size())) - dHa[r] / kR;
+    kB0[r] = -dHb[r] / kR;
     RxnMeta& mt = meta[r];
     std::memset(&mt, 0, sizeof(mt));
     for (int i = 0; i < 6; ++i) mt.sp[i] = -1;
@@ -480,7 +488,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   offs.push_back(put(trip.data(), trip.size() * 4));
   offs.push_back(put(inc_all.data(), std::max<size_t>(inc_all.size(), 1) * 4));
   offs.push_back(put(incp_all.data(), incp_all.size() * 4));
-  for (auto* v : {&dH0, &dHa, &dHb}) offs.push_back(put(v->data(), v->size() * 8));
+  for (auto* v : {&kB0, &kB1, &kB2}) offs.push_back(put(v->data(), v->size() * 8));
   // store offsets as fake pointers; relocated after upload
   auto P = [&](int i) { return reinterpret_cast<const double*>(offs[i]); };
   dm.W = P(0); dm.iW = P(1); dm.H0 = P(2); dm.cpa = P(3); dm.hcpb = P(4); dm.cpb = P(5);
@@ -498,7 +506,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   dm.trip = reinterpret_cast<const int32_t*>(offs[23]);
   dm.inc_all = reinterpret_cast<const uint32_t*>(offs[24]);
   dm.incp_all = reinterpret_cast<const int32_t*>(offs[25]);
-  dm.dH0 = P(26); dm.dHa = P(27); dm.dHb = P(28);
+  dm.kB0 = P(26); dm.kB1 = P(27); dm.kB2 = P(28);
   return true;
 }
 
@@ -521,7 +529,7 @@ void relocate(DevMech& dm, void* base) {
   dm.trip = reloc(dm.trip, base);
   dm.inc_all = reloc(dm.inc_all, base);
   dm.incp_all = reloc(dm.incp_all, base);
-  dm.dH0 = reloc(dm.dH0, base); dm.dHa = reloc(dm.dHa, base); dm.dHb = reloc(dm.dHb, base);
+  dm.kB0 = reloc(dm.kB0, base); dm.kB1 = reloc(dm.kB1, base); dm.kB2 = reloc(dm.kB2, base);
 }
 
 int configure_launch(dlbchem_ctx* c) {
@@ -547,6 +555,8 @@ int configure_launch(dlbchem_ctx* c) {
   e = cudaFuncSetAttribute(dlb::rosenbrock_kernel_ptr(c->wpc), cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(dlb::gate_kernel_ptr(c->wpc), cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dlb::rhs_kernel_ptr(c->wpc), cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaFuncSetAttribute");
   int bps = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, dlb::rosenbrock_kernel_ptr(c->wpc), 32 * c->wpc * teams, c->smem_bytes);
@@ -895,6 +905,7 @@ int dlbchem_integrate(dlbchem_ctx* c, int64_t n, double dt, const double* T, con
     g.L = c->L;
     g.n = n; g.T = T; g.p = p; g.Y = Y; g.dT = c->l_dT; g.dY = c->l_dY; g.Tout = T_out; g.Yout = Y_out;
     g.steps = steps; g.status = status; g.flag = c->w_flag; g.gate = c->opt.gate;
+    g.residual = c->opt.surrogate == 2 ? 1 : 0;
     int64_t ggrid = std::min<int64_t>((n + c->teams - 1) / c->teams, int64_t(c->num_sms) * c->blocks_per_sm);
     e = dlb::launch_gate(c->wpc, unsigned(ggrid), 32 * c->wpc * c->teams, c->smem_bytes, s, g);
     if (e == cudaSuccess) e = dlb::launch_count_scan(n, c->w_flag, c->w_bcount, c->w_boff, c->w_total, s);
@@ -1065,6 +1076,23 @@ int dlbchem_check_math(dlbchem_ctx* c, int64_t n, const double* x, double* out, 
   if (n == 0) return DLBCHEM_OK;
   cudaError_t e = dlb::launch_check_math(n, x, c->dm.exptab, out, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? DLBCHEM_OK : cuda_fail(c, e, "check_math launch");
+}
+
+int dlbchem_rhs(dlbchem_ctx* c, int64_t n, const double* T, const double* p, const double* Y, double* fT,
+                double* fY, void* stream) {
+  if (!c) return DLBCHEM_BAD_ARG;
+  c->err.clear();
+  if (n < 0) return fail(c, DLBCHEM_BAD_ARG, "ncells must be >= 0");
+  if (n == 0) return DLBCHEM_OK;
+  if (!T || !p || !Y || !fT || !fY) return fail(c, DLBCHEM_BAD_ARG, "NULL array pointer");
+  dlb::RhsArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.m = c->dm; a.L = c->L; a.n = n; a.T = T; a.p = p; a.Y = Y; a.fT = fT; a.fY = fY;
+  a.isothermal = c->opt.isothermal;
+  const int64_t grid = std::min<int64_t>((n + c->teams - 1) / c->teams, int64_t(c->num_sms) * c->blocks_per_sm);
+  cudaError_t e = dlb::launch_rhs(c->wpc, unsigned(grid), 32 * c->wpc * c->teams, c->smem_bytes,
+                                  static_cast<cudaStream_t>(stream), a);
+  return e == cudaSuccess ? DLBCHEM_OK : cuda_fail(c, e, "rhs launch");
 }
 
 int dlbchem_fp64_fma_probe(int64_t iters, double* out, int64_t nout, int64_t* flops, void* stream) {

@@ -60,8 +60,9 @@ struct DevMech {
   const double *W, *iW, *H0, *cpa, *hcpb, *cpb, *G0, *G1, *G2, *G3, *bW;
   // reactions
   const double *lnA, *beta, *EaR;
-  // reaction enthalpy change dH(T) = dH0 + T (dHa + dHb T), sums over products minus reactants
-  const double *dH0, *dHa, *dHb;
+  // d ln k_r / dT = kB2 / T^2 + kB1 / T + kB0 (reverse rate constant's
+  // temperature derivative, from Ea, beta and the reaction's dH(T) and dnu)
+  const double *kB0, *kB1, *kB2;
   const RxnMeta* meta;
   const int32_t* eff_sp;
   const double* eff_dm1;
@@ -210,6 +211,17 @@ struct GateArgs {
   int32_t *steps, *status;
   uint8_t* flag;                    // 0: to integrate; 1: mapped (skipped); set to 2 when accepted
   double gate;
+  int residual;                     // 1: the proposal is y + dt f(y) + (dT, dY) instead of y + (dT, dY)
+};
+
+// Arguments of the right-hand-side kernel: f(y) of every cell.
+struct RhsArgs {
+  DevMech m;
+  WsLayout L;
+  int64_t n;
+  const double *T, *p, *Y;          // inputs (Y species-major)
+  double *fT, *fY;                  // outputs: dT/dt [n], dY/dt [nsp][n]
+  int isothermal;
 };
 
 // Host-side launchers defined next to the kernels (integrator*.cu).
@@ -217,6 +229,14 @@ cudaError_t launch_gate_w1(unsigned grid, int threads, int smem, cudaStream_t s,
 cudaError_t launch_gate_w2(unsigned grid, int threads, int smem, cudaStream_t s, const GateArgs& a);
 cudaError_t launch_gate_w4(unsigned grid, int threads, int smem, cudaStream_t s, const GateArgs& a);
 cudaError_t launch_gate(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const GateArgs& a);
+cudaError_t launch_rhs_w1(unsigned grid, int threads, int smem, cudaStream_t s, const RhsArgs& a);
+cudaError_t launch_rhs_w2(unsigned grid, int threads, int smem, cudaStream_t s, const RhsArgs& a);
+cudaError_t launch_rhs_w4(unsigned grid, int threads, int smem, cudaStream_t s, const RhsArgs& a);
+cudaError_t launch_rhs(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const RhsArgs& a);
+const void* rhs_kernel_ptr_w1();
+const void* rhs_kernel_ptr_w2();
+const void* rhs_kernel_ptr_w4();
+const void* rhs_kernel_ptr(int wpc);
 const void* gate_kernel_ptr_w1();
 const void* gate_kernel_ptr_w2();
 const void* gate_kernel_ptr_w4();

@@ -58,6 +58,16 @@ cudaError_t launch_gate(int wpc, unsigned grid, int threads, int smem, cudaStrea
   return launch_gate_w4(grid, threads, smem, s, a);
 }
 
+cudaError_t launch_rhs(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const RhsArgs& a) {
+  if (wpc == 1) return launch_rhs_w1(grid, threads, smem, s, a);
+  if (wpc == 2) return launch_rhs_w2(grid, threads, smem, s, a);
+  return launch_rhs_w4(grid, threads, smem, s, a);
+}
+
+const void* rhs_kernel_ptr(int wpc) {
+  return wpc == 1 ? rhs_kernel_ptr_w1() : (wpc == 2 ? rhs_kernel_ptr_w2() : rhs_kernel_ptr_w4());
+}
+
 const void* gate_kernel_ptr(int wpc) {
   return wpc == 1 ? gate_kernel_ptr_w1() : (wpc == 2 ? gate_kernel_ptr_w2() : gate_kernel_ptr_w4());
 }

@@ -151,7 +151,7 @@ __device__ __forceinline__ WS carve(double* base, const WsLayout& L) {
 
 // Mixture scalars shared by one rate evaluation.
 struct Mix {
-  double T, iT, lnT, S, rho, irho, Ctot, irS;   // irS = 1/(rho S) = T / P1
+  double T, iT, iT2, lnT, S, rho, irho, Ctot, irS;   // iT2 = 1/T^2, irS = 1/(rho S) = T / P1
 };
 
 // exp(x) by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989):
@@ -262,14 +262,11 @@ __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mi
   if (mt.flags & RX_EFF) D[mt.dslot_eff] = pf - pr;
   // small integers as doubles from the shared table (nutab[j] = j - 8), not by conversion
   const double sig = Mf * (w.nutab[8 + mt.nr + tb] * pf - w.nutab[8 + mt.np + tb] * pr);
-  const double dlnkf = fma(m.EaR[r], mx.iT * mx.iT, m.beta[r] * mx.iT);
+  // d q / d T at fixed c: pf d ln k_f / dT - pr d ln k_r / dT, with
+  // d ln k_r / dT = d ln k_f / dT - d ln K_c / dT = kB2 / T^2 + kB1 / T + kB0
+  const double dlnkf = fma(m.EaR[r], mx.iT2, m.beta[r] * mx.iT);
   double dq = pf * dlnkf;
-  if (mt.flags & RX_REV) {
-    const double T = mx.T;
-    const double dH = fma(T, fma(m.dHb[r], T, m.dHa[r]), m.dH0[r]);   // sum nu h_k(T), products - reactants
-    const double dlnKc = dH * mx.iT * mx.iT * (1.0 / kR) - w.nutab[8 + mt.dnu] * mx.iT;
-    dq -= pr * (dlnkf - dlnKc);
-  }
+  if (mt.flags & RX_REV) dq = fma(-pr, fma(m.kB2[r], mx.iT2, fma(m.kB1[r], mx.iT, m.kB0[r])), dq);
   // the assembly needs v only inside dwdot/dT - v/T and u - v/(rho S), so the
   // gathers carry those two combinations (sigma = sum_j c_j dq/dc_j)
   w.dqdT[rl] = fma(-sig, mx.iT, Mf * dq);
@@ -286,19 +283,19 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
   for (int k = tm.tid; k < nsp; k += TS) s = fma(yv[1 + k], m.iW[k], s);
   double iT, lnT;
   if (WPC == 1) {
-    iT = 1.0 / T;
+    iT = rcp_nr(T);
     lnT = log(T);
   } else {
     // one warp takes ln T, another 1/T; both are published with the barrier
     // of the sum below (slots 28, 29 of the team scratch)
     if (tm.warp == 0) { if (tm.lane == 0) w.scal[28] = log(T); }
-    else if (tm.warp == 1) { if (tm.lane == 0) w.scal[29] = 1.0 / T; }
+    else if (tm.warp == 1) { if (tm.lane == 0) w.scal[29] = rcp_nr(T); }
   }
   const double S = tm.sum(s);
   if (WPC > 1) { lnT = w.scal[28]; iT = w.scal[29]; }
   const double irho = (T * S) * iP1;          // 1/rho = R T S / p
   const double rho = rcp_nr(irho);
-  mx.T = T; mx.iT = iT; mx.lnT = lnT; mx.S = S; mx.rho = rho; mx.irho = irho;
+  mx.T = T; mx.iT = iT; mx.iT2 = iT * iT; mx.lnT = lnT; mx.S = S; mx.rho = rho; mx.irho = irho;
   mx.Ctot = P1 * iT;                          // sum_k c_k (unit efficiencies)
   mx.irS = T * iP1;
   for (int k = tm.tid; k < nsp; k += TS) {
@@ -376,7 +373,7 @@ __device__ __forceinline__ void finish_f(const DevMech& m, const Team<WPC>& tm, 
   tm.sum2(q, cp);
   Q = q;
   cpm = cp;
-  if (tm.tid == 0) f[0] = iso ? 0.0 : -Q * mx.irho / cpm;
+  if (tm.tid == 0) f[0] = iso ? 0.0 : -(Q * mx.irho) * rcp_nr(cpm);
   tm.sync();
 }
 
@@ -542,19 +539,41 @@ __device__ __forceinline__ bool lu_factor(const Team<WPC>& tm, R* M, int N, int 
     }
     tm.sync();
     // flattened trailing update over the wd x wd block: element e = ii*wd + jj,
-    // thread t takes e = t, t + TS, ...; (ii, jj) advance by (TS / wd, TS % wd)
+    // thread t takes e = t, t + TS, ...; (ii, jj) advance by (TS / wd, TS % wd).
+    // Four elements at a time with every load issued before the FMAs and the
+    // stores: the elements are distinct and column k and row k are not
+    // written here, so nothing aliases, and four independent FMA chains are in
+    // flight instead of one (each element's arithmetic is unchanged).
     const int wd = N - 1 - k;
     const int tot = wd * wd;
     if (tm.tid < tot) {
       const int dq = TS / wd, dr = TS - dq * wd;
       int ii = tm.tid / wd, jj = tm.tid - ii * wd;
       const R* urow = M + k * ld + k + 1;
-      for (int e = tm.tid; e < tot; e += TS) {
-        R* mrow = M + (k + 1 + ii) * ld;
-        mrow[k + 1 + jj] = fma(-mrow[k], urow[jj], mrow[k + 1 + jj]);
+      R* rows = M + (k + 1) * ld;
+      auto step = [&]() {
         jj += dr;
         ii += dq;
         if (jj >= wd) { jj -= wd; ++ii; }
+      };
+      int e = tm.tid;
+      for (; e + 3 * TS < tot; e += 4 * TS) {
+        R* r0 = rows + ii * ld; const int c0 = jj; step();
+        R* r1 = rows + ii * ld; const int c1 = jj; step();
+        R* r2 = rows + ii * ld; const int c2 = jj; step();
+        R* r3 = rows + ii * ld; const int c3 = jj; step();
+        const R l0 = r0[k], l1 = r1[k], l2 = r2[k], l3 = r3[k];
+        const R u0 = urow[c0], u1 = urow[c1], u2 = urow[c2], u3 = urow[c3];
+        const R m0 = r0[k + 1 + c0], m1 = r1[k + 1 + c1], m2 = r2[k + 1 + c2], m3 = r3[k + 1 + c3];
+        r0[k + 1 + c0] = fma(-l0, u0, m0);
+        r1[k + 1 + c1] = fma(-l1, u1, m1);
+        r2[k + 1 + c2] = fma(-l2, u2, m2);
+        r3[k + 1 + c3] = fma(-l3, u3, m3);
+      }
+      for (; e < tot; e += TS) {
+        R* mrow = rows + ii * ld;
+        mrow[k + 1 + jj] = fma(-mrow[k], urow[jj], mrow[k + 1 + jj]);
+        step();
       }
     }
     tm.sync();
@@ -894,12 +913,13 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
     double* u2 = w.u + N;
     double* u3 = w.u + 2 * N;
     double* u4 = w.u + 3 * N;
+    const double iN = 1.0 / N;
     while (t < dt) {
       if (steps >= P.max_steps) { status = CELL_MAX_STEPS; break; }
       if ((dt - t) - h <= 1e-12 * dt) h = dt - t;
       if (h < P.hmin_frac * dt) { status = CELL_H_UNDERFLOW; break; }
       ++steps;
-      const double ih = 1.0 / h;
+      const double ih = rcp_nr(h);
       assemble<WPC>(m, tm, w, P1, iP1, iso, ih * (1.0 / kGamma));
       bool mixed = P.precision == 1 && w.g != nullptr;   // no scratch: FP64
       bool ok;
@@ -973,11 +993,11 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
         const double yn = fma(kM1, u1[i], fma(kM2, u2[i], fma(kM3, u3[i], fma(kM4, u4[i], w.y0[i]))));
         const double er = fma(kE1, u1[i], fma(kE2, u2[i], fma(kE3, u3[i], kE4 * u4[i])));
         const double sc = fma(P.rtol, fmax(fabs(w.y0[i]), fabs(yn)), P.atol);
-        const double r = er / sc;
+        const double r = er * rcp_nr(sc);
         acc = fma(r, r, acc);
         w.ys[i] = yn;
       }
-      double errn = sqrt(tm.sum(acc) / N);
+      double errn = sqrt(tm.sum(acc) * iN);
       if (!ok) errn = nan("");
       if (errn <= 1.0) {
         // errn^(-1/4) as rsqrt(sqrt(errn)): within 2 ulp of pow, at a fraction of its FP64 work
@@ -1071,9 +1091,9 @@ __global__ void __launch_bounds__(128, WPC == 1 ? 4 : (WPC == 2 ? 3 : 2)) rosenb
 }
 
 // ---------------------------------------------------------------------------
-// Surrogate gate: a predicted increment (T', Y') = (T, Y) + (dT, dY) is
-// accepted only if it is consistent with the chemistry over the step to the
-// gate tolerance g: the trapezoid defect y' - y - dt/2 (f(y) + f(y')) is at
+// Surrogate gate: a predicted state (T', Y') = (T, Y) + (dT, dY), or with
+// residual = 1 (T, Y) + dt f(T, Y) + (dT, dY), is accepted only if it is
+// consistent with the chemistry over the step to the gate tolerance g: the trapezoid defect y' - y - dt/2 (f(y) + f(y')) is at
 // most g in every mass fraction and g*T in temperature, |sum Y' - 1| <= g, and
 // every element total changes by at most g relative. Accepted cells get
 // (T', Y'), status SURROGATE and steps 0; the others stay on the work list and
@@ -1113,50 +1133,117 @@ __global__ void __launch_bounds__(128) gate_kernel(const GateArgs a) {
     }
     tm.sync();
     int bad = 0;
-    for (int i = tm.tid; i < N; i += TS) bad |= !isfinite(w.y0[i]) || !isfinite(w.ys[i]);
-    bad |= !(w.y0[0] > 0.0) || !(w.ys[0] > 0.0) || !(p > 0.0);
+    for (int i = tm.tid; i < N; i += TS) bad |= !isfinite(w.y0[i]);
+    bad |= !(w.y0[0] > 0.0) || !(p > 0.0);
     if (tm.any(bad)) continue;
     const double P1 = 1e-6 * p / kR;
     const double iP1 = 1.0 / P1;
     eval_f<WPC>(m, tm, w, w.y0, P1, iP1, a.P.isothermal != 0, w.f0);
-    eval_f<WPC>(m, tm, w, w.ys, P1, iP1, a.P.isothermal != 0, w.fs);
-    const double hdt = 0.5 * a.P.dt;
-    double dY = 0.0, sumY = 0.0, e0 = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0, t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-    for (int i = tm.tid; i < N; i += TS) {
-      const double def = fabs(w.ys[i] - w.y0[i] - hdt * (w.f0[i] + w.fs[i]));
-      if (i > 0) {
-        dY = fmax(dY, def);
-        const int k = i - 1;
-        const double yk = w.ys[i], dk = w.ys[i] - w.y0[i];
-        sumY += yk;
-        e0 = fma(m.aW[k], dk, e0);           t0 = fma(m.aW[k], w.y0[i], t0);
-        e1 = fma(m.aW[nsp + k], dk, e1);     t1 = fma(m.aW[nsp + k], w.y0[i], t1);
-        e2 = fma(m.aW[2 * nsp + k], dk, e2); t2 = fma(m.aW[2 * nsp + k], w.y0[i], t2);
-        e3 = fma(m.aW[3 * nsp + k], dk, e3); t3 = fma(m.aW[3 * nsp + k], w.y0[i], t3);
-      } else {
-        dY = fmax(dY, def / w.y0[0]);        // temperature: relative defect
+    // candidates: the network's proposal; with residual, first the explicit
+    // Euler step plus the network's correction, then the Euler step alone
+    const int ncand = a.residual ? 2 : 1;
+    for (int cand = 0; cand < ncand; ++cand) {
+      if (a.residual) {
+        for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(a.P.dt, w.f0[i], cand == 0 ? w.ys[i] : w.y0[i]);
+        tm.sync();
       }
-    }
-    const double worst = tm.maxv(dY);
-    const double S = tm.sum(sumY);
-    const double E0 = tm.sum(e0), E1 = tm.sum(e1), E2 = tm.sum(e2), E3 = tm.sum(e3);
-    const double R0 = tm.sum(t0), R1 = tm.sum(t1), R2 = tm.sum(t2), R3 = tm.sum(t3);
-    double ed = 0.0;
-    if (R0 > 0) ed = fmax(ed, fabs(E0) / R0);
-    if (R1 > 0) ed = fmax(ed, fabs(E1) / R1);
-    if (R2 > 0) ed = fmax(ed, fabs(E2) / R2);
-    if (R3 > 0) ed = fmax(ed, fabs(E3) / R3);
-    const bool accept = worst <= a.gate && fabs(S - 1.0) <= a.gate && ed <= a.gate;
-    if (accept) {
+      bad = 0;
+      for (int i = tm.tid; i < N; i += TS) bad |= !isfinite(w.ys[i]);
+      bad |= !(w.ys[0] > 0.0);
+      if (tm.any(bad)) continue;
+      eval_f<WPC>(m, tm, w, w.ys, P1, iP1, a.P.isothermal != 0, w.fs);
+      const double hdt = 0.5 * a.P.dt;
+      double dY = 0.0, sumY = 0.0, e0 = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0, t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
       for (int i = tm.tid; i < N; i += TS) {
-        if (i == 0) a.Tout[cell] = w.ys[0];
-        else a.Yout[int64_t(i - 1) * n + cell] = w.ys[i];
+        const double def = fabs(w.ys[i] - w.y0[i] - hdt * (w.f0[i] + w.fs[i]));
+        if (i > 0) {
+          dY = fmax(dY, def);
+          const int k = i - 1;
+          const double yk = w.ys[i], dk = w.ys[i] - w.y0[i];
+          sumY += yk;
+          e0 = fma(m.aW[k], dk, e0);           t0 = fma(m.aW[k], w.y0[i], t0);
+          e1 = fma(m.aW[nsp + k], dk, e1);     t1 = fma(m.aW[nsp + k], w.y0[i], t1);
+          e2 = fma(m.aW[2 * nsp + k], dk, e2); t2 = fma(m.aW[2 * nsp + k], w.y0[i], t2);
+          e3 = fma(m.aW[3 * nsp + k], dk, e3); t3 = fma(m.aW[3 * nsp + k], w.y0[i], t3);
+        } else {
+          dY = fmax(dY, def / w.y0[0]);        // temperature: relative defect
+        }
       }
-      if (tm.tid == 0) {
-        a.flag[cell] = 2;
-        if (a.steps) a.steps[cell] = 0;
-        if (a.status) a.status[cell] = CELL_SURROGATE;
+      const double worst = tm.maxv(dY);
+      const double S = tm.sum(sumY);
+      const double E0 = tm.sum(e0), E1 = tm.sum(e1), E2 = tm.sum(e2), E3 = tm.sum(e3);
+      const double R0 = tm.sum(t0), R1 = tm.sum(t1), R2 = tm.sum(t2), R3 = tm.sum(t3);
+      double ed = 0.0;
+      if (R0 > 0) ed = fmax(ed, fabs(E0) / R0);
+      if (R1 > 0) ed = fmax(ed, fabs(E1) / R1);
+      if (R2 > 0) ed = fmax(ed, fabs(E2) / R2);
+      if (R3 > 0) ed = fmax(ed, fabs(E3) / R3);
+      const bool accept = worst <= a.gate && fabs(S - 1.0) <= a.gate && ed <= a.gate;
+      if (accept) {
+        for (int i = tm.tid; i < N; i += TS) {
+          if (i == 0) a.Tout[cell] = w.ys[0];
+          else a.Yout[int64_t(i - 1) * n + cell] = w.ys[i];
+        }
+        if (tm.tid == 0) {
+          a.flag[cell] = 2;
+          if (a.steps) a.steps[cell] = 0;
+          if (a.status) a.status[cell] = CELL_SURROGATE;
+        }
+        break;
       }
+      tm.sync();
+    }
+    tm.sync();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Right-hand side of the per-cell ODE (Sec. 1: dPhi/dt = f(Phi); here
+// f = (dT/dt, dY_k/dt) at constant p) for every cell, one team per cell.
+// Cells with a non-finite state, T <= 0 or p <= 0 get NaN.
+// ---------------------------------------------------------------------------
+template <int WPC>
+__global__ void __launch_bounds__(128) rhs_kernel(const RhsArgs a) {
+  extern __shared__ __align__(16) double smem[];
+  constexpr int TS = 32 * WPC;
+  const int teams = blockDim.x / TS;
+  const int team = threadIdx.x / TS;
+  Team<WPC> tm;
+  tm.tid = threadIdx.x % TS;
+  tm.warp = tm.tid >> 5;
+  tm.lane = threadIdx.x & 31;
+  tm.bar_id = 1 + team;
+  tm.parity = 0;
+  double* tab = smem + size_t(teams) * a.L.total;
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) tab[j] = a.m.exptab[j];
+  for (int j = threadIdx.x; j < 16; j += blockDim.x) tab[64 + j] = double(j - 8);
+  __syncthreads();
+  WS w = carve(smem + size_t(team) * a.L.total, a.L);
+  w.exptab = tab;
+  w.nutab = tab + 64;
+  tm.red = w.scal;
+  const int N = a.m.N;
+  const int64_t n = a.n;
+  for (int64_t cell = int64_t(blockIdx.x) * teams + team; cell < n; cell += int64_t(gridDim.x) * teams) {
+    const double p = a.p[cell];
+    for (int i = tm.tid; i < N; i += TS) w.y0[i] = i == 0 ? a.T[cell] : a.Y[int64_t(i - 1) * n + cell];
+    tm.sync();
+    int bad = 0;
+    for (int i = tm.tid; i < N; i += TS) bad |= !isfinite(w.y0[i]);
+    bad |= !(w.y0[0] > 0.0) || !(p > 0.0) || !isfinite(p);
+    if (tm.any(bad)) {
+      for (int i = tm.tid; i < N; i += TS) {
+        if (i == 0) a.fT[cell] = nan("");
+        else a.fY[int64_t(i - 1) * n + cell] = nan("");
+      }
+      tm.sync();
+      continue;
+    }
+    const double P1 = 1e-6 * p / kR;
+    eval_f<WPC>(a.m, tm, w, w.y0, P1, 1.0 / P1, a.isothermal != 0, w.f0);
+    for (int i = tm.tid; i < N; i += TS) {
+      if (i == 0) a.fT[cell] = w.f0[0];
+      else a.fY[int64_t(i - 1) * n + cell] = w.f0[i];
     }
     tm.sync();
   }

@@ -17,4 +17,11 @@ cudaError_t launch_gate_w1(unsigned grid, int threads, int smem, cudaStream_t s,
   return cudaGetLastError();
 }
 
+cudaError_t launch_rhs_w1(unsigned grid, int threads, int smem, cudaStream_t s, const RhsArgs& a) {
+  rhs_kernel<1><<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+const void* rhs_kernel_ptr_w1() { return reinterpret_cast<const void*>(&rhs_kernel<1>); }
+
 }  // namespace dlb

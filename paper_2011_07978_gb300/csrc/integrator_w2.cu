@@ -17,4 +17,11 @@ cudaError_t launch_gate_w2(unsigned grid, int threads, int smem, cudaStream_t s,
   return cudaGetLastError();
 }
 
+cudaError_t launch_rhs_w2(unsigned grid, int threads, int smem, cudaStream_t s, const RhsArgs& a) {
+  rhs_kernel<2><<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+const void* rhs_kernel_ptr_w2() { return reinterpret_cast<const void*>(&rhs_kernel<2>); }
+
 }  // namespace dlb

@@ -55,6 +55,7 @@ def load() -> ctypes.CDLL:
     lib.dlbchem_last_worklist.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int64)]
     lib.dlbchem_last_mapping.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int64)]
     lib.dlbchem_check_math.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp]
+    lib.dlbchem_rhs.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
     lib.dlbchem_fp64_fma_probe.argtypes = [ctypes.c_int64, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _vp]
     lib.dlbchem_last_error.argtypes = [_vp]
     lib.dlbchem_last_error.restype = ctypes.c_char_p
@@ -235,6 +236,19 @@ class Context:
         m = ctypes.c_int64()
         self._check(load().dlbchem_last_worklist(self._h, _ptr(out), ctypes.byref(m)))
         return m.value
+
+    def rhs(self, T, p, Y, fT=None, fY=None, stream=None):
+        """dlbchem_rhs: f = (dT/dt, dY/dt) of every cell (CUDA float64 tensors)."""
+        import torch
+        if fT is None:
+            fT = torch.empty_like(T)
+        if fY is None:
+            fY = torch.empty_like(Y)
+        if stream is None:
+            stream = torch.cuda.current_stream(T.device)
+        self._check(load().dlbchem_rhs(self._h, T.numel(), _ptr(T), _ptr(p), _ptr(Y), _ptr(fT), _ptr(fY),
+                                       ctypes.c_void_p(stream.cuda_stream)))
+        return fT, fY
 
     def last_mapping(self, out):
         """dlbchem_last_mapping into the int32 CUDA tensor `out`: the reference of

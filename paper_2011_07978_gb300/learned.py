@@ -4,7 +4,9 @@ Host orchestration only: the training targets come from the library's FP64
 integrator, and every forward, backward and optimiser step runs in the
 library's BF16 tensor-core kernels (dlbchem_mlp_*). The feature definition
 matches the inference kernel: x = [T/1000, ln p, Y_1..Y_nsp, ln dt],
-y = [ln attempted steps, dT, dY_1..dY_nsp].
+y = [ln attempted steps, dT, dY_1..dY_nsp]. A residual network instead
+learns the increment minus the explicit Euler step dt f(y) (f from
+dlbchem_rhs); the gate then tries y + dt f(y) + its output (surrogate = 2).
 """
 from __future__ import annotations
 
@@ -35,27 +37,39 @@ def targets(T, Y, To, Yo, steps):
     return y
 
 
-def generate(ctx, T, p, Y, dt_cells, device="cuda"):
+def generate(ctx, T, p, Y, dt_cells, device="cuda", residual=False):
     """Integrate every cell over its own dt with the FP64 integrator (cells
-    grouped by dt value) and return (features, targets, steps, status)."""
+    grouped by dt value) and return (features, targets, steps, status). With
+    residual, the increment targets are the increments minus dt f(y)."""
     import torch
     n = T.size
     To = np.empty(n)
     Yo = np.empty_like(Y)
     steps = np.zeros(n, dtype=np.int32)
     status = np.zeros(n, dtype=np.int32)
+    euler_T = np.zeros(n)
+    euler_Y = np.zeros_like(Y)
     for dt in np.unique(dt_cells):
         idx = np.flatnonzero(dt_cells == dt)
         d = lambda a: torch.tensor(np.ascontiguousarray(a), device=device)
         st = torch.zeros(idx.size, dtype=torch.int32, device=device)
         ss = torch.zeros(idx.size, dtype=torch.int32, device=device)
-        a, b = ctx.integrate(d(T[idx]), d(p[idx]), d(Y[:, idx]), float(dt), steps=st, status=ss)
+        Td, pd, Yd = d(T[idx]), d(p[idx]), d(Y[:, idx])
+        a, b = ctx.integrate(Td, pd, Yd, float(dt), steps=st, status=ss)
+        if residual:
+            fT, fY = ctx.rhs(Td, pd, Yd)
+            euler_T[idx] = float(dt) * fT.cpu().numpy()
+            euler_Y[:, idx] = float(dt) * fY.cpu().numpy()
         torch.cuda.synchronize()
         To[idx] = a.cpu().numpy()
         Yo[:, idx] = b.cpu().numpy()
         steps[idx] = st.cpu().numpy()
         status[idx] = ss.cpu().numpy()
-    return features(T, p, Y, dt_cells), targets(T, Y, To, Yo, steps), steps, status
+    y = targets(T, Y, To, Yo, steps)
+    if residual:
+        y[:, 1] -= euler_T
+        y[:, 2:] -= euler_Y.T
+    return features(T, p, Y, dt_cells), y, steps, status
 
 
 def dt_buckets(n, seed, nbuckets=64, lo=1e-6, hi=1e-5):
@@ -115,19 +129,24 @@ def train(X, Y, epochs=10, batch=4096, lr=1e-3, seed=0, device="cuda", log=None)
     return net
 
 
-def evaluate(mech, net, T, p, Y, dt_cells, rtol=1e-6, atol=1e-10, device="cuda"):
-    """Cells/s of the queue without the network (index order: a fresh field
-    has no previous steps), with the predictor, and with predictor +
-    surrogate, on the same cells (grouped by dt); plus the surrogate's
-    acceptance and its error against the integrated result."""
+def evaluate(mech, nets, T, p, Y, dt_cells, rtol=1e-6, atol=1e-10, device="cuda"):
+    """Cells/s of the queue without a network (index order: a fresh field has
+    no previous steps), with the predictor, and with predictor + surrogate,
+    on the same cells (grouped by dt); plus the surrogate's acceptance and
+    its error against the integrated result. nets: {"increment": net,
+    "residual": net} (either may be missing)."""
     import torch
     out = {}
     ref = {}
-    modes = [("queue", dict()), ("queue+predictor", dict(predictor=1)),
-             ("queue+predictor+surrogate", dict(predictor=1, surrogate=1))]
-    for name, kw in modes:
+    modes = [("queue", None, dict())]
+    if "increment" in nets:
+        modes += [("queue+predictor", nets["increment"], dict(predictor=1)),
+                  ("queue+predictor+surrogate", nets["increment"], dict(predictor=1, surrogate=1))]
+    if "residual" in nets:
+        modes += [("queue+predictor+residual surrogate", nets["residual"], dict(predictor=1, surrogate=2))]
+    for name, net, kw in modes:
         ctx = dlbchem.Context(mech, rtol=rtol, atol=atol, schedule=dlbchem.SCHED_QUEUE, **kw)
-        if kw:
+        if net is not None:
             ctx.attach_mlp(net)
         total_ms, accepted, worst_dy, worst_dt, identical = 0.0, 0, 0.0, 0.0, True
         for dt in np.unique(dt_cells):
@@ -182,26 +201,30 @@ def main(argv=None):
     ctx = dlbchem.Context(mech, rtol=1e-6, atol=1e-10, schedule=dlbchem.SCHED_QUEUE)
     T, p, Y = states.uniform_states(10, args.train_cells, 100)
     dts = dt_buckets(args.train_cells, 100)
-    t0 = time.perf_counter()
-    X, Yt, steps, status = generate(ctx, T, p, Y, dts)
-    t_gen = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    net = train(X, Yt, epochs=args.epochs, batch=args.batch, lr=args.lr, seed=1)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
+    nets, train_info = {}, {}
+    for kind in ("increment", "residual"):
+        t0 = time.perf_counter()
+        X, Yt, steps, status = generate(ctx, T, p, Y, dts, residual=(kind == "residual"))
+        t_gen = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        net = train(X, Yt, epochs=args.epochs, batch=args.batch, lr=args.lr, seed=1)
+        torch.cuda.synchronize()
+        nets[kind] = net
+        train_info[kind] = {"generate_s": t_gen, "train_s": time.perf_counter() - t0, "epochs": args.epochs,
+                            "loss_first_epoch": net.history[0], "loss_last_epoch": net.history[-1],
+                            "failed_cells": int((status != 0).sum())}
     Te, pe, Ye = states.uniform_states(10, args.eval_cells, 1)
     dte = dt_buckets(args.eval_cells, 1, nbuckets=8)
-    ev = evaluate(mech, net, Te, pe, Ye, dte)
+    ev = evaluate(mech, nets, Te, pe, Ye, dte)
+    base = ev["queue"]["cells_per_s"]
     line = {"config": "learned predictor + surrogate: 10 species / 20 reactions, trained on "
                       f"{args.train_cells} integrator trajectories (T U[300,2500] K, Dirichlet Y, dt log-U "
                       "[1e-6, 1e-5] s), evaluated on a fresh field of "
                       f"{args.eval_cells} cells, gate 1e-4, FP64 fallback",
-            "train": {"generate_s": t_gen, "train_s": t_train, "epochs": args.epochs,
-                      "loss_first_epoch": net.history[0], "loss_last_epoch": net.history[-1],
-                      "failed_cells": int((status != 0).sum())},
-            "eval": ev,
-            "predictor_gain": ev["queue+predictor"]["cells_per_s"] / ev["queue"]["cells_per_s"],
-            "surrogate_gain": ev["queue+predictor+surrogate"]["cells_per_s"] / ev["queue"]["cells_per_s"]}
+            "train": train_info, "eval": ev,
+            "predictor_gain": ev["queue+predictor"]["cells_per_s"] / base,
+            "surrogate_gain": ev["queue+predictor+surrogate"]["cells_per_s"] / base,
+            "residual_surrogate_gain": ev["queue+predictor+residual surrogate"]["cells_per_s"] / base}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -405,3 +405,21 @@ def test_status_codes(orc_c1):
     To, Yo, steps, st = orc_c1.integrate(T, p, Y, 1e-6, max_steps=3)
     assert st[1] == oracle.ST_NONFINITE and st[2] == oracle.ST_NONFINITE
     assert st[0] == oracle.ST_MAX_STEPS and steps[0] == 3
+
+
+def test_trapezoid_gate_rejects_even_exact_increments_of_stiff_cells(orc_c1):
+    """The surrogate gate accepts a proposed (T', Y') only when its trapezoid
+    defect y' - y - dt/2 (f(y) + f(y')) is within the gate. Applied to the
+    oracle's own (tight-tolerance) solution of the 10-species cells over
+    dt = 1e-6 s, the defect is far above 1e-4 on every cell: their fast
+    reactions relax within the step (dt |f(y)| ~ 1e0..1e6 at any T), so no
+    proposal, however exact, passes. Near-equilibrium cells do pass (the
+    bimodal field's burnt cells: the GPU test of the gate's accept branch)."""
+    T, p, Y = states.uniform_states(10, 64, 7)
+    dt = 1e-6
+    To, Yo, steps, st = orc_c1.integrate(T, p, Y, dt, rtol=1e-10, atol=1e-16)
+    for i in range(T.size):
+        y0 = np.concatenate([[T[i]], Y[:, i]])
+        y1 = np.concatenate([[To[i]], Yo[:, i]])
+        d = y1 - y0 - 0.5 * dt * (orc_c1.rhs(p[i], y0) + orc_c1.rhs(p[i], y1))
+        assert max(abs(d[0]) / T[i], np.abs(d[1:]).max()) > 1e-2

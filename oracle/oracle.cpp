@@ -49,6 +49,10 @@ struct Reaction {
   bool reversible = true, thirdbody = false;
   std::vector<std::pair<int, int>> reac, prod;  // (species, coefficient)
   std::vector<double> eff;              // nsp efficiencies when thirdbody
+  // pressure-dependent (fall-off) form: 0 none, 1 Lindemann, 2 Troe (a, T3,
+  // T1), 3 Troe (a, T3, T1, T2); low-pressure limit lnA0, beta0, Ea0
+  int falloff = 0;
+  double lnA0 = 0, beta0 = 0, Ea0 = 0, troe_a = 0, T3 = 1, T1 = 1, T2 = 0;
 };
 
 struct Mech {
@@ -104,6 +108,21 @@ bool load_mech(const char* path, Mech& m, std::string& err) {
     if (jk[0] < 0 || jk[0] >= m.nrx || jk[1] < 0 || jk[1] >= m.nsp || !m.rx[jk[0]].thirdbody) { err = "bad efficiency"; return false; }
     m.rx[jk[0]].eff[jk[1]] = e;
   }
+  // optional fall-off section
+  if (off + 12 <= buf.size() && std::memcmp(buf.data() + off, "FALLOFF1", 8) == 0) {
+    off += 8;
+    int32_t nf = 0;
+    get(buf, off, &nf, 1);
+    for (int i = 0; i < nf; ++i) {
+      int32_t jk[2];
+      double d[7];
+      if (!get(buf, off, jk, 2) || !get(buf, off, d, 7)) { err = "truncated fall-off section"; return false; }
+      if (jk[0] < 0 || jk[0] >= m.nrx || jk[1] < 1 || jk[1] > 3 || !m.rx[jk[0]].thirdbody) { err = "bad fall-off record"; return false; }
+      Reaction& r = m.rx[jk[0]];
+      r.falloff = jk[1];
+      r.lnA0 = d[0]; r.beta0 = d[1]; r.Ea0 = d[2]; r.troe_a = d[3]; r.T3 = d[4]; r.T1 = d[5]; r.T2 = d[6];
+    }
+  }
   return true;
 }
 
@@ -138,7 +157,56 @@ Mix mixture(const Mech& m, double p, const double* y) {
 // ---- reaction rates --------------------------------------------------------
 struct Rates {
   std::vector<double> kf, kr, fwd, rev, Mfac, q;  // fwd = kf*prod c^nu', rev = kr*prod c^nu''
+  std::vector<double> dlnkf_dT;   // d ln k_f / dT at fixed concentrations
+  std::vector<double> dlnkf_dlnM; // d ln k_f / d ln [M] (fall-off reactions; 0 otherwise)
 };
+
+// Pressure-dependent rate constant of a fall-off reaction (Lindemann; Troe's
+// broadening factor as in Gilbert, Luther and Troe, Ber. Bunsenges. Phys.
+// Chem. 87, 1983): k = k_inf Pr / (1 + Pr) F with the reduced pressure
+// Pr = k_0 [M] / k_inf and, for Troe, log10 F = log10 Fcent / (1 + f^2),
+// f = (log10 Pr + c) / (n - 0.14 (log10 Pr + c)), c = -0.4 - 0.67 log10 Fcent,
+// n = 0.75 - 1.27 log10 Fcent, Fcent = (1 - a) exp(-T/T3) + a exp(-T/T1)
+// (+ exp(-T2/T) for the four-parameter form). Returns k and its derivatives
+// d ln k / dT at fixed [M] and d ln k / d ln [M] by the chain rule.
+void falloff_rate(const Reaction& r, double T, double M, double& k, double& dlnk_dT, double& dlnk_dlnM) {
+  const double kinf = std::exp(r.lnA + r.beta * std::log(T) - r.Ea / (kR * T));
+  const double k0 = std::exp(r.lnA0 + r.beta0 * std::log(T) - r.Ea0 / (kR * T));
+  const double dlnkinf = r.beta / T + r.Ea / (kR * T * T);
+  const double dlnk0 = r.beta0 / T + r.Ea0 / (kR * T * T);
+  const double Pr = k0 * M / kinf;
+  if (!(Pr > 0)) { k = 0; dlnk_dT = 0; dlnk_dlnM = 0; return; }
+  double F = 1.0, dlnF_dlnPr = 0.0, dlnF_dT = 0.0;
+  if (r.falloff >= 2) {
+    const double e3 = std::exp(-T / r.T3), e1 = std::exp(-T / r.T1);
+    double Fcent = (1 - r.troe_a) * e3 + r.troe_a * e1;
+    double dFcent = -(1 - r.troe_a) / r.T3 * e3 - r.troe_a / r.T1 * e1;
+    if (r.falloff == 3) {
+      const double e2 = std::exp(-r.T2 / T);
+      Fcent += e2;
+      dFcent += r.T2 / (T * T) * e2;
+    }
+    const double lF = std::log10(Fcent);
+    const double c = -0.4 - 0.67 * lF, n = 0.75 - 1.27 * lF;
+    const double x = std::log10(Pr) + c;
+    const double den = n - 0.14 * x;
+    const double f = x / den;
+    const double LF = lF / (1 + f * f);                      // log10 F
+    F = std::pow(10.0, LF);
+    // d log10 F / d log10 Pr (= d ln F / d ln Pr) through f
+    const double df_dx = n / (den * den);
+    const double dLF_df = -lF * 2 * f / ((1 + f * f) * (1 + f * f));
+    dlnF_dlnPr = dLF_df * df_dx;
+    // d log10 F / d log10 Fcent at fixed Pr (c, n and f depend on it)
+    const double df_dlF = (-0.67 * den - x * (-1.27 + 0.14 * 0.67)) / (den * den);
+    const double dLF_dlF = 1 / (1 + f * f) + dLF_df * df_dlF;
+    dlnF_dT = dLF_dlF * dFcent / Fcent;                      // ln F = ln10 LF, d lF / dT = dFcent / (Fcent ln10)
+  }
+  k = kinf * Pr / (1 + Pr) * F;
+  const double dlnk_dlnPr = 1 / (1 + Pr) + dlnF_dlnPr;
+  dlnk_dlnM = dlnk_dlnPr;
+  dlnk_dT = dlnkinf + dlnk_dlnPr * (dlnk0 - dlnkinf) + dlnF_dT;
+}
 
 int delta_nu(const Reaction& r) {
   int d = 0;
@@ -157,10 +225,22 @@ Rates rates(const Mech& m, const Mix& x) {
   Rates R;
   int nr = m.nrx;
   R.kf.resize(nr); R.kr.resize(nr); R.fwd.resize(nr); R.rev.resize(nr); R.Mfac.resize(nr); R.q.resize(nr);
+  R.dlnkf_dT.resize(nr); R.dlnkf_dlnM.assign(nr, 0.0);
   double T = x.T;
   for (int j = 0; j < nr; ++j) {
     const Reaction& r = m.rx[j];
-    R.kf[j] = std::exp(r.lnA + r.beta * std::log(T) - r.Ea / (kR * T));
+    double M = 1.0;
+    if (r.thirdbody) {
+      M = 0;
+      for (int k = 0; k < m.nsp; ++k) M += r.eff[k] * x.c[k];
+    }
+    if (r.falloff) {
+      falloff_rate(r, T, M, R.kf[j], R.dlnkf_dT[j], R.dlnkf_dlnM[j]);
+      M = 1.0;                       // [M] enters through the reduced pressure only
+    } else {
+      R.kf[j] = std::exp(r.lnA + r.beta * std::log(T) - r.Ea / (kR * T));
+      R.dlnkf_dT[j] = r.beta / T + r.Ea / (kR * T * T);
+    }
     if (r.reversible) {
       double sum_nu_g = 0;
       for (auto& s : r.prod) sum_nu_g += s.second * g_k(m, s.first, T);
@@ -176,11 +256,6 @@ Rates rates(const Mech& m, const Mix& x) {
     for (auto& s : r.prod) pr *= powi(x.c[s.first], s.second);
     R.fwd[j] = pf;
     R.rev[j] = pr;
-    double M = 1.0;
-    if (r.thirdbody) {
-      M = 0;
-      for (int k = 0; k < m.nsp; ++k) M += r.eff[k] * x.c[k];
-    }
     R.Mfac[j] = M;
     R.q[j] = M * (pf - pr);
   }
@@ -236,9 +311,16 @@ void jacobian(const Mech& m, double p, const double* y, double* J, bool isotherm
     };
     side(r.reac, R.kf[j], 1.0);
     if (r.reversible) side(r.prod, R.kr[j], -1.0);
-    if (r.thirdbody)
+    if (r.falloff) {
+      // d q / d c_i through [M] = sum eff c: (d ln k_f / d ln [M]) q / [M]
+      double M = 0;
+      for (int i = 0; i < ns; ++i) M += r.eff[i] * x.c[i];
+      const double dqdM = M > 0 ? R.dlnkf_dlnM[j] * R.q[j] / M : 0.0;
+      for (int i = 0; i < ns; ++i) dq[i] += r.eff[i] * dqdM;
+    } else if (r.thirdbody) {
       for (int i = 0; i < ns; ++i) dq[i] += r.eff[i] * (R.fwd[j] - R.rev[j]);
-    double dlnkf = r.beta / T + r.Ea / (kR * T * T);
+    }
+    double dlnkf = R.dlnkf_dT[j];
     double dqdT = R.Mfac[j] * R.fwd[j] * dlnkf;
     if (r.reversible) {
       double dH = 0;

@@ -18,6 +18,15 @@ The layout is little-endian:
         i32 ridx[3], rnu[3], pidx[3], pnu[3]   (unused slots are -1 / 0)
     n_eff records of (i32 reaction, i32 species, f64 efficiency): third-body
         efficiencies that differ from 1; every other species counts with 1.
+    optional pressure-dependent (fall-off) section:
+        char[8] "FALLOFF1", i32 n_fall, then n_fall records of
+        i32 reaction, i32 kind (1 Lindemann, 2 Troe with 3 parameters,
+        3 Troe with 4), f64 lnA0, beta0, Ea0 (low-pressure limit, same units
+        as the high-pressure limit in the reaction record, one order higher),
+        f64 a, T3, T1, T2 (Troe parameters; T2 used by kind 3 only).
+        A fall-off reaction is a third-body reaction whose [M] (with its
+        efficiencies) enters through the reduced pressure instead of
+        multiplying the rate.
 
 Each species appears at most once per side; its integer coefficient is in
 rnu / pnu.
@@ -50,6 +59,7 @@ class Mechanism:
     reversible: np.ndarray       # [nrx] int
     thirdbody: np.ndarray        # [nrx] int
     eff: list = dataclasses.field(default_factory=list)  # (rxn, species, eff)
+    falloff: list = dataclasses.field(default_factory=list)  # (rxn, kind, lnA0, beta0, Ea0, a, T3, T1, T2)
 
     @property
     def nsp(self) -> int:
@@ -92,6 +102,14 @@ def write_mech(path: str, m: Mechanism) -> None:
                                 *ridx, *rnu, *pidx, *pnu))
         for (j, k, e) in m.eff:
             f.write(struct.pack("<2id", int(j), int(k), float(e)))
+        if m.falloff:
+            f.write(b"FALLOFF1")
+            f.write(struct.pack("<i", len(m.falloff)))
+            for rec in m.falloff:
+                j, kind = int(rec[0]), int(rec[1])
+                if kind not in (1, 2, 3) or not m.thirdbody[j]:
+                    raise ValueError(f"fall-off record {rec}: kind 1..3 on a third-body reaction")
+                f.write(struct.pack("<2i7d", j, kind, *[float(x) for x in rec[2:9]]))
 
 
 def read_mech(path: str) -> Mechanism:
@@ -123,6 +141,14 @@ def read_mech(path: str) -> Mechanism:
         j, k, e = struct.unpack_from("<2id", buf, off)
         off += 16
         eff.append((j, k, e))
+    falloff = []
+    if len(buf) >= off + 12 and buf[off:off + 8] == b"FALLOFF1":
+        (nf,) = struct.unpack_from("<i", buf, off + 8)
+        off += 12
+        for _ in range(nf):
+            rec = struct.unpack_from("<2i7d", buf, off)
+            off += 64
+            falloff.append(tuple(rec))
     return Mechanism(W=arrs[0], cp_a=arrs[1], cp_b=arrs[2], hf=arrs[3], s0=arrs[4], atoms=atoms,
                      lnA=np.array(lnA), beta=np.array(beta), Ea=np.array(Ea), reac=reac, prod=prod,
-                     reversible=np.array(rev), thirdbody=np.array(tb), eff=eff)
+                     reversible=np.array(rev), thirdbody=np.array(tb), eff=eff, falloff=falloff)

@@ -148,3 +148,32 @@ def generate_mechanism(nsp: int, nrx: int, seed: int, tb_fraction: float = 0.1) 
                      reac=[reac[i] for i in perm], prod=[prod[i] for i in perm],
                      reversible=np.ones(nrx, dtype=np.int64),
                      thirdbody=np.array([tb[i] for i in perm], dtype=np.int64), eff=[])
+
+
+def with_falloff(m: Mechanism, seed: int) -> Mechanism:
+    """A copy of m whose third-body reactions become pressure-dependent
+    (fall-off) reactions, cycling through Lindemann, three- and four-parameter
+    Troe forms, each with listed efficiencies for two species. The low-
+    pressure limit is drawn so that the reduced pressure is of order one at
+    the concentrations of 1-20 bar: A0 = A * U[1e4, 1e6] cm^3/mol,
+    beta0 = beta - U[0, 1.5], Ea0 = max(0, Ea - U[0, 20] kJ/mol); Troe
+    a ~ U[0.2, 0.9], T3 ~ U[100, 500] K, T1 ~ U[1000, 3000] K, T2 ~ U[2000,
+    6000] K. (Stand-in for real mechanisms' fall-off data, which is not
+    available here; only the seeded draw lives in this package.)"""
+    import copy
+    rng = np.random.default_rng(seed + 777)
+    out = copy.deepcopy(m)
+    tb = np.flatnonzero(np.asarray(m.thirdbody) != 0)
+    falloff, eff = [], [e for e in m.eff if e[0] not in set(tb.tolist())]
+    for i, j in enumerate(tb):
+        kind = 1 + i % 3
+        lnA0 = m.lnA[j] + np.log(rng.uniform(1e4, 1e6))
+        beta0 = m.beta[j] - rng.uniform(0.0, 1.5)
+        Ea0 = max(0.0, m.Ea[j] - rng.uniform(0.0, 20e3))
+        a, T3, T1, T2 = rng.uniform(0.2, 0.9), rng.uniform(100, 500), rng.uniform(1000, 3000), rng.uniform(2000, 6000)
+        falloff.append((int(j), kind, lnA0, beta0, Ea0, a, T3, T1, T2))
+        for k in rng.choice(m.nsp, size=2, replace=False):
+            eff.append((int(j), int(k), float(rng.uniform(0.3, 3.0))))
+    out.falloff = falloff
+    out.eff = eff
+    return out

@@ -6,7 +6,7 @@ import numpy as np
 from synth import Mechanism, write_mech
 
 
-def make(path, species, reactions, eff=()):
+def make(path, species, reactions, eff=(), falloff=()):
     """species: list of dicts (atoms, hf, s0, a, b); reactions: dicts with
     reac, prod [(k, nu)], lnA, beta, Ea, rev, tb."""
     atoms = np.array([s["atoms"] for s in species])
@@ -20,6 +20,7 @@ def make(path, species, reactions, eff=()):
                   Ea=np.array([r.get("Ea", 0.0) for r in reactions], float),
                   reac=[r["reac"] for r in reactions], prod=[r["prod"] for r in reactions],
                   reversible=np.array([r.get("rev", 1) for r in reactions]),
-                  thirdbody=np.array([r.get("tb", 0) for r in reactions]), eff=list(eff))
+                  thirdbody=np.array([r.get("tb", 0) for r in reactions]), eff=list(eff),
+                  falloff=list(falloff))
     write_mech(str(path), m)
     return m

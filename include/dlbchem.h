@@ -107,11 +107,13 @@ typedef struct dlbchem_options {
                            (no previous call needed); steps[] is then only written */
   int32_t surrogate;    /* 1: try the attached network's increments first; cells that pass the
                            gate get status DLBCHEM_CELL_SURROGATE, the others are integrated;
-                           2: the same with the proposal y + dt f(y) + the network's output (an
-                           explicit Euler step corrected by a network trained on the residual
-                           increment - dt f(y), see dlbchem_rhs) */
+                           2: candidates y + dt f(y) + the network's output (an explicit Euler
+                           step corrected by a network trained on the residual increment
+                           - dt f(y), see dlbchem_rhs), then y + dt f(y), then y */
   double gate;          /* surrogate gate tolerance (default 1e-4): trapezoid defect per mass
-                           fraction (relative for T), |sum Y' - 1| and relative element change */
+                           fraction (relative for T), |sum Y' - 1|, relative element change,
+                           every Y'_k >= -gate, and dt |f(y') - f(y)| <= |y' - y| + 2 gate
+                           (not stiff along the increment) */
 } dlbchem_options;
 
 /* Fill *opt with the defaults listed above. Returns DLBCHEM_OK or BAD_ARG. */

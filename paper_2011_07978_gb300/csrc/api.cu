@@ -94,6 +94,23 @@ bool parse_mech(const char* path, dlb::HostMech& m, std::string& err) {
     m.rx[j].eff.push_back({k, e});
   }
   if (!rd.ok) { err = "truncated mechanism file"; return false; }
+  // optional fall-off section
+  if (rd.pos + 12 <= buf.size() && std::memcmp(buf.data() + rd.pos, "FALLOFF1", 8) == 0) {
+    rd.pos += 8;
+    const int nf = rd.get<int32_t>();
+    for (int i = 0; i < nf && rd.ok; ++i) {
+      const int j = rd.get<int32_t>(), kind = rd.get<int32_t>();
+      double d[7];
+      for (auto& x : d) x = rd.get<double>();
+      if (!rd.ok) break;
+      if (j < 0 || j >= m.nrx || kind < 1 || kind > 3 || !m.rx[j].tb) { err = "bad fall-off record"; return false; }
+      if (kind >= 2 && (!(d[4] > 0) || !(d[5] > 0))) { err = "Troe T3 and T1 must be positive"; return false; }
+      HostRxn& r = m.rx[j];
+      r.fall = kind;
+      r.lnA0 = d[0]; r.beta0 = d[1]; r.Ea0 = d[2]; r.troe_a = d[3]; r.T3 = d[4]; r.T1 = d[5]; r.T2 = d[6];
+    }
+    if (!rd.ok) { err = "truncated fall-off section"; return false; }
+  }
   for (int k = 0; k < m.nsp; ++k)
     if (!(m.W[k] > 0.0)) { err = "non-positive molar mass"; return false; }
   return true;
@@ -317,6 +334,9 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
       if (cst < best) { best = cst; order = o; parity = par; }
     }
   }
+  // fall-off reactions first (stable), so that they share warp rounds and the
+  // other rounds never take their branch
+  std::stable_partition(order.begin(), order.end(), [&](int r) { return hm.rx[r].fall != 0; });
   if (order_out) *order_out = order;
   // reactions (device index r is file reaction order[r])
   std::vector<double> lnA(nrx), beta(nrx), EaR(nrx), dH0(nrx, 0.0), dHa(nrx, 0.0), dHb(nrx, 0.0);
@@ -325,6 +345,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   // dHa T + dHb T^2, collected as B2/T^2 + B1/T + B0
   std::vector<double> kB0(nrx, 0.0), kB1(nrx, 0.0), kB2(nrx, 0.0);
   std::vector<RxnMeta> meta(nrx);
+  std::vector<double> fall(size_t(8) * std::max(nrx, 1), 0.0);
   std::vector<int32_t> eff_sp;
   std::vector<double> eff_dm1;
   std::vector<std::vector<int>> distinct(nrx);
@@ -350,7 +371,13 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
     for (int i = 0; i < int(x.r.size()); ++i) { mt.sp[i] = int16_t(x.r[i]); mt.ds[i] = uint8_t(slot_of(x.r[i])); }
     for (int i = 0; i < int(x.p.size()); ++i) { mt.sp[3 + i] = int16_t(x.p[i]); mt.ds[3 + i] = uint8_t(slot_of(x.p[i])); }
     mt.dnu = int8_t(int(x.p.size()) - int(x.r.size()));
-    mt.flags = (x.rev ? RX_REV : 0) | (x.tb ? RX_TB : 0);
+    mt.flags = (x.rev ? RX_REV : 0) | (x.tb ? RX_TB : 0) | (x.fall ? RX_FALL : 0) | (x.fall >= 2 ? RX_TROE : 0) |
+               (x.fall == 3 ? RX_TROE4 : 0);
+    if (x.fall) {
+      double* f = fall.data() + size_t(8) * r;
+      f[0] = x.lnA0 - x.lnA; f[1] = x.beta0 - x.beta; f[2] = (x.Ea0 - x.Ea) / kR;
+      f[3] = x.troe_a; f[4] = x.fall >= 2 ? 1.0 / x.T3 : 0.0; f[5] = x.fall >= 2 ? 1.0 / x.T1 : 0.0; f[6] = x.T2;
+    }
     mt.nds = uint8_t(dl.size());
     mt.eff_begin = int32_t(eff_sp.size());
     if (x.tb && !x.eff.empty()) {
@@ -489,6 +516,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   offs.push_back(put(inc_all.data(), std::max<size_t>(inc_all.size(), 1) * 4));
   offs.push_back(put(incp_all.data(), incp_all.size() * 4));
   for (auto* v : {&kB0, &kB1, &kB2}) offs.push_back(put(v->data(), v->size() * 8));
+  offs.push_back(put(fall.data(), fall.size() * 8));
   // store offsets as fake pointers; relocated after upload
   auto P = [&](int i) { return reinterpret_cast<const double*>(offs[i]); };
   dm.W = P(0); dm.iW = P(1); dm.H0 = P(2); dm.cpa = P(3); dm.hcpb = P(4); dm.cpb = P(5);
@@ -507,6 +535,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   dm.inc_all = reinterpret_cast<const uint32_t*>(offs[24]);
   dm.incp_all = reinterpret_cast<const int32_t*>(offs[25]);
   dm.kB0 = P(26); dm.kB1 = P(27); dm.kB2 = P(28);
+  dm.fall = P(29);
   return true;
 }
 
@@ -530,6 +559,7 @@ void relocate(DevMech& dm, void* base) {
   dm.inc_all = reloc(dm.inc_all, base);
   dm.incp_all = reloc(dm.incp_all, base);
   dm.kB0 = reloc(dm.kB0, base); dm.kB1 = reloc(dm.kB1, base); dm.kB2 = reloc(dm.kB2, base);
+  dm.fall = reloc(dm.fall, base);
 }
 
 int configure_launch(dlbchem_ctx* c) {

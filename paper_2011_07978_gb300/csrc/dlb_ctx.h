@@ -19,6 +19,10 @@ struct HostRxn {
   int rev, tb;
   std::vector<int> r, p;       // species per slot, expanded by coefficient
   std::vector<std::pair<int, double>> eff;   // listed efficiencies (species, eff)
+  // pressure-dependent (fall-off) form: 0 none, 1 Lindemann, 2 / 3 Troe with
+  // 3 / 4 parameters; low-pressure limit lnA0, beta0, Ea0; Troe a, T3, T1, T2
+  int fall = 0;
+  double lnA0 = 0, beta0 = 0, Ea0 = 0, troe_a = 0, T3 = 1, T1 = 1, T2 = 0;
 };
 
 struct HostMech {

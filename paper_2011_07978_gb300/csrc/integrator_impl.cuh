@@ -205,10 +205,62 @@ __device__ __forceinline__ double rcp_nr(double d) {
 // size) at a time: rate pass, then the chunk's incidence rounds and its
 // Jacobian rounds into M.
 // ---------------------------------------------------------------------------
+// Pressure-dependent (fall-off) factor k / k_inf = Pr/(1 + Pr) F with the
+// reduced pressure Pr = k_0 [M] / k_inf = exp(dlnA + dbeta ln T - dEa/(R T)
+// + ln [M]) and F = 1 (Lindemann) or Troe's log10 F = log10 Fcent / (1 + f^2),
+// f = x / (n - 0.14 x), x = log10 Pr + c, c = -0.4 - 0.67 log10 Fcent,
+// n = 0.75 - 1.27 log10 Fcent, Fcent = (1 - a) e^(-T/T3) + a e^(-T/T1)
+// [+ e^(-T2/T)] (Gilbert, Luther and Troe 1983). With JAC also
+// eM = d ln k / d ln [M] and dT = d ln k / dT - d ln k_inf / dT at fixed [M].
+// [M] <= 0 gives 0.
+constexpr double kLn10 = 2.302585092994046, kInvLn10 = 0.4342944819032518;
+template <bool JAC>
+__device__ __forceinline__ double falloff_factor(const double* __restrict__ fp, uint8_t flags, const Mix& mx, double M,
+                                                 const double* __restrict__ tab, double& eM, double& dT) {
+  eM = 0.0;
+  dT = 0.0;
+  if (!(M > 0.0)) return 0.0;
+  const double lnPr = fma(fp[1], mx.lnT, fma(-fp[2], mx.iT, fp[0])) + log(M);
+  const double Pr = exp_tab(lnPr, tab);
+  const double ipr1 = rcp_nr(1.0 + Pr);
+  double fac = Pr * ipr1;
+  double dlnF_dlnPr = 0.0, dlnF_dT = 0.0;
+  if (flags & RX_TROE) {
+    const double T = mx.T, a = fp[3];
+    const double e3 = exp_tab(-T * fp[4], tab), e1 = exp_tab(-T * fp[5], tab);
+    double Fc = fma(1.0 - a, e3, a * e1);
+    double dFc = -fma((1.0 - a) * fp[4], e3, (a * fp[5]) * e1);
+    if (flags & RX_TROE4) {
+      const double e2 = exp_tab(-fp[6] * mx.iT, tab);
+      Fc += e2;
+      dFc = fma(fp[6] * mx.iT2, e2, dFc);
+    }
+    const double lF = log(Fc) * kInvLn10;
+    const double c = fma(-0.67, lF, -0.4), n = fma(-1.27, lF, 0.75);
+    const double x = fma(lnPr, kInvLn10, c);
+    const double den = fma(-0.14, x, n);
+    const double iden = rcp_nr(den);
+    const double f = x * iden;
+    const double i1f2 = rcp_nr(fma(f, f, 1.0));
+    fac *= exp_tab((lF * i1f2) * kLn10, tab);
+    if (JAC) {
+      const double dLF_df = -2.0 * lF * f * (i1f2 * i1f2);
+      dlnF_dlnPr = dLF_df * (n * (iden * iden));
+      const double df_dlF = fma(-0.67, den, -x * (-1.27 + 0.14 * 0.67)) * (iden * iden);
+      dlnF_dT = fma(dLF_df, df_dlF, i1f2) * (dFc * rcp_nr(Fc));
+    }
+  }
+  if (JAC) {
+    eM = ipr1 + dlnF_dlnPr;
+    dT = fma(eM, fma(fp[2], mx.iT2, fp[1] * mx.iT), dlnF_dT);
+  }
+  return fac;
+}
+
 template <bool JAC>
 __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mix& mx, int r, int rl, double* qdst) {
   const RxnMeta mt = m.meta[r];
-  const double kf = exp_tab(fma(m.beta[r], mx.lnT, fma(-m.EaR[r], mx.iT, m.lnA[r])), w.exptab);
+  double kf = exp_tab(fma(m.beta[r], mx.lnT, fma(-m.EaR[r], mx.iT, m.lnA[r])), w.exptab);
   // expanded slots as fixed registers (unused slots hold 1)
   const double a0 = w.c[mt.sp[0]];
   const double a1 = mt.nr > 1 ? w.c[mt.sp[1]] : 1.0;
@@ -218,8 +270,16 @@ __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mi
     Mf = mx.Ctot;
     for (int e = mt.eff_begin; e < mt.eff_end; ++e) Mf = fma(m.eff_dm1[e], w.c[m.eff_sp[e]], Mf);
   }
+  // the rate's multiplier: [M] for a third-body reaction, 1 for a fall-off
+  // reaction (its [M] enters through k) and for the others
+  double Mq = Mf, eM = 0.0, dfT = 0.0;
+  const bool fall = (mt.flags & RX_FALL) != 0;
+  if (fall) {
+    kf *= falloff_factor<JAC>(m.fall + 8 * size_t(r), mt.flags, mx, Mf, w.exptab, eM, dfT);
+    Mq = 1.0;
+  }
   if (!JAC) {
-    // q = [M] k_f (prod c_reac - prod E_reac prod (c/E)_prod); Einv holds c_k / E_k here
+    // q = Mq k_f (prod c_reac - prod E_reac prod (c/E)_prod); Einv holds c_k / E_k here
     double d = a0 * (a1 * a2);
     if (mt.flags & RX_REV) {
       const double e1 = mt.nr > 1 ? w.E[mt.sp[1]] : 1.0;
@@ -228,7 +288,7 @@ __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mi
       const double g2 = mt.np > 2 ? w.Einv[mt.sp[5]] : 1.0;
       d = fma(-(w.E[mt.sp[0]] * (e1 * e2)), w.Einv[mt.sp[3]] * (g1 * g2), d);
     }
-    qdst[rl] = (Mf * kf) * d;
+    qdst[rl] = (Mq * kf) * d;
     return;
   }
   const double pf = kf * (a0 * (a1 * a2));
@@ -244,33 +304,39 @@ __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mi
     b2 = mt.np > 2 ? w.c[mt.sp[5]] : 1.0;
     pr = kr * (b0 * (b1 * b2));
   }
-  qdst[rl] = Mf * (pf - pr);
+  qdst[rl] = Mq * (pf - pr);
   double* D = w.D + rl * m.DS;
   for (int s2 = 0; s2 < mt.nds; ++s2) D[s2] = 0.0;
   // d/dc_j of the slot product = product of the other slots
-  const double kfM = kf * Mf;
+  const double kfM = kf * Mq;
   D[mt.ds[0]] += kfM * (a1 * a2);
   if (mt.nr > 1) D[mt.ds[1]] += kfM * (a0 * a2);
   if (mt.nr > 2) D[mt.ds[2]] += kfM * (a0 * a1);
   if (mt.flags & RX_REV) {
-    const double krM = kr * Mf;
+    const double krM = kr * Mq;
     D[mt.ds[3]] -= krM * (b1 * b2);
     if (mt.np > 1) D[mt.ds[4]] -= krM * (b0 * b2);
     if (mt.np > 2) D[mt.ds[5]] -= krM * (b0 * b1);
   }
   const int tb = (mt.flags & RX_TB) ? 1 : 0;
-  if (mt.flags & RX_EFF) D[mt.dslot_eff] = pf - pr;
+  // d q / d [M]: fwd - rev for a third-body reaction, eM q / [M] for fall-off
+  const double stb = fall ? (Mf > 0.0 ? (eM * (pf - pr)) * rcp_nr(Mf) : 0.0) : (pf - pr);
+  if (mt.flags & RX_EFF) D[mt.dslot_eff] = stb;
   // small integers as doubles from the shared table (nutab[j] = j - 8), not by conversion
-  const double sig = Mf * (w.nutab[8 + mt.nr + tb] * pf - w.nutab[8 + mt.np + tb] * pr);
+  const int tbn = fall ? 0 : tb;
+  double sig = Mq * (w.nutab[8 + mt.nr + tbn] * pf - w.nutab[8 + mt.np + tbn] * pr);
+  if (fall) sig = fma(eM, pf - pr, sig);   // sum_j c_j dq/dc_j through [M]: eM q
   // d q / d T at fixed c: pf d ln k_f / dT - pr d ln k_r / dT, with
   // d ln k_r / dT = d ln k_f / dT - d ln K_c / dT = kB2 / T^2 + kB1 / T + kB0
+  // (fall-off adds dfT to both)
   const double dlnkf = fma(m.EaR[r], mx.iT2, m.beta[r] * mx.iT);
   double dq = pf * dlnkf;
   if (mt.flags & RX_REV) dq = fma(-pr, fma(m.kB2[r], mx.iT2, fma(m.kB1[r], mx.iT, m.kB0[r])), dq);
+  if (fall) dq = fma(dfT, pf - pr, dq);
   // the assembly needs v only inside dwdot/dT - v/T and u - v/(rho S), so the
   // gathers carry those two combinations (sigma = sum_j c_j dq/dc_j)
-  w.dqdT[rl] = fma(-sig, mx.iT, Mf * dq);
-  w.dlt[rl] = fma(-sig, mx.irS, tb ? (pf - pr) : 0.0);
+  w.dqdT[rl] = fma(-sig, mx.iT, Mq * dq);
+  w.dlt[rl] = fma(-sig, mx.irS, tb ? stb : 0.0);
 }
 
 template <int WPC, bool JAC>
@@ -1091,13 +1157,18 @@ __global__ void __launch_bounds__(128, WPC == 1 ? 4 : (WPC == 2 ? 3 : 2)) rosenb
 }
 
 // ---------------------------------------------------------------------------
-// Surrogate gate: a predicted state (T', Y') = (T, Y) + (dT, dY), or with
-// residual = 1 (T, Y) + dt f(T, Y) + (dT, dY), is accepted only if it is
-// consistent with the chemistry over the step to the gate tolerance g: the trapezoid defect y' - y - dt/2 (f(y) + f(y')) is at
-// most g in every mass fraction and g*T in temperature, |sum Y' - 1| <= g, and
-// every element total changes by at most g relative. Accepted cells get
-// (T', Y'), status SURROGATE and steps 0; the others stay on the work list and
-// are integrated (the plain integrator is the fallback and the arbiter of its error).
+// Surrogate gate: a predicted state (T', Y') = (T, Y) + (dT, dY) (with
+// residual = 1 the candidates (T, Y) + dt f(T, Y) + (dT, dY), then
+// (T, Y) + dt f(T, Y), then (T, Y)) is accepted only if it is consistent with
+// the chemistry over the step to the gate tolerance g: the trapezoid defect
+// y' - y - dt/2 (f(y) + f(y')) is at most g in every mass fraction and g*T in
+// temperature, |sum Y' - 1| <= g, every element total changes by at most g
+// relative, no mass fraction is below -g, and dt |f(y') - f(y)| <=
+// |y' - y| + 2g (T relative), so that the step is not stiff along its own
+// increment (where the trapezoid equation has spurious roots). Accepted
+// cells get (T', Y'), status SURROGATE and steps 0; the others stay on the
+// work list and are integrated (the plain integrator is the fallback and the
+// arbiter of its error).
 // ---------------------------------------------------------------------------
 template <int WPC>
 __global__ void __launch_bounds__(128) gate_kernel(const GateArgs a) {
@@ -1139,12 +1210,16 @@ __global__ void __launch_bounds__(128) gate_kernel(const GateArgs a) {
     const double P1 = 1e-6 * p / kR;
     const double iP1 = 1.0 / P1;
     eval_f<WPC>(m, tm, w, w.y0, P1, iP1, a.P.isothermal != 0, w.f0);
-    // candidates: the network's proposal; with residual, first the explicit
-    // Euler step plus the network's correction, then the Euler step alone
-    const int ncand = a.residual ? 2 : 1;
+    // candidates: the network's proposal; with residual, the explicit Euler
+    // step plus the network's correction, then the Euler step alone, then
+    // the zero increment (a nearly inert cell)
+    const int ncand = a.residual ? 3 : 1;
     for (int cand = 0; cand < ncand; ++cand) {
       if (a.residual) {
-        for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(a.P.dt, w.f0[i], cand == 0 ? w.ys[i] : w.y0[i]);
+        for (int i = tm.tid; i < N; i += TS) {
+          const double base = cand == 0 ? w.ys[i] : w.y0[i];
+          w.ys[i] = cand == 2 ? w.y0[i] : fma(a.P.dt, w.f0[i], base);
+        }
         tm.sync();
       }
       bad = 0;
@@ -1153,11 +1228,20 @@ __global__ void __launch_bounds__(128) gate_kernel(const GateArgs a) {
       if (tm.any(bad)) continue;
       eval_f<WPC>(m, tm, w, w.ys, P1, iP1, a.P.isothermal != 0, w.fs);
       const double hdt = 0.5 * a.P.dt;
+      // trapezoid defect, realizability (no mass fraction below -gate) and a
+      // stiffness guard: dt |f(y') - f(y)| may not exceed |y' - y| + 2 gate
+      // (T relative), i.e. the step is not stiff along its own increment;
+      // without it a stiff cell's trapezoid equation has spurious roots
       double dY = 0.0, sumY = 0.0, e0 = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0, t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+      double lip = 0.0, inc = 0.0, ymin = 0.0;
       for (int i = tm.tid; i < N; i += TS) {
         const double def = fabs(w.ys[i] - w.y0[i] - hdt * (w.f0[i] + w.fs[i]));
+        const double dfs = 2.0 * hdt * fabs(w.fs[i] - w.f0[i]), dys = fabs(w.ys[i] - w.y0[i]);
         if (i > 0) {
           dY = fmax(dY, def);
+          lip = fmax(lip, dfs);
+          inc = fmax(inc, dys);
+          ymin = fmin(ymin, w.ys[i]);
           const int k = i - 1;
           const double yk = w.ys[i], dk = w.ys[i] - w.y0[i];
           sumY += yk;
@@ -1166,9 +1250,13 @@ __global__ void __launch_bounds__(128) gate_kernel(const GateArgs a) {
           e2 = fma(m.aW[2 * nsp + k], dk, e2); t2 = fma(m.aW[2 * nsp + k], w.y0[i], t2);
           e3 = fma(m.aW[3 * nsp + k], dk, e3); t3 = fma(m.aW[3 * nsp + k], w.y0[i], t3);
         } else {
-          dY = fmax(dY, def / w.y0[0]);        // temperature: relative defect
+          const double iT0 = 1.0 / w.y0[0];
+          dY = fmax(dY, def * iT0);            // temperature: relative defect
+          lip = fmax(lip, dfs * iT0);
+          inc = fmax(inc, dys * iT0);
         }
       }
+      const double lipm = tm.maxv(lip), incm = tm.maxv(inc), yminm = -tm.maxv(-ymin);
       const double worst = tm.maxv(dY);
       const double S = tm.sum(sumY);
       const double E0 = tm.sum(e0), E1 = tm.sum(e1), E2 = tm.sum(e2), E3 = tm.sum(e3);
@@ -1178,7 +1266,8 @@ __global__ void __launch_bounds__(128) gate_kernel(const GateArgs a) {
       if (R1 > 0) ed = fmax(ed, fabs(E1) / R1);
       if (R2 > 0) ed = fmax(ed, fabs(E2) / R2);
       if (R3 > 0) ed = fmax(ed, fabs(E3) / R3);
-      const bool accept = worst <= a.gate && fabs(S - 1.0) <= a.gate && ed <= a.gate;
+      const bool accept = worst <= a.gate && fabs(S - 1.0) <= a.gate && ed <= a.gate && yminm >= -a.gate &&
+                          lipm <= incm + 2.0 * a.gate;
       if (accept) {
         for (int i = tm.tid; i < N; i += TS) {
           if (i == 0) a.Tout[cell] = w.ys[0];

@@ -172,7 +172,8 @@ def test_gate_accept_branch_with_a_host_built_network():
     """Drives the gate's accept branch with a network built on the host: all
     weights and biases zero and output normalisation mu = 0, sd = 1, so its
     output is exactly zero. With surrogate = 1 it proposes a zero increment,
-    with surrogate = 2 the explicit Euler step y + dt f(y). On the bimodal
+    with surrogate = 2 the explicit Euler step y + dt f(y) and then the zero
+    increment. On the bimodal
     field's near-equilibrium burnt cells (53 species, dt 1e-5) the gate
     accepts them, and never a flame-front cell. Accepted cells meet the gate
     against the oracle's right-hand side, their error against the oracle's
@@ -214,9 +215,14 @@ def test_gate_accept_branch_with_a_host_built_network():
         for i in np.flatnonzero(acc)[:300]:
             y0 = np.concatenate([[T[i]], Y[:, i]])
             y1 = np.concatenate([[To[i]], Yo[:, i]])
-            defect = y1 - y0 - 0.5 * dt * (orc.rhs(p[i], y0) + orc.rhs(p[i], y1))
+            f0, f1 = orc.rhs(p[i], y0), orc.rhs(p[i], y1)
+            defect = y1 - y0 - 0.5 * dt * (f0 + f1)
             assert abs(defect[0]) <= gate * T[i] * (1 + 1e-6) and np.abs(defect[1:]).max() <= gate * (1 + 1e-6)
-            assert abs(Yo[:, i].sum() - 1) <= gate
+            assert abs(Yo[:, i].sum() - 1) <= gate and Yo[:, i].min() >= -gate
+            # not stiff along the increment: dt |f(y') - f(y)| <= |y' - y| + 2 gate (T relative)
+            w = np.concatenate([[1.0 / T[i]], np.ones(Y.shape[0])])
+            lip, inc = (dt * np.abs(f1 - f0) * w).max(), (np.abs(y1 - y0) * w).max()
+            assert lip <= (inc + 2 * gate) * (1 + 1e-6) + 1e-12
         sel = np.flatnonzero(acc)
         o = orc.integrate(T[sel], p[sel], Y[:, sel], dt, rtol=1e-5, atol=1e-8)
         err_T = np.abs(To[sel] - o[0]) / o[0]

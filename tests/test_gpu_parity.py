@@ -542,7 +542,12 @@ def test_falloff_mechanism_parity(tmp_path, which):
     p = np.geomspace(1e4, 5e6, T.size)[np.random.default_rng(1).permutation(T.size)]
     ctx = dlb().Context(path, rtol=rtol, atol=atol, schedule=dlb().SCHED_QUEUE)
     g = run_gpu(ctx, T, p, Y, dt)
-    o = oracle.Oracle(path).integrate(T, p, Y, dt, rtol=rtol, atol=atol)
+    orc = oracle.Oracle(path)
+    o = orc.integrate(T, p, Y, dt, rtol=rtol, atol=atol)
+    tight = orc.integrate(T, p, Y, dt, rtol=rtol * 1e-3, atol=atol * 1e-4)
     assert (g[3] == 0).all()
-    dT, dY, frac = assert_parity(g, o)
-    print(f"fall-off {which}: max dT/T {dT:.2e}, max dY {dY:.2e}")
+    # measured: 399 of 400 cells of the 10-species field within 1e-9, one at 2.7e-9
+    # (a rounding-sensitive step sequence); such a cell must be as close to a
+    # tight-tolerance solution as the oracle's own result, within a factor 2
+    dT, dY, frac = assert_parity(g, o, min_tight=0.99, tight_ref=tight[:2])
+    print(f"fall-off {which}: max dT/T {dT:.2e}, max dY {dY:.2e}, within 1e-9 {frac:.4f}")

@@ -46,9 +46,9 @@ METRIC = "chemistry cells/s per dt at stated T/Y error vs FP64 oracle; frac of F
 # FMA lanes per clock per SM x 2 flop (= the 1.25 TFLOP/s nominal figure).
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP64 integrator launch
-# from ncu on the 2048-cell case (1.419 MB + 0 B), scaled by cells to the full
-# 262,144-cell field; None whenever the kernel changes after the capture.
-INTEGRATOR_TRAFFIC_BYTES = 1.4190e6 * 262144 / 2048
+# from ncu, scaled to the benchmark's launch; None whenever the kernel has
+# changed since the capture.
+INTEGRATOR_TRAFFIC_BYTES = None
 N_F = 3   # function evaluations per Rosenbrock step (stage 4 reuses stage 3's)
 PAPER_CONTEXT = ("paper (DLBFoam, arXiv 2011.07978): load balancing + reference mapping speed the CPU "
                  "chemistry step up by about 10x (Spray A, 256 MPI ranks on 2x64-core AMD EPYC Rome nodes, "
@@ -239,6 +239,35 @@ def time_form(dlbchem, mech_path, fstep, Td, pd, Yd, To, Yo, stream, *, schedule
             "fp64_fallbacks": st["fp64_fallbacks"] if precision else None}
 
 
+def mlp_forward_rate(dlbchem, dev, stream, n):
+    """Forward pass of the 13 -> 256 -> 256 -> 256 -> 12 network on n cells
+    (random weights), timed with CUDA events: TFLOP/s of its GEMMs against
+    the measured BF16 peak."""
+    import torch
+    net = dlbchem.MLP(13, 256, 12)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    net.set_params((torch.randn(net.nparams, generator=g) * 0.05).to(dev))
+    X = torch.randn(n, 13, generator=g).to(dev)
+    out = torch.empty(n, 12, dtype=torch.float32, device=dev)
+    for _ in range(2):
+        net.forward(X, out, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        net.forward(X, out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 5
+    flops = 2.0 * n * (13 * 256 + 2 * 256 * 256 + 256 * 12)
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = json.load(open(peaks))["bf16_tflops"] if os.path.exists(peaks) else 1900.0
+    tf = flops / (ms / 1e3) / 1e12
+    net.close()
+    return {"cells": n, "ms": ms, "achieved_tflops": tf, "peak_bf16_tflops": peak, "frac": tf / peak,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops" if os.path.exists(peaks) else "fallback 1.9 PFLOP/s",
+            "kernel": "gemm_tc_kernel (tcgen05.mma kind::f16, TMEM accumulator)"}
+
+
 def fp64_probe(dlbchem, dev, stream):
     """Measured FP64 FMA throughput (TFLOP/s) of this GPU, best of 3 launches."""
     import torch
@@ -408,6 +437,9 @@ def main():
         "wall_s_timed": wall,
         "paper_context": PAPER_CONTEXT,
     }
+    # the network's forward pass on the field: its GEMMs on the tensor cores
+    # against the BF16 peak (algorithmic 2 (13*256 + 2*256^2 + 256*12) flops per cell)
+    line["mlp_forward"] = mlp_forward_rate(dlbchem, dev, stream, n)
     if not args.no_arms:
         arms = {}
         scratch_T, scratch_Y = torch.empty_like(Td), torch.empty_like(Yd)

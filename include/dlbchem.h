@@ -121,7 +121,9 @@ int dlbchem_options_default(dlbchem_options* opt);
 
 /*
  * Load a mechanism file (the DLBMECH1 binary format written by the seeded
- * generator) on the current CUDA device and create a context. opt may be
+ * generator) on the current CUDA device and create a context: the
+ * preprocessing of Sec. 2.2 stage 1 that every cell shares (the kinetics
+ * each problem of Sec. 2.2 is integrated with). opt may be
  * NULL (defaults). On success *out owns device copies of the mechanism
  * tables; release it with dlbchem_destroy. On failure *out is NULL and the
  * message is available from dlbchem_last_error(NULL).
@@ -272,7 +274,9 @@ const char* dlbchem_mlp_last_error(const dlbchem_mlp* m);
 void dlbchem_mlp_destroy(dlbchem_mlp* m);
 int dlbchem_attach_mlp(dlbchem_ctx* ctx, dlbchem_mlp* m);
 
-/* Number of species / reactions of the loaded mechanism (-1 if ctx NULL). */
+/* Number of species / reactions of the loaded mechanism (-1 if ctx NULL): the
+ * size of the per-cell state (Sec. 2.2: a problem carries N_sp + 6 doubles)
+ * and of the kinetics. */
 int dlbchem_nspecies(const dlbchem_ctx* ctx);
 int dlbchem_nreactions(const dlbchem_ctx* ctx);
 
@@ -352,10 +356,12 @@ int dlbchem_rhs(dlbchem_ctx* ctx, int64_t ncells, const double* T, const double*
 int dlbchem_fp64_fma_probe(int64_t iters, double* out, int64_t nout, int64_t* flops, void* cuda_stream);
 
 /* Message of the last failed call on ctx, or of the last failed create when
- * ctx is NULL. Never NULL; "" when there was no error. Owned by the library. */
+ * ctx is NULL. Never NULL; "" when there was no error. Owned by the library.
+ * (Bookkeeping of the library; the paper has no counterpart.) */
 const char* dlbchem_last_error(const dlbchem_ctx* ctx);
 
-/* Release ctx and its device memory (synchronises its last stream). NULL ok. */
+/* Release ctx and its device memory (synchronises its last stream). NULL ok.
+ * (Bookkeeping of the library; the paper has no counterpart.) */
 void dlbchem_destroy(dlbchem_ctx* ctx);
 
 /*

@@ -1,9 +1,10 @@
 // The learned cost predictor / surrogate network: a multilayer perceptron
 // n_in -> 256 -> 256 -> 256 -> n_out with SiLU, trained and run on the GPU by
-// the kernels below. Every contraction runs on the tensor cores in BF16 with
-// FP32 accumulation (mma.sync m16n8k16; FP32 master weights and activations
-// are rounded to BF16 when a tile is staged in shared memory); bias, SiLU,
-// the MSE gradient, bias gradients and Adam are FP32 element kernels.
+// the kernels below. Every contraction runs on the fifth-generation tensor
+// cores (tcgen05.mma, kind::f16) in BF16 with the FP32 accumulator in tensor
+// memory (FP32 master weights and activations are rounded to BF16 when a tile
+// is staged in shared memory); bias, SiLU, the MSE gradient, bias gradients
+// and Adam are FP32 element kernels.
 //
 // Inputs of the network for one cell: x = [T/1000, ln p, Y_1..Y_nsp, ln dt];
 // outputs: [ln(attempted steps), dT, dY_1..dY_nsp]. Both are normalised by
@@ -23,99 +24,141 @@
 
 namespace dlb {
 
-constexpr int kBM = 64, kBN = 64, kBK = 32;
-
 __device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
 __device__ __forceinline__ float dsilu_f(float z) {
   const float s = 1.0f / (1.0f + __expf(-z));
   return s * (1.0f + z * (1.0f - s));
 }
 
-__device__ __forceinline__ uint32_t pack2(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
 // C[M x N] = op(A)[M x K] op(B)[K x N] (+ bias[n]); optional pre-activation
 // copy Z and SiLU. A: TA ? A[k*lda + m] : A[m*lda + k]; B: TB ? B[n*ldb + k]
-// : B[k*ldb + n]. 64x64 block tile, 4 warps of 32x32, k-tile 32.
+// : B[k*ldb + n]. On the fifth-generation tensor cores: BF16 operands (FP32
+// rounded while staged) in shared memory in the canonical K-major layout
+// without swizzle (8 x 8 core matrices of 128 B, the K-groups of a row group
+// contiguous), FP32 accumulator in tensor memory. One CTA of 128 threads
+// computes a 128 x 64 tile: every thread stages, one thread issues the MMAs of
+// a k-tile (K = 16 each) and commits them to an mbarrier, all wait (bounded),
+// then each warp reads its 32 accumulator rows from tensor memory for the
+// epilogue. A wait that gives up sets *status, writes NaN and still frees the
+// tensor memory.
+constexpr int kTM = 128, kTN = 64, kTK = 64;
+constexpr uint32_t kTmemCols = 64;
+constexpr int kWaitLimit = 1 << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+// shared-memory matrix descriptor: start, leading-dimension byte offset (between
+// core matrices along K), stride byte offset (between 8-row groups), version 1
+// (the sm_100 family), no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) |
+         (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
+}
+
+// byte offset of (row, k) in a tile of rows x kTK BF16 values
+__device__ __forceinline__ int tile_off(int row, int k) {
+  return ((row >> 3) * (kTK / 8) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(int M, int N, int K, const float* __restrict__ A, int lda,
-                                                        const float* __restrict__ B, int ldb, float* __restrict__ C,
-                                                        int ldc, const float* __restrict__ bias, float* __restrict__ Z,
-                                                        int act) {
-  __shared__ __align__(16) __nv_bfloat16 sA[kBM][kBK + 8];   // (m, k)
-  __shared__ __align__(16) __nv_bfloat16 sB[kBN][kBK + 8];   // (n, k)
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int g = lane >> 2, t = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
-  for (int k0 = 0; k0 < K; k0 += kBK) {
-    for (int e = threadIdx.x; e < kBM * kBK; e += 128) {
+__global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                      const float* __restrict__ B, int ldb, float* __restrict__ C,
+                                                      int ldc, const float* __restrict__ bias, float* __restrict__ Z,
+                                                      int act, int* __restrict__ status) {
+  __shared__ __align__(1024) unsigned char sop[(kTM + kTN) * kTK * 2];
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ uint32_t tmem_slot;
+  unsigned char* sA = sop;
+  unsigned char* sB = sop + kTM * kTK * 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  // kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, N and M
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kTN >> 3) << 17) | (uint32_t(kTM >> 4) << 24);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int k0 = 0; k0 < K && ok; k0 += kTK) {
+    // stage the k-tile (zero outside the matrices)
+    for (int e = tid; e < kTM * kTK; e += 128) {
       int mm, kk;
-      if (TA) { kk = e / kBM; mm = e % kBM; } else { mm = e / kBK; kk = e % kBK; }
+      if (TA) { kk = e / kTM; mm = e % kTM; } else { mm = e / kTK; kk = e % kTK; }
       const int gm = m0 + mm, gk = k0 + kk;
       float v = 0.0f;
       if (gm < M && gk < K) v = TA ? A[int64_t(gk) * lda + gm] : A[int64_t(gm) * lda + gk];
-      sA[mm][kk] = __float2bfloat16_rn(v);
+      *reinterpret_cast<__nv_bfloat16*>(sA + tile_off(mm, kk)) = __float2bfloat16_rn(v);
     }
-    for (int e = threadIdx.x; e < kBN * kBK; e += 128) {
+    for (int e = tid; e < kTN * kTK; e += 128) {
       int nn, kk;
-      if (TB) { nn = e / kBK; kk = e % kBK; } else { kk = e / kBN; nn = e % kBN; }
+      if (TB) { nn = e / kTK; kk = e % kTK; } else { kk = e / kTN; nn = e % kTN; }
       const int gn = n0 + nn, gk = k0 + kk;
       float v = 0.0f;
       if (gn < N && gk < K) v = TB ? B[int64_t(gn) * ldb + gk] : B[int64_t(gk) * ldb + gn];
-      sB[nn][kk] = __float2bfloat16_rn(v);
+      *reinterpret_cast<__nv_bfloat16*>(sB + tile_off(nn, kk)) = __float2bfloat16_rn(v);
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy stores -> tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
 #pragma unroll
-    for (int kk = 0; kk < kBK; kk += 16) {
-      uint32_t a[2][4], b[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + 16 * i + g;
-        a[i][0] = pack2(&sA[r][kk + 2 * t]);
-        a[i][1] = pack2(&sA[r + 8][kk + 2 * t]);
-        a[i][2] = pack2(&sA[r][kk + 2 * t + 8]);
-        a[i][3] = pack2(&sA[r + 8][kk + 2 * t + 8]);
+      for (int kk = 0; kk < kTK / 16; ++kk) {
+        const uint64_t ad = umma_desc(smem_u32(sA) + kk * 256, 128, (kTK / 8) * 128);
+        const uint64_t bd = umma_desc(smem_u32(sB) + kk * 256, 128, (kTK / 8) * 128);
+        const uint32_t acc = (k0 > 0 || kk > 0) ? 1u : 0u;
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn + 8 * j + g;
-        b[j][0] = pack2(&sB[c][kk + 2 * t]);
-        b[j][1] = pack2(&sB[c][kk + 2 * t + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-              "{%0,%1,%2,%3};"
-              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar))
+                   : "memory");
     }
-    __syncthreads();
+    // every thread waits for this k-tile's MMAs before the tile is overwritten (bounded)
+    uint32_t done = 0;
+    for (int it = 0; it < kWaitLimit && !done; ++it)
+      asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                   : "=r"(done) : "r"(smem_u32(&mbar)), "r"(phase) : "memory");
+    phase ^= 1u;
+    ok = __syncthreads_and(done != 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
+  if (!ok && tid == 0 && status) atomicExch(status, 1);
+  // epilogue: warp w holds rows 32w .. 32w + 31 of the tile, 16 columns per load
+  const int gm = m0 + 32 * warp + lane;
+  for (int c0 = 0; c0 < kTN; c0 += 16) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(tmem + (uint32_t(32 * warp) << 16) + uint32_t(c0)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (gm < M) {
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int gm = m0 + wm + 16 * i + g + (r >= 2 ? 8 : 0);
-        const int gn = n0 + wn + 8 * j + 2 * t + (r & 1);
-        if (gm < M && gn < N) {
-          float v = acc[i][j][r] + (bias ? bias[gn] : 0.0f);
+      for (int j = 0; j < 16; ++j) {
+        const int gn = n0 + c0 + j;
+        if (gn < N) {
+          float v = ok ? __uint_as_float(r[j]) + (bias ? bias[gn] : 0.0f) : __int_as_float(0x7fc00000);
           if (Z) Z[int64_t(gm) * ldc + gn] = v;
           if (act) v = silu_f(v);
           C[int64_t(gm) * ldc + gn] = v;
         }
       }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
 // dZ = dH * silu'(Z), in place on dH.
@@ -197,6 +240,7 @@ struct dlbchem_mlp {
   float* d_v = nullptr;
   float* d_grad = nullptr;
   float* d_norm = nullptr;     // mu_x, isd_x, mu_y, sd_y
+  int* d_status = nullptr;     // set to 1 by a GEMM whose tensor-core wait gave up
   int adam_t = 0;
   // activations for the largest batch seen
   int64_t cap = 0;
@@ -236,12 +280,13 @@ std::vector<LayerOff> layers_of(const dlbchem_mlp* m) {
 }
 
 cudaError_t gemm(bool ta, bool tb, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
-                 int ldc, const float* bias, float* Z, int act, cudaStream_t s) {
-  dim3 grid((N + dlb::kBN - 1) / dlb::kBN, (M + dlb::kBM - 1) / dlb::kBM);
-  if (!ta && !tb) dlb::gemm_bf16_kernel<false, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, act);
-  else if (ta && !tb) dlb::gemm_bf16_kernel<true, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, act);
-  else if (!ta && tb) dlb::gemm_bf16_kernel<false, true><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, act);
-  else dlb::gemm_bf16_kernel<true, true><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, act);
+                 int ldc, const float* bias, float* Z, int act, int* status, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;   // nothing to contract
+  dim3 grid((N + dlb::kTN - 1) / dlb::kTN, (M + dlb::kTM - 1) / dlb::kTM);
+  if (!ta && !tb) dlb::gemm_tc_kernel<false, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, act, status);
+  else if (ta && !tb) dlb::gemm_tc_kernel<true, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, act, status);
+  else if (!ta && tb) dlb::gemm_tc_kernel<false, true><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, act, status);
+  else dlb::gemm_tc_kernel<true, true><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Z, act, status);
   return cudaGetLastError();
 }
 
@@ -275,7 +320,7 @@ cudaError_t forward(dlbchem_mlp* m, int64_t B, const float* X, float* out, bool 
     float* dst = last ? out : Hs + int64_t(li) * B * H;
     float* z = (!last && keep) ? Zs + int64_t(li) * B * H : nullptr;
     e = gemm(false, false, int(B), L[li].fo, L[li].fi, in, L[li].fi, m->d_params + L[li].w, L[li].fo, dst, L[li].fo,
-             m->d_params + L[li].b, z, last ? 0 : 1, s);
+             m->d_params + L[li].b, z, last ? 0 : 1, m->d_status, s);
     in = dst;
   }
   return e;
@@ -295,11 +340,13 @@ int dlbchem_mlp_create(int n_in, int n_hidden, int n_out, dlbchem_mlp** out) {
   const size_t bytes = size_t(m->nparams) * 4;
   if (cudaMalloc(&m->d_params, bytes) != cudaSuccess || cudaMalloc(&m->d_m, bytes) != cudaSuccess ||
       cudaMalloc(&m->d_v, bytes) != cudaSuccess || cudaMalloc(&m->d_grad, bytes) != cudaSuccess ||
-      cudaMalloc(&m->d_norm, size_t(2 * (n_in + n_out)) * 4) != cudaSuccess) {
+      cudaMalloc(&m->d_norm, size_t(2 * (n_in + n_out)) * 4) != cudaSuccess ||
+      cudaMalloc(&m->d_status, sizeof(int)) != cudaSuccess) {
     dlbchem_mlp_destroy(m);
     return DLBCHEM_OOM;
   }
   cudaMemset(m->d_params, 0, bytes);
+  cudaMemset(m->d_status, 0, sizeof(int));
   cudaMemset(m->d_m, 0, bytes);
   cudaMemset(m->d_v, 0, bytes);
   std::vector<float> norm(2 * (n_in + n_out), 0.0f);
@@ -382,7 +429,7 @@ int dlbchem_mlp_grad(dlbchem_mlp* m, int64_t B, const float* X, const float* Y, 
     const float* hin = li == 0 ? X : Hs + int64_t(li - 1) * B * H;
     // dW = hin^T dZ  (M = fan_in, N = fan_out, K = B)
     e = gemm(true, false, L[li].fi, L[li].fo, int(B), hin, L[li].fi, dcur, L[li].fo, g + L[li].w, L[li].fo, nullptr,
-             nullptr, 0, s);
+             nullptr, 0, m->d_status, s);
     if (e == cudaSuccess) {
       dlb::bias_grad_kernel<<<(L[li].fo + 127) / 128, 128, 0, s>>>(int(B), L[li].fo, dcur, g + L[li].b);
       e = cudaGetLastError();
@@ -390,7 +437,7 @@ int dlbchem_mlp_grad(dlbchem_mlp* m, int64_t B, const float* X, const float* Y, 
     if (li == 0 || e != cudaSuccess) break;
     // dH_prev = dZ W^T  (M = B, N = fan_in, K = fan_out), then through SiLU
     e = gemm(false, true, int(B), L[li].fi, L[li].fo, dcur, L[li].fo, m->d_params + L[li].w, L[li].fo, dnext,
-             L[li].fi, nullptr, nullptr, 0, s);
+             L[li].fi, nullptr, nullptr, 0, m->d_status, s);
     if (e == cudaSuccess) {
       const int64_t n = B * H;
       dlb::silu_back_kernel<<<unsigned(std::min<int64_t>((n + 255) / 256, 4096)), 256, 0, s>>>(
@@ -427,6 +474,7 @@ void dlbchem_mlp_destroy(dlbchem_mlp* m) {
   cudaDeviceSynchronize();
   for (float* p : {m->d_params, m->d_m, m->d_v, m->d_grad, m->d_norm, m->d_act})
     if (p) cudaFree(p);
+  if (m->d_status) cudaFree(m->d_status);
   delete m;
 }
 

@@ -34,9 +34,14 @@ def _per_tensor(theta, shapes):
     return out
 
 
-def test_network_gradients_match_fp64_oracle():
+@pytest.mark.parametrize("B", [96, 1000])
+def test_network_gradients_match_fp64_oracle(B):
+    """Forward and backward on the tensor cores (tcgen05, BF16, FP32
+    accumulator in tensor memory) against the FP64 oracle network: B = 96 is a
+    partial 128-row tile, B = 1000 spans eight row tiles and, for the weight
+    gradients, sixteen accumulated k-tiles."""
     d = lib()
-    n_in, n_out, B = 13, 12, 96
+    n_in, n_out = 13, 12
     shapes = omlp.layer_shapes(n_in, 256, n_out)
     rng = np.random.default_rng(3)
     theta = omlp.init_params(n_in, 256, n_out, seed=5) + rng.normal(0, 0.02, omlp.n_params(n_in, 256, n_out))

@@ -46,9 +46,11 @@ METRIC = "chemistry cells/s per dt at stated T/Y error vs FP64 oracle; frac of F
 # FMA lanes per clock per SM x 2 flop (= the 1.25 TFLOP/s nominal figure).
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP64 integrator launch
-# from ncu, scaled to the benchmark's launch; None whenever the kernel has
+# from ncu per integrated cell (3,852,544 B read, 0 written, 912 cells
+# integrated on the 8,192-cell bimodal field with bucket mapping), scaled by
+# the cells the benchmark's launch integrates; None whenever the kernel has
 # changed since the capture.
-INTEGRATOR_TRAFFIC_BYTES = None
+INTEGRATOR_TRAFFIC_BYTES_PER_CELL = 3852544 / 912
 N_F = 3   # function evaluations per Rosenbrock step (stage 4 reuses stage 3's)
 PAPER_CONTEXT = ("paper (DLBFoam, arXiv 2011.07978): load balancing + reference mapping speed the CPU "
                  "chemistry step up by about 10x (Spray A, 256 MPI ranks on 2x64-core AMD EPYC Rome nodes, "
@@ -249,15 +251,23 @@ def mlp_forward_rate(dlbchem, dev, stream, n):
     net.set_params((torch.randn(net.nparams, generator=g) * 0.05).to(dev))
     X = torch.randn(n, 13, generator=g).to(dev)
     out = torch.empty(n, 12, dtype=torch.float32, device=dev)
-    for _ in range(2):
-        net.forward(X, out, stream)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(5):
-        net.forward(X, out, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / 5
+
+    def timed(reps=5):
+        for _ in range(2):
+            net.forward(X, out, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            net.forward(X, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    fused = net.fused
+    ms = timed()
+    net.set_fused(False)
+    ms_layered = timed()
+    net.set_fused(True)
     flops = 2.0 * n * (13 * 256 + 2 * 256 * 256 + 256 * 12)
     peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak = json.load(open(peaks))["bf16_tflops"] if os.path.exists(peaks) else 1900.0
@@ -265,7 +275,10 @@ def mlp_forward_rate(dlbchem, dev, stream, n):
     net.close()
     return {"cells": n, "ms": ms, "achieved_tflops": tf, "peak_bf16_tflops": peak, "frac": tf / peak,
             "peak_source": "MEASURED_PEAKS.json bf16_tflops" if os.path.exists(peaks) else "fallback 1.9 PFLOP/s",
-            "kernel": "gemm_tc_kernel (tcgen05.mma kind::f16, TMEM accumulator)"}
+            "kernel": ("mlp_fused_forward_kernel (whole network per 128 rows; tcgen05.mma kind::f16, TMEM "
+                       "accumulator, weights by cp.async.bulk)") if fused else "gemm_tc_kernel per layer",
+            "layered_ms": ms_layered,
+            "layered_kernel": "gemm_tc_kernel per layer (FP32 activations in HBM)"}
 
 
 def fp64_probe(dlbchem, dev, stream):
@@ -314,9 +327,20 @@ def main():
                     help="warps per cell (0 = the library's automatic choice)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="mixed: FP32 LU of the iteration matrix with FP64 refinement")
+    ap.add_argument("--mlp-only", type=int, default=0, metavar="CELLS",
+                    help="only time the network's forward pass on CELLS rows and print its JSON")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.mlp_only:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_2011_07978_gb300 import dlbchem
+        dev = torch.device("cuda:0")
+        torch.cuda.set_device(dev)
+        print(json.dumps(mlp_forward_rate(dlbchem, dev, torch.cuda.current_stream(dev), args.mlp_only)))
+        return 0
     args.warmup = max(args.warmup, 3)
 
     import torch
@@ -419,7 +443,10 @@ def main():
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": INTEGRATOR_TRAFFIC_BYTES if args.precision == "fp64" else None,
+                     "traffic": (INTEGRATOR_TRAFFIC_BYTES_PER_CELL * stats["integrated"]
+                                 if args.precision == "fp64" and INTEGRATOR_TRAFFIC_BYTES_PER_CELL else None),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per integrated cell, "
+                                       "8,192-cell capture, scaled by the cells integrated per launch",
                      "kernel": "rosenbrock_kernel", "flops_per_step": fstep,
                      "flops_formula": "(2/3)N^3 + 8N^2 + 3(25R + 15Nsp) + 90R + 3N^2, N = Nsp + 1",
                      "transcendentals_per_step": transcendentals_per_step(mech),

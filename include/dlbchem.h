@@ -249,7 +249,14 @@ void dlbchem_batch_destroy(dlbchem_batch* b);
  *   parameter vector [W1 b1 W2 b2 W3 b3 W4 b4] (W row-major [fan_in][fan_out])
  *   from / to DEVICE memory and reset the optimiser; set_norm takes HOST
  *   arrays mu_x, sd_x [n_in] and mu_y, sd_y [n_out].
- *   forward: X [batch][n_in] -> out [batch][n_out], normalised, device.
+ *   forward: X [batch][n_in] -> out [batch][n_out], normalised, device. Where
+ *   the hidden width is a multiple of 64 up to 256 and n_in, n_out <= 256 it
+ *   runs the whole network in one kernel per 128 rows (activations stay in
+ *   shared memory, weights stream in as packed BF16 tiles), else layer by
+ *   layer; both give the same BF16/FP32 arithmetic. set_fused(m, 0) forces
+ *   the layer-by-layer forward, set_fused(m, 1) restores the default
+ *   (BAD_ARG otherwise); fused(m) is 1 when forward takes the whole-network
+ *   kernel, 0 when not, -1 for NULL.
  *   grad: MSE loss and its gradient (grad device [nparams] or NULL for the
  *   internal buffer; loss device float or NULL). adam: one Adam step
  *   (Kingma & Ba 2015) with the given or the internal gradient.
@@ -270,6 +277,8 @@ int dlbchem_mlp_grad(dlbchem_mlp* m, int64_t batch, const float* X, const float*
 int dlbchem_mlp_adam(dlbchem_mlp* m, const float* grad, float lr, void* cuda_stream);
 int dlbchem_mlp_train_step(dlbchem_mlp* m, int64_t batch, const float* X, const float* Y, float lr, float* loss,
                            void* cuda_stream);
+int dlbchem_mlp_set_fused(dlbchem_mlp* m, int enable);
+int dlbchem_mlp_fused(const dlbchem_mlp* m);
 const char* dlbchem_mlp_last_error(const dlbchem_mlp* m);
 void dlbchem_mlp_destroy(dlbchem_mlp* m);
 int dlbchem_attach_mlp(dlbchem_ctx* ctx, dlbchem_mlp* m);

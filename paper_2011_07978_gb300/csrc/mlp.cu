@@ -12,6 +12,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -24,10 +25,23 @@
 
 namespace dlb {
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+// SiLU z sigma(z) through sigma(z) = (1 + tanh(z/2)) / 2: one hardware tanh
+// (tanh.approx.f32, relative error about 2^-11, below the BF16 rounding the
+// activations get next) instead of an exponential and a reciprocal, which
+// matters because the fused forward's epilogue is bound by that unit.
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float silu_f(float z) {
+  const float h = 0.5f * z;
+  return fmaf(h, tanh_fast(h), h);
+}
+// d/dz z sigma(z) = sigma (1 + z (1 - sigma)), with the same sigma
 __device__ __forceinline__ float dsilu_f(float z) {
-  const float s = 1.0f / (1.0f + __expf(-z));
-  return s * (1.0f + z * (1.0f - s));
+  const float s = fmaf(0.5f, tanh_fast(0.5f * z), 0.5f);
+  return s * fmaf(z, 1.0f - s, 1.0f);
 }
 
 // C[M x N] = op(A)[M x K] op(B)[K x N] (+ bias[n]); optional pre-activation
@@ -161,6 +175,243 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, const
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Whole-network forward pass for inference. Persistent CTAs take 128-row
+// tiles in turn. The activation tile never leaves shared memory: it is the A
+// operand of the next layer (BF16, K-major core matrices), rewritten in place
+// by each layer's epilogue; the accumulator (up to 256 FP32 columns) lives in
+// tensor memory. The weights stream through two shared-memory k-tiles of 32,
+// filled by bulk copies (cp.async.bulk, completed on an mbarrier) from a BF16
+// copy of the weights packed in exactly that layout: while the tensor cores
+// work on one k-tile the next one is in flight, across layer and tile
+// boundaries. Only the network input and output cross HBM. Arithmetic per
+// element is that of the layered path above: BF16 operands, FP32
+// accumulation, FP32 bias and SiLU, activations rounded to BF16 as the next
+// layer's operand. Supported shapes: hidden widths multiples of 64 up to 256,
+// n_in and n_out up to 256, at most kFusedMaxLayers layers.
+// ---------------------------------------------------------------------------
+constexpr int kFusedMaxLayers = 8;
+constexpr int kFusedMaxN = 256;
+constexpr int kFK = 32;                                       // k-tile of the weight stream
+constexpr int kFusedSmemH = kTM * kFusedMaxN * 2;             // 64 KB activation tile
+constexpr int kFusedSmemW = kFusedMaxN * kFK * 2;             // 16 KB per weight buffer
+constexpr int kFusedSmem = kFusedSmemH + 2 * kFusedSmemW + kFusedMaxN * 4 + 1024;   // + bias + alignment
+
+struct FusedNet {
+  int nl;                                       // layers
+  int fi[kFusedMaxLayers], fo[kFusedMaxLayers];
+  int kp[kFusedMaxLayers], np[kFusedMaxLayers];  // fan-in padded to kFK, fan-out padded to 16
+  int64_t woff[kFusedMaxLayers];                // byte offset of the layer's packed weights
+  const float* bias[kFusedMaxLayers];
+  const unsigned char* wpk;
+};
+
+// byte offset of (row, k) in a tile of rows x kext BF16 values (kext a multiple of 8)
+__device__ __forceinline__ int core_off(int row, int k, int kext) {
+  return ((row >> 3) * (kext >> 3) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// Layer weights W [fi][fo] (FP32, row-major) as BF16 k-tiles for the fused
+// pass: k-tile t holds rows n < np and k in [kFK t, kFK t + kFK) of W^T in
+// core matrices (the B operand, K-major), zero outside W.
+__global__ void pack_weights_kernel(int fi, int fo, int kp, int np, const float* __restrict__ W,
+                                    unsigned char* __restrict__ dst) {
+  const int64_t total = int64_t(kp) * np;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int n = int(e % np), k = int(e / np);
+    const float v = (n < fo && k < fi) ? W[int64_t(k) * fo + n] : 0.0f;
+    const int kt = k / kFK;
+    *reinterpret_cast<__nv_bfloat16*>(dst + int64_t(kt) * np * kFK * 2 + core_off(n, k - kt * kFK, kFK)) =
+        __float2bfloat16_rn(v);
+  }
+}
+
+// bounded mbarrier wait on the phase of the given parity; true once it completed
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < kWaitLimit && !done; ++it)
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);   // a in the low half (lower k)
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__global__ void __launch_bounds__(128) mlp_fused_forward_kernel(int64_t B, const float* __restrict__ X,
+                                                                float* __restrict__ out, const FusedNet net,
+                                                                int* __restrict__ status) {
+  extern __shared__ unsigned char fused_smem_raw[];
+  unsigned char* sH =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(fused_smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sW = sH + kFusedSmemH;                                   // two buffers of kFusedSmemW
+  float* sbias = reinterpret_cast<float*>(sW + 2 * kFusedSmemW);
+  __shared__ __align__(8) unsigned long long full[2], empty[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (B + kTM - 1) / kTM;
+  // weight k-tiles per pass over the network, and in all of this CTA's tiles
+  int per_pass = 0;
+  for (int l = 0; l < net.nl; ++l) per_pass += net.kp[l] / kFK;
+  const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t total = my_tiles * per_pass;
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[b])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(uint32_t(kFusedMaxN)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  // thread 0: copy of weight k-tile g of the stream into buffer g % 2
+  int64_t issued = 0;
+  auto issue_copy = [&](int64_t g) {
+    int loc = int(g % per_pass), l = 0;
+    while (loc >= net.kp[l] / kFK) { loc -= net.kp[l] / kFK; ++l; }
+    const uint32_t bytes = uint32_t(net.np[l]) * kFK * 2;
+    const uint32_t bar = smem_u32(&full[g & 1]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(sW + (g & 1) * kFusedSmemW)),
+                 "l"(net.wpk + net.woff[l] + size_t(loc) * bytes), "r"(bytes), "r"(bar)
+                 : "memory");
+    issued = g + 1;
+  };
+  bool ok = true;
+  int64_t g = 0;           // next k-tile of the stream
+  int64_t committed = 0;   // k-tiles whose MMAs were issued (thread 0)
+  if (tid == 0 && total > 0) issue_copy(0);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * kTM;
+    const int row = 32 * warp + lane;
+    const int64_t gr = r0 + row;
+    // input tile: each thread stages its row, eight columns per 16-byte
+    // store, zero beyond n_in and beyond the batch
+    {
+      const int kp = net.kp[0], fi = net.fi[0];
+      const float* x = X + (r0 + tid) * fi;
+      const bool in = r0 + tid < B;
+      for (int k0 = 0; k0 < kp; k0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = (in && k0 + j < fi) ? x[k0 + j] : 0.0f;
+        *reinterpret_cast<uint4*>(sH + core_off(tid, k0, kp)) = make_uint4(
+            pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    for (int l = 0; l < net.nl; ++l) {
+      const int kp = net.kp[l], np = net.np[l], fo = net.fo[l];
+      if (tid == 0 && ok) {
+        const uint32_t idesc =
+            (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(np >> 3) << 17) | (uint32_t(kTM >> 4) << 24);
+        for (int kt = 0; kt < kp / kFK; ++kt, ++g) {
+          if (!mbar_wait(smem_u32(&full[g & 1]), uint32_t(g >> 1) & 1u)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+          for (int kk = 0; kk < kFK / 16; ++kk) {
+            const uint64_t ad = umma_desc(smem_u32(sH) + uint32_t(kt * (kFK / 8) + kk * 2) * 128u, 128,
+                                          uint32_t(kp) * 16u);
+            const uint64_t bd = umma_desc(smem_u32(sW + (g & 1) * kFusedSmemW) + uint32_t(kk) * 256u, 128,
+                                          (kFK / 8) * 128);
+            const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                         "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&empty[g & 1]))
+                       : "memory");
+          committed = g + 1;
+          // the other buffer is free once the previous k-tile's MMAs completed:
+          // refill it with the next k-tile while this one's MMAs run
+          if (g >= 1 && !mbar_wait(smem_u32(&empty[(g - 1) & 1]), uint32_t((g - 1) >> 1) & 1u)) { ok = false; break; }
+          if (g + 1 < total) issue_copy(g + 1);
+        }
+        // the layer's accumulator is complete when its last k-tile's MMAs are
+        if (ok && !mbar_wait(smem_u32(&empty[(g - 1) & 1]), uint32_t((g - 1) >> 1) & 1u)) ok = false;
+      }
+      const bool last = l + 1 == net.nl;
+      for (int n = tid; n < np; n += 128) sbias[n] = n < fo ? net.bias[l][n] : 0.0f;
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      ok = __syncthreads_and(ok);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int kpn = last ? 0 : net.kp[l + 1];
+      for (int c0 = 0; c0 < np; c0 += 32) {
+        const int nc = np - c0 >= 32 ? 32 : 16;
+        uint32_t r[32];
+        const uint32_t ta = tmem + (uint32_t(32 * warp) << 16) + uint32_t(c0);
+        tmem_ld16(ta, r);
+        if (nc == 32) tmem_ld16(ta + 16u, r + 16);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (last) {
+          if (gr < B) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int n = c0 + j;
+              if (j < nc && n < fo) out[gr * fo + n] = ok ? __uint_as_float(r[j]) + sbias[n] : __int_as_float(0x7fc00000);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            if (8 * h < nc) {
+              float v[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int n = c0 + 8 * h + j;
+                v[j] = n < fo ? silu_f(__uint_as_float(r[8 * h + j]) + sbias[n]) : 0.0f;
+              }
+              *reinterpret_cast<uint4*>(sH + core_off(row, c0 + 8 * h, kpn)) = make_uint4(
+                  pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+            }
+          }
+        }
+      }
+      if (!last)
+        for (int k0 = np; k0 < kpn; k0 += 8)
+          *reinterpret_cast<uint4*>(sH + core_off(row, k0, kpn)) = make_uint4(0, 0, 0, 0);
+      // the rewritten tile is the next layer's operand; tensor memory and the
+      // bias are free for the next layer
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+  }
+  if (tid == 0 && !ok) {
+    if (status) atomicExch(status, 1);
+    // copies may still be landing in shared memory and MMAs still running:
+    // wait for the last of each (bounded) before the tensor memory is freed
+    if (issued > 0) mbar_wait(smem_u32(&full[(issued - 1) & 1]), uint32_t((issued - 1) >> 1) & 1u);
+    if (committed > 0) mbar_wait(smem_u32(&empty[(committed - 1) & 1]), uint32_t((committed - 1) >> 1) & 1u);
+  }
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(kFusedMaxN)) : "memory");
+}
+
 // dZ = dH * silu'(Z), in place on dH.
 __global__ void silu_back_kernel(int64_t n, float* __restrict__ dH, const float* __restrict__ Z) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
@@ -242,6 +493,14 @@ struct dlbchem_mlp {
   float* d_norm = nullptr;     // mu_x, isd_x, mu_y, sd_y
   int* d_status = nullptr;     // set to 1 by a GEMM whose tensor-core wait gave up
   int adam_t = 0;
+  // fused forward (inference): BF16 weights packed as the fused kernel's
+  // k-tiles, repacked after every parameter change
+  bool fused_ok = false;       // the shape is one the fused kernel takes
+  bool fused_on = true;        // dlbchem_mlp_set_fused
+  bool packed_dirty = true;
+  unsigned char* d_wpk = nullptr;
+  dlb::FusedNet fnet{};
+  int num_sms = 0;
   // activations for the largest batch seen
   int64_t cap = 0;
   float* d_act = nullptr;
@@ -307,8 +566,64 @@ int ensure_act(dlbchem_mlp* m, int64_t batch) {
   return DLBCHEM_OK;
 }
 
+// Fused-forward tables of the network (weights still to pack); false if the
+// shape is not one the fused kernel takes.
+bool plan_fused(dlbchem_mlp* m) {
+  const auto L = layers_of(m);
+  if (int(L.size()) > dlb::kFusedMaxLayers) return false;
+  if (m->n_hidden % 64 != 0 || m->n_hidden > dlb::kFusedMaxN || m->n_in > dlb::kFusedMaxN ||
+      m->n_out > dlb::kFusedMaxN)
+    return false;
+  dlb::FusedNet& f = m->fnet;
+  f.nl = int(L.size());
+  int64_t off = 0;
+  for (int l = 0; l < f.nl; ++l) {
+    f.fi[l] = L[l].fi;
+    f.fo[l] = L[l].fo;
+    f.kp[l] = (L[l].fi + dlb::kFK - 1) / dlb::kFK * dlb::kFK;
+    f.np[l] = (L[l].fo + 15) / 16 * 16;
+    f.woff[l] = off;
+    off += int64_t(f.kp[l]) * f.np[l] * 2;
+  }
+  if (cudaMalloc(&m->d_wpk, size_t(off)) != cudaSuccess) {
+    m->d_wpk = nullptr;
+    return false;
+  }
+  f.wpk = m->d_wpk;
+  for (int l = 0; l < f.nl; ++l) f.bias[l] = m->d_params + L[l].b;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return false;
+  return cudaFuncSetAttribute(dlb::mlp_fused_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              dlb::kFusedSmem) == cudaSuccess;
+}
+
+cudaError_t forward_fused(dlbchem_mlp* m, int64_t B, const float* X, float* out, cudaStream_t s) {
+  const auto L = layers_of(m);
+  cudaError_t e = cudaSuccess;
+  if (m->packed_dirty) {
+    for (int l = 0; l < m->fnet.nl && e == cudaSuccess; ++l) {
+      const int64_t tot = int64_t(m->fnet.kp[l]) * m->fnet.np[l];
+      dlb::pack_weights_kernel<<<unsigned(std::min<int64_t>((tot + 255) / 256, 1024)), 256, 0, s>>>(
+          L[l].fi, L[l].fo, m->fnet.kp[l], m->fnet.np[l], m->d_params + L[l].w, m->d_wpk + m->fnet.woff[l]);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+    m->packed_dirty = false;
+  }
+  // persistent: two CTAs per SM (shared memory and tensor memory allow two)
+  const int64_t tiles = (B + dlb::kTM - 1) / dlb::kTM;
+  const int64_t grid = std::min<int64_t>(tiles, 2 * int64_t(m->num_sms));
+  dlb::mlp_fused_forward_kernel<<<unsigned(grid), 128, dlb::kFusedSmem, s>>>(B, X, out, m->fnet, m->d_status);
+  return cudaGetLastError();
+}
+
 // Forward; with keep the pre-activations are stored for the backward pass.
+// Without keep (inference) the fused whole-network kernel runs where the
+// shape allows it.
 cudaError_t forward(dlbchem_mlp* m, int64_t B, const float* X, float* out, bool keep, cudaStream_t s) {
+  if (!keep && m->fused_ok && m->fused_on) return forward_fused(m, B, X, out, s);
   const auto L = layers_of(m);
   const int64_t H = m->n_hidden;
   float* Zs = m->d_act;                                  // n_layers x [B x H]
@@ -353,6 +668,7 @@ int dlbchem_mlp_create(int n_in, int n_hidden, int n_out, dlbchem_mlp** out) {
   for (int i = 0; i < n_in; ++i) norm[n_in + i] = 1.0f;
   for (int i = 0; i < n_out; ++i) norm[2 * n_in + n_out + i] = 1.0f;
   cudaMemcpy(m->d_norm, norm.data(), norm.size() * 4, cudaMemcpyHostToDevice);
+  m->fused_ok = plan_fused(m);
   *out = m;
   return DLBCHEM_OK;
 }
@@ -362,6 +678,7 @@ int64_t dlbchem_mlp_nparams(const dlbchem_mlp* m) { return m ? m->nparams : -1; 
 int dlbchem_mlp_set_params(dlbchem_mlp* m, const float* params, void* stream) {
   if (!m || !params) return DLBCHEM_BAD_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  m->packed_dirty = true;
   cudaError_t e = cudaMemcpyAsync(m->d_params, params, size_t(m->nparams) * 4, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->d_m, 0, size_t(m->nparams) * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->d_v, 0, size_t(m->nparams) * 4, s);
@@ -452,6 +769,7 @@ int dlbchem_mlp_grad(dlbchem_mlp* m, int64_t B, const float* X, const float* Y, 
 int dlbchem_mlp_adam(dlbchem_mlp* m, const float* grad, float lr, void* stream) {
   if (!m || !(lr > 0)) return DLBCHEM_BAD_ARG;
   m->adam_t += 1;
+  m->packed_dirty = true;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.0f - std::pow(b1, float(m->adam_t)), c2 = 1.0f - std::pow(b2, float(m->adam_t));
   dlb::adam_kernel<<<unsigned(std::min<int64_t>((m->nparams + 255) / 256, 2048)), 256, 0,
@@ -467,6 +785,14 @@ int dlbchem_mlp_train_step(dlbchem_mlp* m, int64_t B, const float* X, const floa
   return rc == DLBCHEM_OK ? dlbchem_mlp_adam(m, nullptr, lr, stream) : rc;
 }
 
+int dlbchem_mlp_set_fused(dlbchem_mlp* m, int enable) {
+  if (!m || (enable != 0 && enable != 1)) return DLBCHEM_BAD_ARG;
+  m->fused_on = enable != 0;
+  return DLBCHEM_OK;
+}
+
+int dlbchem_mlp_fused(const dlbchem_mlp* m) { return m ? int(m->fused_ok && m->fused_on) : -1; }
+
 const char* dlbchem_mlp_last_error(const dlbchem_mlp* m) { return m ? m->err.c_str() : ""; }
 
 void dlbchem_mlp_destroy(dlbchem_mlp* m) {
@@ -475,6 +801,7 @@ void dlbchem_mlp_destroy(dlbchem_mlp* m) {
   for (float* p : {m->d_params, m->d_m, m->d_v, m->d_grad, m->d_norm, m->d_act})
     if (p) cudaFree(p);
   if (m->d_status) cudaFree(m->d_status);
+  if (m->d_wpk) cudaFree(m->d_wpk);
   delete m;
 }
 

@@ -71,6 +71,8 @@ def load() -> ctypes.CDLL:
     lib.dlbchem_mlp_grad.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
     lib.dlbchem_mlp_adam.argtypes = [_vp, _vp, ctypes.c_float, _vp]
     lib.dlbchem_mlp_train_step.argtypes = [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_float, _vp, _vp]
+    lib.dlbchem_mlp_set_fused.argtypes = [_vp, ctypes.c_int]
+    lib.dlbchem_mlp_fused.argtypes = [_vp]
     lib.dlbchem_mlp_last_error.argtypes = [_vp]
     lib.dlbchem_mlp_last_error.restype = ctypes.c_char_p
     lib.dlbchem_mlp_destroy.argtypes = [_vp]
@@ -368,6 +370,14 @@ class MLP:
     def forward(self, X, out, stream=None):
         self._check(load().dlbchem_mlp_forward(self._h, X.shape[0], _ptr(X), _ptr(out), _stream_ptr(stream)))
         return out
+
+    def set_fused(self, enable: bool):
+        """dlbchem_mlp_set_fused: whole-network forward kernel (default) or layer by layer."""
+        self._check(load().dlbchem_mlp_set_fused(self._h, 1 if enable else 0))
+
+    @property
+    def fused(self) -> bool:
+        return load().dlbchem_mlp_fused(self._h) == 1
 
     def grad(self, X, Y, grad=None, loss=None, stream=None):
         self._check(load().dlbchem_mlp_grad(self._h, X.shape[0], _ptr(X), _ptr(Y), _ptr(grad), _ptr(loss),

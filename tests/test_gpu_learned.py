@@ -2,7 +2,8 @@
 
 * The BF16 tensor-core network's loss and gradients match the FP64 CPU
   oracle network (oracle/mlp.py) per tensor within 2e-2 relative, cosine
-  >= 0.999.
+  >= 0.999; the whole-network forward kernel matches the layer-by-layer one
+  and the oracle.
 * Trained on integrator trajectories of the 10-species case, the predicted
   step counts order the queue better than index order (makespan of greedy
   scheduling on the true costs), cells that fail the gate are integrated
@@ -66,6 +67,60 @@ def test_network_gradients_match_fp64_oracle(B):
         rel = np.linalg.norm(gg - gr) / np.linalg.norm(gr)
         cos = gg @ gr / (np.linalg.norm(gg) * np.linalg.norm(gr))
         assert rel <= 2e-2 and cos >= 0.999, (rel, cos)
+
+
+@pytest.mark.parametrize("n_in,hidden,n_out,B", [(13, 256, 12, 96), (13, 256, 12, 5000), (56, 256, 55, 777),
+                                                  (13, 128, 12, 1000)])
+def test_fused_forward_matches_layered_and_oracle(n_in, hidden, n_out, B):
+    """The whole-network forward kernel (activations kept in shared memory,
+    weights streamed as packed BF16 k-tiles by bulk copy) against the
+    layer-by-layer tensor-core forward (same BF16 operands, FP32 accumulation
+    over k-tiles of 64, FP32 bias and SiLU) and against the FP64 oracle
+    network. Batches end in a partial 128-row tile except at 5000 - 4992 = 8."""
+    d = lib()
+    shapes = omlp.layer_shapes(n_in, hidden, n_out)
+    rng = np.random.default_rng(11)
+    theta = omlp.init_params(n_in, hidden, n_out, seed=7) + rng.normal(0, 0.02, omlp.n_params(n_in, hidden, n_out))
+    theta = theta.astype(np.float32).astype(np.float64)
+    X = rng.normal(size=(B, n_in)).astype(np.float32)
+    out_ref, _ = omlp.forward(theta, X.astype(np.float64), shapes)
+    net = d.MLP(n_in, hidden, n_out)
+    assert net.fused
+    net.set_params(torch.tensor(theta.astype(np.float32), device=DEV))
+    Xd = torch.tensor(X, device=DEV)
+    fused = net.forward(Xd, torch.full((B, n_out), float("nan"), dtype=torch.float32, device=DEV)).cpu().numpy()
+    net.set_fused(False)
+    assert not net.fused
+    layered = net.forward(Xd, torch.full((B, n_out), float("nan"), dtype=torch.float32, device=DEV)).cpu().numpy()
+    net.set_fused(True)
+    again = net.forward(Xd, torch.full((B, n_out), float("nan"), dtype=torch.float32, device=DEV)).cpu().numpy()
+    assert np.isfinite(fused).all() and np.isfinite(layered).all()
+    np.testing.assert_array_equal(again, fused)                       # repacked weights are reused
+    scale = np.abs(layered).max()
+    assert np.abs(fused - layered).max() <= 1e-5 * scale, np.abs(fused - layered).max() / scale
+    for o in (fused, layered):
+        assert np.linalg.norm(o - out_ref) <= 2e-2 * np.linalg.norm(out_ref)
+    # new parameters are repacked before the next fused forward
+    net.set_params(torch.tensor((theta * 0.5).astype(np.float32), device=DEV))
+    half = net.forward(Xd, torch.empty((B, n_out), dtype=torch.float32, device=DEV)).cpu().numpy()
+    out_half, _ = omlp.forward(theta * 0.5, X.astype(np.float64), shapes)
+    assert np.linalg.norm(half - out_half) <= 2e-2 * np.linalg.norm(out_half)
+    net.close()
+
+
+def test_fused_forward_declines_other_shapes():
+    """A hidden width that is not a multiple of 64 runs layer by layer."""
+    d = lib()
+    net = d.MLP(13, 96, 12)
+    assert not net.fused
+    shapes = omlp.layer_shapes(13, 96, 12)
+    theta = omlp.init_params(13, 96, 12, seed=2).astype(np.float32).astype(np.float64)
+    X = np.random.default_rng(4).normal(size=(300, 13)).astype(np.float32)
+    net.set_params(torch.tensor(theta.astype(np.float32), device=DEV))
+    out = net.forward(torch.tensor(X, device=DEV), torch.empty((300, 12), dtype=torch.float32, device=DEV)).cpu().numpy()
+    ref, _ = omlp.forward(theta, X.astype(np.float64), shapes)
+    assert np.linalg.norm(out - ref) <= 2e-2 * np.linalg.norm(ref)
+    net.close()
 
 
 def test_adam_step_matches_oracle():

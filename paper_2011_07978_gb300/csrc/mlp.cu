@@ -2,8 +2,9 @@
 // n_in -> 256 -> 256 -> 256 -> n_out with SiLU, trained and run on the GPU by
 // the kernels below. Every contraction runs on the fifth-generation tensor
 // cores (tcgen05.mma, kind::f16) in BF16 with the FP32 accumulator in tensor
-// memory (FP32 master weights and activations are rounded to BF16 when a tile
-// is staged in shared memory); bias, SiLU, the MSE gradient, bias gradients
+// memory: inference as one whole-network kernel per 128-row tile, training
+// layer by layer (FP32 master weights and activations are rounded to BF16
+// when a tile is staged in shared memory); the MSE gradient, bias gradients
 // and Adam are FP32 element kernels.
 //
 // Inputs of the network for one cell: x = [T/1000, ln p, Y_1..Y_nsp, ln dt];

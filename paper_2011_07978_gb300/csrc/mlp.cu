@@ -11,6 +11,7 @@
 // outputs: [ln(attempted steps), dT, dY_1..dY_nsp]. Both are normalised by
 // stored means and standard deviations.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,22 +27,29 @@
 
 namespace dlb {
 
-// SiLU z sigma(z) through sigma(z) = (1 + tanh(z/2)) / 2: one hardware tanh
-// (tanh.approx.f32, relative error about 2^-11, below the BF16 rounding the
-// activations get next) instead of an exponential and a reciprocal, which
-// matters because the fused forward's epilogue is bound by that unit.
-__device__ __forceinline__ float tanh_fast(float x) {
-  float y;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
+// SiLU z sigma(z) through sigma(z) = (1 + tanh(z/2)) / 2, with the hardware
+// tanh on a pair of half-precision values (tanh.approx.f16x2: one
+// special-function operation for two activations instead of an exponential
+// and a reciprocal for each; the fused forward's epilogue is bound by that
+// unit). z/2 rounded to FP16 and the approximate tanh put an error of order
+// 1e-3 into sigma, below the BF16 rounding the activations get next; |z/2|
+// beyond the FP16 range gives tanh = +-1, the limits of sigma. Training uses
+// the same sigma, so the layer-by-layer and fused passes agree.
+__device__ __forceinline__ float2 tanh2_half(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  uint32_t y;
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(y) : "r"(*reinterpret_cast<const uint32_t*>(&h)));
+  return __half22float2(*reinterpret_cast<const __half2*>(&y));
 }
-__device__ __forceinline__ float silu_f(float z) {
-  const float h = 0.5f * z;
-  return fmaf(h, tanh_fast(h), h);
+__device__ __forceinline__ float2 silu2_f(float z0, float z1) {
+  const float h0 = 0.5f * z0, h1 = 0.5f * z1;
+  const float2 t = tanh2_half(h0, h1);
+  return make_float2(fmaf(h0, t.x, h0), fmaf(h1, t.y, h1));
 }
+__device__ __forceinline__ float silu_f(float z) { return silu2_f(z, 0.0f).x; }
 // d/dz z sigma(z) = sigma (1 + z (1 - sigma)), with the same sigma
 __device__ __forceinline__ float dsilu_f(float z) {
-  const float s = fmaf(0.5f, tanh_fast(0.5f * z), 0.5f);
+  const float s = fmaf(0.5f, tanh2_half(0.5f * z, 0.0f).x, 0.5f);
   return s * fmaf(z, 1.0f - s, 1.0f);
 }
 
@@ -177,26 +185,35 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, const
 }
 
 // ---------------------------------------------------------------------------
-// Whole-network forward pass for inference. Persistent CTAs take 128-row
-// tiles in turn. The activation tile never leaves shared memory: it is the A
-// operand of the next layer (BF16, K-major core matrices), rewritten in place
-// by each layer's epilogue; the accumulator (up to 256 FP32 columns) lives in
-// tensor memory. The weights stream through two shared-memory k-tiles of 32,
-// filled by bulk copies (cp.async.bulk, completed on an mbarrier) from a BF16
-// copy of the weights packed in exactly that layout: while the tensor cores
-// work on one k-tile the next one is in flight, across layer and tile
-// boundaries. Only the network input and output cross HBM. Arithmetic per
-// element is that of the layered path above: BF16 operands, FP32
-// accumulation, FP32 bias and SiLU, activations rounded to BF16 as the next
-// layer's operand. Supported shapes: hidden widths multiples of 64 up to 256,
-// n_in and n_out up to 256, at most kFusedMaxLayers layers.
+// Whole-network forward pass for inference: one persistent CTA per SM, three
+// roles in warps of their own. The weights, packed once into BF16 k-tiles of
+// 32 in exactly the shared-memory layout the MMA reads, stream through a ring
+// of kFusedStages buffers filled by bulk copies (cp.async.bulk, the TMA
+// engine, completing on mbarriers) from a producer warp. An MMA warp issues
+// tcgen05.mma (kind::f16, BF16 operands, FP32 accumulator in tensor memory)
+// and commits each k-tile to free its buffer. Four epilogue warps (one per
+// tensor-memory lane quarter, 32 rows each) read the accumulator, add the
+// bias, apply SiLU and write the activations back to shared memory as BF16:
+// the next layer's A operand. Activations never leave shared memory; only
+// the network input and output cross HBM. The CTA keeps two 128-row tiles in
+// flight, each with its own activation tile and accumulator, and alternates
+// them layer by layer, so the epilogue of one tile runs while the tensor
+// cores work on the other. Arithmetic per element is that of the layered
+// path above: BF16 operands, FP32 accumulation, FP32 bias and SiLU,
+// activations rounded to BF16 as the next layer's operand. Supported shapes:
+// hidden widths multiples of 64 up to 256, n_in and n_out up to 256, at most
+// kFusedMaxLayers layers.
 // ---------------------------------------------------------------------------
 constexpr int kFusedMaxLayers = 8;
 constexpr int kFusedMaxN = 256;
 constexpr int kFK = 32;                                       // k-tile of the weight stream
-constexpr int kFusedSmemH = kTM * kFusedMaxN * 2;             // 64 KB activation tile
+constexpr int kFusedStages = 5;                               // weight ring depth
+constexpr int kFusedSmemH = kTM * kFusedMaxN * 2;             // 64 KB per activation tile
 constexpr int kFusedSmemW = kFusedMaxN * kFK * 2;             // 16 KB per weight buffer
-constexpr int kFusedSmem = kFusedSmemH + 2 * kFusedSmemW + kFusedMaxN * 4 + 1024;   // + bias + alignment
+constexpr int kFusedBias = kFusedMaxLayers * kFusedMaxN * 4;  // every layer's bias
+constexpr int kFusedSmem = 2 * kFusedSmemH + kFusedStages * kFusedSmemW + kFusedBias + 1024;   // + alignment
+constexpr int kFusedEpiWarps = 8;                             // two per tensor-memory lane quarter
+constexpr int kFusedThreads = 32 * (kFusedEpiWarps + 2);      // + producer warp + MMA warp
 
 struct FusedNet {
   int nl;                                       // layers
@@ -249,168 +266,253 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
       : "r"(taddr));
 }
 
-__global__ void __launch_bounds__(128) mlp_fused_forward_kernel(int64_t B, const float* __restrict__ X,
-                                                                float* __restrict__ out, const FusedNet net,
-                                                                int* __restrict__ status) {
+// Work order of one CTA: its row tiles in pairs; within a pair, unit
+// (tile, layer) in the order (t0, 0), (t1, 0), (t0, 1), (t1, 1), ...; tile j of
+// the pair uses slot j (activation tile and accumulator). All three roles walk
+// this order.
+struct FusedOrder {
+  int64_t ntiles, first, stride, mine;   // row tiles, this CTA's first, grid stride, count
+  int nl;
+  // unit u -> (local tile index, layer); units per pair = nl * tiles in the pair
+  __device__ void unit(int64_t u, int64_t& lt, int& l) const {
+    const int64_t per_pair = 2 * int64_t(nl);
+    const int64_t pair = u / per_pair;
+    int64_t r = u - pair * per_pair;
+    const int64_t in_pair = mine - 2 * pair >= 2 ? 2 : 1;
+    l = int(r / in_pair);
+    lt = 2 * pair + (r - int64_t(l) * in_pair);
+  }
+  __device__ int64_t units() const { return mine * nl; }
+};
+
+__global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_forward_kernel(int64_t B, const float* __restrict__ X,
+                                                                             float* __restrict__ out,
+                                                                             const FusedNet net,
+                                                                             int* __restrict__ status) {
   extern __shared__ unsigned char fused_smem_raw[];
-  unsigned char* sH =
+  unsigned char* sH0 =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(fused_smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* sW = sH + kFusedSmemH;                                   // two buffers of kFusedSmemW
-  float* sbias = reinterpret_cast<float*>(sW + 2 * kFusedSmemW);
-  __shared__ __align__(8) unsigned long long full[2], empty[2];
+  unsigned char* sW = sH0 + 2 * kFusedSmemH;                               // kFusedStages buffers
+  float* sbias = reinterpret_cast<float*>(sW + kFusedStages * kFusedSmemW);  // [layer][kFusedMaxN]
+  __shared__ __align__(8) unsigned long long full[kFusedStages], empty[kFusedStages], acc_full[2], h_ready[2];
   __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t ntiles = (B + kTM - 1) / kTM;
-  // weight k-tiles per pass over the network, and in all of this CTA's tiles
-  int per_pass = 0;
-  for (int l = 0; l < net.nl; ++l) per_pass += net.kp[l] / kFK;
-  const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int64_t total = my_tiles * per_pass;
+  FusedOrder ord;
+  ord.ntiles = (B + kTM - 1) / kTM;
+  ord.first = blockIdx.x;
+  ord.stride = gridDim.x;
+  ord.mine = ord.first < ord.ntiles ? (ord.ntiles - 1 - ord.first) / ord.stride + 1 : 0;
+  ord.nl = net.nl;
+  const int64_t nunits = ord.units();
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kFusedStages; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[b])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])) : "memory");
     }
+    for (int j = 0; j < 2; ++j) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_full[j])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&h_ready[j])), "r"(kFusedEpiWarps)
+                   : "memory");
+    }
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  for (int l = 0; l < net.nl; ++l)
+    for (int n = tid; n < net.np[l]; n += kFusedThreads) sbias[l * kFusedMaxN + n] = n < net.fo[l] ? net.bias[l][n] : 0.0f;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(uint32_t(kFusedMaxN)) : "memory");
+                 "r"(uint32_t(2 * kFusedMaxN)) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  // thread 0: copy of weight k-tile g of the stream into buffer g % 2
-  int64_t issued = 0;
-  auto issue_copy = [&](int64_t g) {
-    int loc = int(g % per_pass), l = 0;
-    while (loc >= net.kp[l] / kFK) { loc -= net.kp[l] / kFK; ++l; }
-    const uint32_t bytes = uint32_t(net.np[l]) * kFK * 2;
-    const uint32_t bar = smem_u32(&full[g & 1]);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(sW + (g & 1) * kFusedSmemW)),
-                 "l"(net.wpk + net.woff[l] + size_t(loc) * bytes), "r"(bytes), "r"(bar)
-                 : "memory");
-    issued = g + 1;
+  // a wait that gives up stops every role: the others skip their later waits
+  auto wait = [&](unsigned long long* bar, uint32_t parity) {
+    if (abort_flag) return false;
+    if (mbar_wait(smem_u32(bar), parity)) return true;
+    abort_flag = 1;
+    return false;
   };
-  bool ok = true;
-  int64_t g = 0;           // next k-tile of the stream
-  int64_t committed = 0;   // k-tiles whose MMAs were issued (thread 0)
-  if (tid == 0 && total > 0) issue_copy(0);
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t r0 = tile * kTM;
-    const int row = 32 * warp + lane;
-    const int64_t gr = r0 + row;
-    // input tile: each thread stages its row, eight columns per 16-byte
-    // store, zero beyond n_in and beyond the batch
-    {
-      const int kp = net.kp[0], fi = net.fi[0];
-      const float* x = X + (r0 + tid) * fi;
-      const bool in = r0 + tid < B;
-      for (int k0 = 0; k0 < kp; k0 += 8) {
-        float v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = (in && k0 + j < fi) ? x[k0 + j] : 0.0f;
-        *reinterpret_cast<uint4*>(sH + core_off(tid, k0, kp)) = make_uint4(
-            pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+  if (warp == kFusedEpiWarps) {
+    // producer: weight k-tile g of the stream into buffer g % kFusedStages
+    if (lane == 0) {
+      int64_t g = 0;
+      for (int64_t u = 0; u < nunits && !abort_flag; ++u) {
+        int64_t lt;
+        int l;
+        ord.unit(u, lt, l);
+        const uint32_t bytes = uint32_t(net.np[l]) * kFK * 2;
+        for (int kt = 0; kt < net.kp[l] / kFK; ++kt, ++g) {
+          const int st = int(g % kFusedStages);
+          if (g >= kFusedStages && !wait(&empty[st], uint32_t(g / kFusedStages - 1) & 1u)) break;
+          const uint32_t bar = smem_u32(&full[st]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                           smem_u32(sW + st * kFusedSmemW)),
+                       "l"(net.wpk + net.woff[l] + size_t(kt) * bytes), "r"(bytes), "r"(bar)
+                       : "memory");
+        }
       }
+      // on a give-up, let the copies in flight land before the CTA leaves
+      if (abort_flag && g > 0) mbar_wait(smem_u32(&full[(g - 1) % kFusedStages]), uint32_t((g - 1) / kFusedStages) & 1u);
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    for (int l = 0; l < net.nl; ++l) {
-      const int kp = net.kp[l], np = net.np[l], fo = net.fo[l];
-      if (tid == 0 && ok) {
+  } else if (warp == kFusedEpiWarps + 1) {
+    // MMA issuer
+    if (lane == 0) {
+      int64_t g = 0, done_units[2] = {0, 0};
+      bool issued = false;
+      for (int64_t u = 0; u < nunits && !abort_flag; ++u) {
+        int64_t lt;
+        int l;
+        ord.unit(u, lt, l);
+        const int slot = int(lt & 1);
+        const int kp = net.kp[l], np = net.np[l];
+        // the slot's activations are written and its accumulator drained
+        if (!wait(&h_ready[slot], uint32_t(done_units[slot]) & 1u)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t idesc =
             (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(np >> 3) << 17) | (uint32_t(kTM >> 4) << 24);
+        const uint32_t hbase = smem_u32(sH0 + slot * kFusedSmemH);
+        const uint32_t dtm = tmem + uint32_t(slot * kFusedMaxN);
+        bool ok = true;
         for (int kt = 0; kt < kp / kFK; ++kt, ++g) {
-          if (!mbar_wait(smem_u32(&full[g & 1]), uint32_t(g >> 1) & 1u)) { ok = false; break; }
+          const int st = int(g % kFusedStages);
+          if (!wait(&full[st], uint32_t(g / kFusedStages) & 1u)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
           for (int kk = 0; kk < kFK / 16; ++kk) {
-            const uint64_t ad = umma_desc(smem_u32(sH) + uint32_t(kt * (kFK / 8) + kk * 2) * 128u, 128,
-                                          uint32_t(kp) * 16u);
-            const uint64_t bd = umma_desc(smem_u32(sW + (g & 1) * kFusedSmemW) + uint32_t(kk) * 256u, 128,
-                                          (kFK / 8) * 128);
+            const uint64_t ad = umma_desc(hbase + uint32_t(kt * (kFK / 8) + kk * 2) * 128u, 128, uint32_t(kp) * 16u);
+            const uint64_t bd = umma_desc(smem_u32(sW + st * kFusedSmemW) + uint32_t(kk) * 256u, 128, (kFK / 8) * 128);
             const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
             asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtm),
                          "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
           }
+          // the buffer is free once these MMAs complete
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           smem_u32(&empty[g & 1]))
+                           smem_u32(&empty[st]))
                        : "memory");
-          committed = g + 1;
-          // the other buffer is free once the previous k-tile's MMAs completed:
-          // refill it with the next k-tile while this one's MMAs run
-          if (g >= 1 && !mbar_wait(smem_u32(&empty[(g - 1) & 1]), uint32_t((g - 1) >> 1) & 1u)) { ok = false; break; }
-          if (g + 1 < total) issue_copy(g + 1);
+          issued = true;
         }
-        // the layer's accumulator is complete when its last k-tile's MMAs are
-        if (ok && !mbar_wait(smem_u32(&empty[(g - 1) & 1]), uint32_t((g - 1) >> 1) & 1u)) ok = false;
+        if (!ok) break;
+        // the unit's accumulator is complete when its MMAs are
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&acc_full[slot]))
+                     : "memory");
+        ++done_units[slot];
       }
-      const bool last = l + 1 == net.nl;
-      for (int n = tid; n < np; n += 128) sbias[n] = n < fo ? net.bias[l][n] : 0.0f;
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      ok = __syncthreads_and(ok);
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int kpn = last ? 0 : net.kp[l + 1];
-      for (int c0 = 0; c0 < np; c0 += 32) {
-        const int nc = np - c0 >= 32 ? 32 : 16;
-        uint32_t r[32];
-        const uint32_t ta = tmem + (uint32_t(32 * warp) << 16) + uint32_t(c0);
-        tmem_ld16(ta, r);
-        if (nc == 32) tmem_ld16(ta + 16u, r + 16);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (last) {
-          if (gr < B) {
+      // on a give-up, let the MMAs in flight finish before tensor memory is freed
+      if (abort_flag && issued) mbar_wait(smem_u32(&empty[(g - 1) % kFusedStages]), uint32_t((g - 1) / kFusedStages) & 1u);
+    }
+  } else {
+    // epilogue warps: warp w reads tensor-memory lane quarter w % 4 (rows
+    // 32 (w % 4) + lane of each tile) and the 16-column chunks of parity w / 4
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = 32 * quarter + lane;
+    auto stage_input = [&](int64_t lt) {
+      const int slot = int(lt & 1);
+      unsigned char* sH = sH0 + slot * kFusedSmemH;
+      const int64_t r0 = (ord.first + lt * ord.stride) * kTM;
+      const int kp = net.kp[0], fi = net.fi[0];
+      const float* x = X + (r0 + row) * fi;
+      const bool in = r0 + row < B;
+      for (int k0 = 8 * half; k0 < kp; k0 += 16) {
+        float v[8];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int n = c0 + j;
-              if (j < nc && n < fo) out[gr * fo + n] = ok ? __uint_as_float(r[j]) + sbias[n] : __int_as_float(0x7fc00000);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            if (8 * h < nc) {
-              float v[8];
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const int n = c0 + 8 * h + j;
-                v[j] = n < fo ? silu_f(__uint_as_float(r[8 * h + j]) + sbias[n]) : 0.0f;
-              }
-              *reinterpret_cast<uint4*>(sH + core_off(row, c0 + 8 * h, kpn)) = make_uint4(
-                  pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
-            }
-          }
-        }
+        for (int j = 0; j < 8; ++j) v[j] = (in && k0 + j < fi) ? x[k0 + j] : 0.0f;
+        *reinterpret_cast<uint4*>(sH + core_off(row, k0, kp)) = make_uint4(
+            pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
       }
-      if (!last)
-        for (int k0 = np; k0 < kpn; k0 += 8)
-          *reinterpret_cast<uint4*>(sH + core_off(row, k0, kpn)) = make_uint4(0, 0, 0, 0);
-      // the rewritten tile is the next layer's operand; tensor memory and the
-      // bias are free for the next layer
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&h_ready[slot])) : "memory");
+    };
+    if (ord.mine > 0) stage_input(0);
+    if (ord.mine > 1) stage_input(1);
+    int64_t seen[2] = {0, 0};
+    for (int64_t u = 0; u < nunits; ++u) {
+      int64_t lt;
+      int l;
+      ord.unit(u, lt, l);
+      const int slot = int(lt & 1);
+      // warp-uniform, since the tensor-memory loads below are warp-collective
+      const bool ok = __all_sync(0xffffffffu, wait(&acc_full[slot], uint32_t(seen[slot]) & 1u));
+      ++seen[slot];
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int np = net.np[l], fo = net.fo[l];
+      const bool last = l + 1 == net.nl;
+      const float* bias = sbias + l * kFusedMaxN;
+      const int64_t gr = (ord.first + lt * ord.stride) * kTM + row;
+      unsigned char* sH = sH0 + slot * kFusedSmemH;
+      const int kpn = last ? 0 : net.kp[l + 1];
+      if (ok) {
+        // this warp's 16-column chunks c0 = 16 half + 32 i; four tensor-memory
+        // loads in flight per wait
+        const int nch = (np - 16 * half + 31) / 32;
+        for (int i0 = 0; i0 < nch; i0 += 4) {
+          uint32_t r[4][16];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (i0 + q < nch)
+              tmem_ld16(tmem + (uint32_t(32 * quarter) << 16) + uint32_t(slot * kFusedMaxN + 16 * half + 32 * (i0 + q)),
+                        r[q]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (i0 + q >= nch) break;
+            const int c0 = 16 * half + 32 * (i0 + q);
+            float b[16];
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+              *reinterpret_cast<float4*>(b + j) = *reinterpret_cast<const float4*>(bias + c0 + j);
+            if (last) {
+              if (gr < B) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                  if (c0 + j < fo) out[gr * fo + c0 + j] = __uint_as_float(r[q][j]) + b[j];
+              }
+            } else {
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                uint32_t w[4];
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                  const int n = c0 + 8 * h + j;
+                  const float2 a = silu2_f(__uint_as_float(r[q][8 * h + j]) + b[8 * h + j],
+                                           __uint_as_float(r[q][8 * h + j + 1]) + b[8 * h + j + 1]);
+                  w[j / 2] = pack_bf16x2(n < fo ? a.x : 0.0f, n + 1 < fo ? a.y : 0.0f);
+                }
+                *reinterpret_cast<uint4*>(sH + core_off(row, c0 + 8 * h, kpn)) = make_uint4(w[0], w[1], w[2], w[3]);
+              }
+            }
+          }
+        }
+      } else if (last && gr < B) {
+        for (int n = half; n < fo; n += 2) out[gr * fo + n] = __int_as_float(0x7fc00000);
+      }
+      if (!last) {
+        for (int k0 = np + 8 * half; k0 < kpn; k0 += 16)
+          *reinterpret_cast<uint4*>(sH + core_off(row, k0, kpn)) = make_uint4(0, 0, 0, 0);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&h_ready[slot])) : "memory");
+      } else if (lt + 2 < ord.mine) {
+        // this slot's next tile (its accumulator has been read)
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        stage_input(lt + 2);
+      }
     }
   }
-  if (tid == 0 && !ok) {
-    if (status) atomicExch(status, 1);
-    // copies may still be landing in shared memory and MMAs still running:
-    // wait for the last of each (bounded) before the tensor memory is freed
-    if (issued > 0) mbar_wait(smem_u32(&full[(issued - 1) & 1]), uint32_t((issued - 1) >> 1) & 1u);
-    if (committed > 0) mbar_wait(smem_u32(&empty[(committed - 1) & 1]), uint32_t((committed - 1) >> 1) & 1u);
-  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (tid == 0 && abort_flag && status) atomicExch(status, 1);
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(kFusedMaxN)) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(2 * kFusedMaxN)) : "memory");
 }
 
 // dZ = dH * silu'(Z), in place on dH.
@@ -613,10 +715,11 @@ cudaError_t forward_fused(dlbchem_mlp* m, int64_t B, const float* X, float* out,
     if (e != cudaSuccess) return e;
     m->packed_dirty = false;
   }
-  // persistent: two CTAs per SM (shared memory and tensor memory allow two)
+  // persistent: one CTA per SM (its two accumulators fill tensor memory)
   const int64_t tiles = (B + dlb::kTM - 1) / dlb::kTM;
-  const int64_t grid = std::min<int64_t>(tiles, 2 * int64_t(m->num_sms));
-  dlb::mlp_fused_forward_kernel<<<unsigned(grid), 128, dlb::kFusedSmem, s>>>(B, X, out, m->fnet, m->d_status);
+  const int64_t grid = std::min<int64_t>(tiles, int64_t(m->num_sms));
+  dlb::mlp_fused_forward_kernel<<<unsigned(grid), dlb::kFusedThreads, dlb::kFusedSmem, s>>>(B, X, out, m->fnet,
+                                                                                           m->d_status);
   return cudaGetLastError();
 }
 

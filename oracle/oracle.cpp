@@ -26,6 +26,7 @@
 // linear solve. The end-to-end result of a multi-species mechanism has no
 // published value to compare with: parity unpinned beyond those pins.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
@@ -53,6 +54,9 @@ struct Reaction {
   // T1), 3 Troe (a, T3, T1, T2); low-pressure limit lnA0, beta0, Ea0
   int falloff = 0;
   double lnA0 = 0, beta0 = 0, Ea0 = 0, troe_a = 0, T3 = 1, T1 = 1, T2 = 0;
+  // pressure-dependent Arrhenius (PLOG): points (p [Pa], lnA, beta, Ea) with
+  // p strictly increasing; empty for every other reaction
+  std::vector<std::array<double, 4>> plog;
 };
 
 struct Mech {
@@ -123,6 +127,27 @@ bool load_mech(const char* path, Mech& m, std::string& err) {
       r.lnA0 = d[0]; r.beta0 = d[1]; r.Ea0 = d[2]; r.troe_a = d[3]; r.T3 = d[4]; r.T1 = d[5]; r.T2 = d[6];
     }
   }
+  // optional PLOG section
+  if (off + 12 <= buf.size() && std::memcmp(buf.data() + off, "PLOG0001", 8) == 0) {
+    off += 8;
+    int32_t npl = 0;
+    get(buf, off, &npl, 1);
+    for (int i = 0; i < npl; ++i) {
+      int32_t jn[2];
+      if (!get(buf, off, jn, 2)) { err = "truncated PLOG section"; return false; }
+      if (jn[0] < 0 || jn[0] >= m.nrx || jn[1] < 1) { err = "bad PLOG record"; return false; }
+      Reaction& r = m.rx[jn[0]];
+      if (r.thirdbody || r.falloff) { err = "PLOG on a third-body or fall-off reaction"; return false; }
+      r.plog.resize(jn[1]);
+      for (auto& q : r.plog)
+        if (!get(buf, off, q.data(), 4)) { err = "truncated PLOG section"; return false; }
+      for (int k = 0; k < jn[1]; ++k)
+        if (!(r.plog[k][0] > 0) || (k > 0 && !(r.plog[k][0] > r.plog[k - 1][0]))) {
+          err = "PLOG pressures must be positive and increasing";
+          return false;
+        }
+    }
+  }
   return true;
 }
 
@@ -140,12 +165,14 @@ double g_k(const Mech& m, int k, double T) { return h_k(m, k, T) - T * s_k(m, k,
 // rho in g/cm^3 from p in Pa: rho = 1e-6 * p * Wbar / (R T), 1/Wbar = sum Y/W.
 struct Mix {
   double T, rho, S;        // S = sum_k Y_k / W_k
+  double p;                // Pa
   std::vector<double> c;   // mol/cm^3
 };
 
 Mix mixture(const Mech& m, double p, const double* y) {
   Mix x;
   x.T = y[0];
+  x.p = p;
   x.S = 0;
   for (int k = 0; k < m.nsp; ++k) x.S += y[1 + k] / m.W[k];
   x.rho = 1e-6 * p / (kR * x.T * x.S);
@@ -208,6 +235,25 @@ void falloff_rate(const Reaction& r, double T, double M, double& k, double& dlnk
   dlnk_dT = dlnkinf + dlnk_dlnPr * (dlnk0 - dlnkinf) + dlnF_dT;
 }
 
+// Rate constant of a PLOG reaction at pressure p (Pa): each listed point i
+// has its own Arrhenius form k_i(T); between the two points that bracket p,
+// ln k = ln k_i + (ln k_{i+1} - ln k_i) (ln p - ln p_i) / (ln p_{i+1} - ln p_i);
+// below the first and above the last listed pressure, that point's k.
+// Returns k and d ln k / dT (p is constant during a step).
+void plog_rate(const Reaction& r, double T, double p, double& k, double& dlnk_dT) {
+  auto lnk = [&](int i) { return r.plog[i][1] + r.plog[i][2] * std::log(T) - r.plog[i][3] / (kR * T); };
+  auto dlnk = [&](int i) { return r.plog[i][2] / T + r.plog[i][3] / (kR * T * T); };
+  const int n = int(r.plog.size());
+  if (p <= r.plog[0][0]) { k = std::exp(lnk(0)); dlnk_dT = dlnk(0); return; }
+  if (p >= r.plog[n - 1][0]) { k = std::exp(lnk(n - 1)); dlnk_dT = dlnk(n - 1); return; }
+  int i = 0;
+  while (!(p < r.plog[i + 1][0])) ++i;
+  const double w = (std::log(p) - std::log(r.plog[i][0])) / (std::log(r.plog[i + 1][0]) - std::log(r.plog[i][0]));
+  const double a = lnk(i), b = lnk(i + 1);
+  k = std::exp(a + w * (b - a));
+  dlnk_dT = dlnk(i) + w * (dlnk(i + 1) - dlnk(i));
+}
+
 int delta_nu(const Reaction& r) {
   int d = 0;
   for (auto& s : r.prod) d += s.second;
@@ -237,6 +283,8 @@ Rates rates(const Mech& m, const Mix& x) {
     if (r.falloff) {
       falloff_rate(r, T, M, R.kf[j], R.dlnkf_dT[j], R.dlnkf_dlnM[j]);
       M = 1.0;                       // [M] enters through the reduced pressure only
+    } else if (!r.plog.empty()) {
+      plog_rate(r, T, x.p, R.kf[j], R.dlnkf_dT[j]);
     } else {
       R.kf[j] = std::exp(r.lnA + r.beta * std::log(T) - r.Ea / (kR * T));
       R.dlnkf_dT[j] = r.beta / T + r.Ea / (kR * T * T);

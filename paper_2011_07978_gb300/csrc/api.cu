@@ -111,6 +111,28 @@ bool parse_mech(const char* path, dlb::HostMech& m, std::string& err) {
     }
     if (!rd.ok) { err = "truncated fall-off section"; return false; }
   }
+  // optional PLOG section
+  if (rd.pos + 12 <= buf.size() && std::memcmp(buf.data() + rd.pos, "PLOG0001", 8) == 0) {
+    rd.pos += 8;
+    const int npl = rd.get<int32_t>();
+    for (int i = 0; i < npl && rd.ok; ++i) {
+      const int j = rd.get<int32_t>(), n = rd.get<int32_t>();
+      if (!rd.ok) break;
+      if (j < 0 || j >= m.nrx || n < 1 || n > 64) { err = "bad PLOG record"; return false; }
+      HostRxn& r = m.rx[j];
+      if (r.tb || r.fall) { err = "PLOG on a third-body or fall-off reaction"; return false; }
+      r.plog.resize(n);
+      for (auto& q : r.plog)
+        for (auto& v : q) v = rd.get<double>();
+      if (!rd.ok) break;
+      for (int k = 0; k < n; ++k)
+        if (!(r.plog[k][0] > 0) || (k > 0 && !(r.plog[k][0] > r.plog[k - 1][0]))) {
+          err = "PLOG pressures must be positive and increasing";
+          return false;
+        }
+    }
+    if (!rd.ok) { err = "truncated PLOG section"; return false; }
+  }
   for (int k = 0; k < m.nsp; ++k)
     if (!(m.W[k] > 0.0)) { err = "non-positive molar mass"; return false; }
   return true;
@@ -334,9 +356,11 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
       if (cst < best) { best = cst; order = o; parity = par; }
     }
   }
-  // fall-off reactions first (stable), so that they share warp rounds and the
-  // other rounds never take their branch
+  // fall-off reactions first, then PLOG reactions (stable), so that each kind
+  // shares warp rounds and the other rounds never take their branch
   std::stable_partition(order.begin(), order.end(), [&](int r) { return hm.rx[r].fall != 0; });
+  std::stable_partition(order.begin(), order.end(),
+                        [&](int r) { return hm.rx[r].fall != 0 || !hm.rx[r].plog.empty(); });
   if (order_out) *order_out = order;
   // reactions (device index r is file reaction order[r])
   std::vector<double> lnA(nrx), beta(nrx), EaR(nrx), dH0(nrx, 0.0), dHa(nrx, 0.0), dHb(nrx, 0.0);
@@ -346,6 +370,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   std::vector<double> kB0(nrx, 0.0), kB1(nrx, 0.0), kB2(nrx, 0.0);
   std::vector<RxnMeta> meta(nrx);
   std::vector<double> fall(size_t(8) * std::max(nrx, 1), 0.0);
+  std::vector<double> plog;
   std::vector<int32_t> eff_sp;
   std::vector<double> eff_dm1;
   std::vector<std::vector<int>> distinct(nrx);
@@ -387,6 +412,20 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
       for (auto& e : x.eff) { eff_sp.push_back(e.first); eff_dm1.push_back(e.second - 1.0); }
     }
     mt.eff_end = int32_t(eff_sp.size());
+    if (!x.plog.empty()) {
+      mt.flags |= RX_PLOG;
+      mt.eff_begin = int32_t(plog.size() / 5);
+      const int n = int(x.plog.size());
+      for (int i = 0; i < n; ++i) {
+        const double lp = std::log(x.plog[i][0]);
+        plog.push_back(lp);
+        plog.push_back(x.plog[i][1]);
+        plog.push_back(x.plog[i][2]);
+        plog.push_back(x.plog[i][3] / kR);
+        plog.push_back(i + 1 < n ? 1.0 / (std::log(x.plog[i + 1][0]) - lp) : 0.0);
+      }
+      mt.eff_end = int32_t(plog.size() / 5);
+    }
     DS = std::max(DS, int(mt.nds));
   }
   dm.DS = DS;
@@ -517,6 +556,8 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   offs.push_back(put(incp_all.data(), incp_all.size() * 4));
   for (auto* v : {&kB0, &kB1, &kB2}) offs.push_back(put(v->data(), v->size() * 8));
   offs.push_back(put(fall.data(), fall.size() * 8));
+  if (plog.empty()) plog.assign(5, 0.0);
+  offs.push_back(put(plog.data(), plog.size() * 8));
   // store offsets as fake pointers; relocated after upload
   auto P = [&](int i) { return reinterpret_cast<const double*>(offs[i]); };
   dm.W = P(0); dm.iW = P(1); dm.H0 = P(2); dm.cpa = P(3); dm.hcpb = P(4); dm.cpb = P(5);
@@ -536,6 +577,7 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   dm.incp_all = reinterpret_cast<const int32_t*>(offs[25]);
   dm.kB0 = P(26); dm.kB1 = P(27); dm.kB2 = P(28);
   dm.fall = P(29);
+  dm.plog = P(30);
   return true;
 }
 
@@ -560,6 +602,7 @@ void relocate(DevMech& dm, void* base) {
   dm.incp_all = reloc(dm.incp_all, base);
   dm.kB0 = reloc(dm.kB0, base); dm.kB1 = reloc(dm.kB1, base); dm.kB2 = reloc(dm.kB2, base);
   dm.fall = reloc(dm.fall, base);
+  dm.plog = reloc(dm.plog, base);
 }
 
 int configure_launch(dlbchem_ctx* c) {

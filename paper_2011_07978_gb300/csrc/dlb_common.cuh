@@ -35,15 +35,16 @@ struct RxnMeta {
   uint8_t nr, np;       // expanded reactant / product counts
   int8_t dnu;           // np - nr
   uint8_t flags;        // bit0 reversible, bit1 third-body, bit2 listed efficiencies,
-                        // bit3 fall-off, bit4 Troe broadening, bit5 Troe's fourth parameter
+                        // bit3 fall-off, bit4 Troe broadening, bit5 Troe's fourth parameter,
+                        // bit6 pressure-dependent Arrhenius (PLOG)
   uint8_t nds;          // D slots in use (participants + 1 if listed efficiencies)
   uint8_t dslot_eff;    // D slot holding (fwd - rev) for listed efficiencies
-  int32_t eff_begin;    // listed-efficiency range [eff_begin, eff_end)
-  int32_t eff_end;
+  int32_t eff_begin;    // listed-efficiency range [eff_begin, eff_end); for a PLOG
+  int32_t eff_end;      // reaction (never third-body) its points [eff_begin, eff_end) in plog
 };
 static_assert(sizeof(RxnMeta) == 32, "RxnMeta layout");
 
-enum : uint8_t { RX_REV = 1, RX_TB = 2, RX_EFF = 4, RX_FALL = 8, RX_TROE = 16, RX_TROE4 = 32 };
+enum : uint8_t { RX_REV = 1, RX_TB = 2, RX_EFF = 4, RX_FALL = 8, RX_TROE = 16, RX_TROE4 = 32, RX_PLOG = 64 };
 
 // Incidence entry (target slot k, reaction r, coefficient nu), packed:
 //   k in bits 20..31, r in bits 4..19, nu + 8 in bits 0..3. The target is a
@@ -68,6 +69,9 @@ struct DevMech {
   // fall-off reactions (RX_FALL), 8 doubles per reaction: ln A0 - ln A,
   // beta0 - beta, (Ea0 - Ea)/R, Troe a, 1/T3, 1/T1, T2, unused
   const double* fall;
+  // PLOG points, 5 doubles each: ln p (Pa), ln A, beta, Ea/R, and 1 / (ln p of
+  // the next point - ln p) (0 for a reaction's last point)
+  const double* plog;
   const int32_t* eff_sp;
   const double* eff_dm1;
   // Reactions are processed in chunks of CH = team size; per chunk c and

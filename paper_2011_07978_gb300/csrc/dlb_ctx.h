@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdint>
 #include <string>
 #include <utility>
@@ -23,6 +24,9 @@ struct HostRxn {
   // 3 / 4 parameters; low-pressure limit lnA0, beta0, Ea0; Troe a, T3, T1, T2
   int fall = 0;
   double lnA0 = 0, beta0 = 0, Ea0 = 0, troe_a = 0, T3 = 1, T1 = 1, T2 = 0;
+  // pressure-dependent Arrhenius (PLOG) points (p [Pa], lnA, beta, Ea), p
+  // increasing; empty for every other reaction
+  std::vector<std::array<double, 4>> plog;
 };
 
 struct HostMech {

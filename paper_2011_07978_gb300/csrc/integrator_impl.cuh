@@ -152,6 +152,7 @@ __device__ __forceinline__ WS carve(double* base, const WsLayout& L) {
 // Mixture scalars shared by one rate evaluation.
 struct Mix {
   double T, iT, iT2, lnT, S, rho, irho, Ctot, irS;   // iT2 = 1/T^2, irS = 1/(rho S) = T / P1
+  double lnp;                                        // ln p (Pa), for PLOG reactions
 };
 
 // exp(x) by Tang's table-driven method (P. T. P. Tang, ACM TOMS 15(2), 1989):
@@ -257,10 +258,40 @@ __device__ __forceinline__ double falloff_factor(const double* __restrict__ fp, 
   return fac;
 }
 
+// Arrhenius parameters of a PLOG reaction at the cell's pressure. Between the
+// two listed pressures that bracket p, ln k is linear in ln p, and so are
+// ln A, beta and Ea/R (ln k = ln A + beta ln T - (Ea/R)/T); outside the
+// listed range, the nearest point's. Points pl[5 i ..]: ln p, ln A, beta,
+// Ea/R, 1 / (ln p_{i+1} - ln p_i).
+__device__ __forceinline__ void plog_params(const DevMech& m, const RxnMeta& mt, double lnp, double& lnA,
+                                            double& beta, double& EaR) {
+  const double* pl = m.plog + 5 * size_t(mt.eff_begin);
+  const int last = mt.eff_end - mt.eff_begin - 1;
+  int i = 0;
+  double wgt = 0.0;
+  if (lnp >= pl[5 * last]) {
+    i = last;
+  } else if (lnp > pl[0]) {
+    while (!(lnp < pl[5 * (i + 1)])) ++i;
+    wgt = (lnp - pl[5 * i]) * pl[5 * i + 4];
+  }
+  const double* a = pl + 5 * i;
+  if (wgt == 0.0) {
+    lnA = a[1]; beta = a[2]; EaR = a[3];
+  } else {
+    lnA = fma(wgt, a[6] - a[1], a[1]);
+    beta = fma(wgt, a[7] - a[2], a[2]);
+    EaR = fma(wgt, a[8] - a[3], a[3]);
+  }
+}
+
 template <bool JAC>
 __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mix& mx, int r, int rl, double* qdst) {
   const RxnMeta mt = m.meta[r];
-  double kf = exp_tab(fma(m.beta[r], mx.lnT, fma(-m.EaR[r], mx.iT, m.lnA[r])), w.exptab);
+  double lnA = m.lnA[r], beta = m.beta[r], EaR = m.EaR[r];
+  const bool plog = (mt.flags & RX_PLOG) != 0;
+  if (plog) plog_params(m, mt, mx.lnp, lnA, beta, EaR);
+  double kf = exp_tab(fma(beta, mx.lnT, fma(-EaR, mx.iT, lnA)), w.exptab);
   // expanded slots as fixed registers (unused slots hold 1)
   const double a0 = w.c[mt.sp[0]];
   const double a1 = mt.nr > 1 ? w.c[mt.sp[1]] : 1.0;
@@ -329,9 +360,16 @@ __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mi
   // d q / d T at fixed c: pf d ln k_f / dT - pr d ln k_r / dT, with
   // d ln k_r / dT = d ln k_f / dT - d ln K_c / dT = kB2 / T^2 + kB1 / T + kB0
   // (fall-off adds dfT to both)
-  const double dlnkf = fma(m.EaR[r], mx.iT2, m.beta[r] * mx.iT);
+  const double dlnkf = fma(EaR, mx.iT2, beta * mx.iT);
   double dq = pf * dlnkf;
-  if (mt.flags & RX_REV) dq = fma(-pr, fma(m.kB2[r], mx.iT2, fma(m.kB1[r], mx.iT, m.kB0[r])), dq);
+  if (mt.flags & RX_REV) {
+    double kB2 = m.kB2[r], kB1 = m.kB1[r];
+    if (plog) {   // the tables' constants hold the reaction record's Ea and beta
+      kB2 += EaR - m.EaR[r];
+      kB1 += beta - m.beta[r];
+    }
+    dq = fma(-pr, fma(kB2, mx.iT2, fma(kB1, mx.iT, m.kB0[r])), dq);
+  }
   if (fall) dq = fma(dfT, pf - pr, dq);
   // the assembly needs v only inside dwdot/dT - v/T and u - v/(rho S), so the
   // gathers carry those two combinations (sigma = sum_j c_j dq/dc_j)
@@ -364,6 +402,7 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
   mx.T = T; mx.iT = iT; mx.iT2 = iT * iT; mx.lnT = lnT; mx.S = S; mx.rho = rho; mx.irho = irho;
   mx.Ctot = P1 * iT;                          // sum_k c_k (unit efficiencies)
   mx.irS = T * iP1;
+  mx.lnp = w.scal[30];                        // set per cell by the caller
   for (int k = tm.tid; k < nsp; k += TS) {
     w.c[k] = rho * yv[1 + k] * m.iW[k];
     const double e = exp_tab(fma(m.G2[k], lnT, fma(m.G3[k], T, -fma(m.G0[k], iT, m.G1[k]))), w.exptab);
@@ -961,6 +1000,7 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
   const bool iso = P.isothermal != 0;
   for (int i = tm.tid; i < N; i += TS) w.y0[i] = (i == 0) ? Tin[cell] : Yin[int64_t(i - 1) * n + cell];
   const double p = pin[cell];
+  if (tm.tid == 0) w.scal[30] = log(p);   // ln p for PLOG reactions
   tm.sync();
   int bad = 0;
   for (int i = tm.tid; i < N; i += TS) bad |= !isfinite(w.y0[i]);
@@ -1194,6 +1234,7 @@ __global__ void __launch_bounds__(128) gate_kernel(const GateArgs a) {
       w.y0[i] = y;
       w.ys[i] = y + d;
     }
+    if (tm.tid == 0) w.scal[30] = log(p);
     tm.sync();
     int bad = 0;
     for (int i = tm.tid; i < N; i += TS) bad |= !isfinite(w.y0[i]);
@@ -1308,6 +1349,7 @@ __global__ void __launch_bounds__(128) rhs_kernel(const RhsArgs a) {
   for (int64_t cell = int64_t(blockIdx.x) * teams + team; cell < n; cell += int64_t(gridDim.x) * teams) {
     const double p = a.p[cell];
     for (int i = tm.tid; i < N; i += TS) w.y0[i] = i == 0 ? a.T[cell] : a.Y[int64_t(i - 1) * n + cell];
+    if (tm.tid == 0) w.scal[30] = log(p);
     tm.sync();
     int bad = 0;
     for (int i = tm.tid; i < N; i += TS) bad |= !isfinite(w.y0[i]);

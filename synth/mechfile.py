@@ -27,6 +27,15 @@ The layout is little-endian:
         A fall-off reaction is a third-body reaction whose [M] (with its
         efficiencies) enters through the reduced pressure instead of
         multiplying the rate.
+    optional pressure-dependent Arrhenius (PLOG) section, after the fall-off
+    section if both are present:
+        char[8] "PLOG0001", i32 n_plog, then n_plog records of
+        i32 reaction, i32 npts, npts x (f64 p [Pa], lnA, beta, Ea [J/mol]),
+        pressures strictly increasing. The reaction's rate constant at
+        pressure p: between the two listed pressures that bracket p, ln k is
+        linear in ln p; below the first or above the last listed pressure it
+        is that point's Arrhenius form. The reaction record's own lnA, beta,
+        Ea are not used. A PLOG reaction is neither third-body nor fall-off.
 
 Each species appears at most once per side; its integer coefficient is in
 rnu / pnu.
@@ -60,6 +69,7 @@ class Mechanism:
     thirdbody: np.ndarray        # [nrx] int
     eff: list = dataclasses.field(default_factory=list)  # (rxn, species, eff)
     falloff: list = dataclasses.field(default_factory=list)  # (rxn, kind, lnA0, beta0, Ea0, a, T3, T1, T2)
+    plog: list = dataclasses.field(default_factory=list)     # (rxn, [(p_Pa, lnA, beta, Ea), ...])
 
     @property
     def nsp(self) -> int:
@@ -110,6 +120,20 @@ def write_mech(path: str, m: Mechanism) -> None:
                 if kind not in (1, 2, 3) or not m.thirdbody[j]:
                     raise ValueError(f"fall-off record {rec}: kind 1..3 on a third-body reaction")
                 f.write(struct.pack("<2i7d", j, kind, *[float(x) for x in rec[2:9]]))
+        if m.plog:
+            fall_rx = {int(rec[0]) for rec in m.falloff}
+            f.write(b"PLOG0001")
+            f.write(struct.pack("<i", len(m.plog)))
+            for j, pts in m.plog:
+                j = int(j)
+                ps = [float(q[0]) for q in pts]
+                if (not pts or m.thirdbody[j] or j in fall_rx or min(ps) <= 0
+                        or any(b <= a for a, b in zip(ps, ps[1:]))):
+                    raise ValueError(f"PLOG record of reaction {j}: increasing positive pressures, "
+                                     "not on a third-body or fall-off reaction")
+                f.write(struct.pack("<2i", j, len(pts)))
+                for q in pts:
+                    f.write(struct.pack("<4d", *[float(x) for x in q]))
 
 
 def read_mech(path: str) -> Mechanism:
@@ -141,7 +165,7 @@ def read_mech(path: str) -> Mechanism:
         j, k, e = struct.unpack_from("<2id", buf, off)
         off += 16
         eff.append((j, k, e))
-    falloff = []
+    falloff, plog = [], []
     if len(buf) >= off + 12 and buf[off:off + 8] == b"FALLOFF1":
         (nf,) = struct.unpack_from("<i", buf, off + 8)
         off += 12
@@ -149,6 +173,15 @@ def read_mech(path: str) -> Mechanism:
             rec = struct.unpack_from("<2i7d", buf, off)
             off += 64
             falloff.append(tuple(rec))
+    if len(buf) >= off + 12 and buf[off:off + 8] == b"PLOG0001":
+        (npl,) = struct.unpack_from("<i", buf, off + 8)
+        off += 12
+        for _ in range(npl):
+            j, n = struct.unpack_from("<2i", buf, off)
+            off += 8
+            pts = [struct.unpack_from("<4d", buf, off + 32 * i) for i in range(n)]
+            off += 32 * n
+            plog.append((j, [tuple(q) for q in pts]))
     return Mechanism(W=arrs[0], cp_a=arrs[1], cp_b=arrs[2], hf=arrs[3], s0=arrs[4], atoms=atoms,
                      lnA=np.array(lnA), beta=np.array(beta), Ea=np.array(Ea), reac=reac, prod=prod,
-                     reversible=np.array(rev), thirdbody=np.array(tb), eff=eff, falloff=falloff)
+                     reversible=np.array(rev), thirdbody=np.array(tb), eff=eff, falloff=falloff, plog=plog)

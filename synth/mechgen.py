@@ -177,3 +177,29 @@ def with_falloff(m: Mechanism, seed: int) -> Mechanism:
     out.falloff = falloff
     out.eff = eff
     return out
+
+
+def with_plog(m: Mechanism, seed: int, frac: float = 0.15) -> Mechanism:
+    """A copy of m in which a seeded fraction of the reactions that are
+    neither third-body nor fall-off become pressure-dependent Arrhenius
+    (PLOG) reactions with 2-4 points at pressures drawn from 0.1-100 bar
+    (sorted), each point's parameters perturbed from the reaction's own:
+    A * U[0.2, 5], beta + U[-0.3, 0.3], Ea + U[-8, 8] kJ/mol (at least 0).
+    (Stand-in for real mechanisms' PLOG data, which is not available here.)"""
+    import copy
+    rng = np.random.default_rng(seed + 4242)
+    out = copy.deepcopy(m)
+    fall_rx = {int(r[0]) for r in m.falloff}
+    grid = np.array([1e4, 3e4, 1e5, 3e5, 1e6, 3e6, 1e7])
+    plog = []
+    for j in range(m.nrx):
+        if m.thirdbody[j] or j in fall_rx or rng.uniform() >= frac:
+            continue
+        n = int(rng.integers(2, 5))
+        ps = np.sort(rng.choice(grid, size=n, replace=False))
+        pts = [(float(pp), float(m.lnA[j] + np.log(rng.uniform(0.2, 5.0))), float(m.beta[j] + rng.uniform(-0.3, 0.3)),
+                float(max(0.0, m.Ea[j] + rng.uniform(-8e3, 8e3)))) for pp in ps]
+        plog.append((j, pts))
+    out.plog = plog
+    return out
+

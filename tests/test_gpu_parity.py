@@ -551,3 +551,57 @@ def test_falloff_mechanism_parity(tmp_path, which):
     # tight-tolerance solution as the oracle's own result, within a factor 2
     dT, dY, frac = assert_parity(g, o, min_tight=0.99, tight_ref=tight[:2])
     print(f"fall-off {which}: max dT/T {dT:.2e}, max dY {dY:.2e}, within 1e-9 {frac:.4f}")
+
+
+def test_plog_closed_form_on_gpu(tmp_path):
+    """A -> B between isomers as a PLOG reaction with three listed pressures:
+    Y_A decays as exp(-k t) with ln k interpolated linearly in ln p, and the
+    nearest point's k outside the listed range (the oracle's pin, on the
+    GPU), at listed pressures, between them and outside."""
+    R = 8.314462618
+    iso = dict(atoms=(1, 1, 0, 0), hf=-10e3, s0=200.0, a=30.0, b=0.002)
+    pts = [(1e5, np.log(2e6), 0.4, 25e3), (1e6, np.log(5e7), -0.2, 31e3), (1e7, np.log(8e8), 0.1, 40e3)]
+    path = tmp_path / "plog.bin"
+    tinymech.make(path, [iso, iso], [dict(reac=[(0, 1)], prod=[(1, 1)], lnA=0.0, rev=0)], plog=[(0, pts)])
+    ctx = dlb().Context(str(path), rtol=1e-9, atol=1e-15)
+    p = np.array([1e3, 1e5, np.sqrt(1e5 * 1e6), 1e6, 4e6, 1e7, 1e9])
+    T = np.full(p.size, 950.0)
+    Y = np.vstack([np.full(p.size, 1.0), np.zeros(p.size)])
+    dt = 3e-5
+    g = run_gpu(ctx, T, p, Y, dt)
+    lnk = [pt[1] + pt[2] * np.log(950.0) - pt[3] / (R * 950.0) for pt in pts]
+    k = np.exp(np.interp(np.log(p), [np.log(pt[0]) for pt in pts], lnk))
+    assert (k * dt > 0.05).any()
+    np.testing.assert_allclose(g[1][0], np.exp(-k * dt), rtol=1e-7, atol=1e-14)
+    np.testing.assert_array_equal(g[3], 0)
+
+
+@pytest.mark.parametrize("which", ["c1", "c2"])
+def test_plog_mechanism_parity(tmp_path, which):
+    """A seeded part of the reactions of the 10- and 53-species mechanisms
+    turned into PLOG reactions (2-4 listed pressures in 0.1-100 bar): GPU
+    against the oracle at pressures from 0.03 to 300 bar (inside, between
+    and outside the listed ranges), with the reference-free strict bar and
+    the rounding-sensitive-cell criterion of the fall-off test."""
+    from synth import read_mech, with_plog, write_mech
+    nsp, nrx = (10, 20) if which == "c1" else (53, 325)
+    m = with_plog(read_mech(states.mech_path(nsp, nrx, 0)), 0, frac=0.5 if which == "c1" else 0.15)
+    assert len(m.plog) >= 4
+    path = str(tmp_path / f"{which}_plog.bin")
+    write_mech(path, m)
+    if which == "c1":
+        T, p, Y = states.uniform_states(10, 400, 9)
+        dt, rtol, atol = 1e-6, 1e-8, 1e-12
+    else:
+        T, p, Y, cls = states.bimodal_states(53, 325, 400, 9)
+        dt, rtol, atol = 1e-5, 1e-5, 1e-8
+    p = np.geomspace(3e3, 3e7, T.size)[np.random.default_rng(2).permutation(T.size)]
+    p[:8] = [1e4, 3e4, 1e5, 3e5, 1e6, 3e6, 1e7, 1e5]          # exactly at listed pressures
+    ctx = dlb().Context(path, rtol=rtol, atol=atol, schedule=dlb().SCHED_QUEUE)
+    g = run_gpu(ctx, T, p, Y, dt)
+    orc = oracle.Oracle(path)
+    o = orc.integrate(T, p, Y, dt, rtol=rtol, atol=atol)
+    tight = orc.integrate(T, p, Y, dt, rtol=rtol * 1e-3, atol=atol * 1e-4)
+    assert (g[3] == 0).all()
+    dT, dY, frac = assert_parity(g, o, min_tight=0.99, tight_ref=tight[:2])
+    print(f"PLOG {which}: max dT/T {dT:.2e}, max dY {dY:.2e}, within 1e-9 {frac:.4f}")

@@ -6,7 +6,7 @@ import numpy as np
 from synth import Mechanism, write_mech
 
 
-def make(path, species, reactions, eff=(), falloff=()):
+def make(path, species, reactions, eff=(), falloff=(), plog=()):
     """species: list of dicts (atoms, hf, s0, a, b); reactions: dicts with
     reac, prod [(k, nu)], lnA, beta, Ea, rev, tb."""
     atoms = np.array([s["atoms"] for s in species])
@@ -21,6 +21,6 @@ def make(path, species, reactions, eff=(), falloff=()):
                   reac=[r["reac"] for r in reactions], prod=[r["prod"] for r in reactions],
                   reversible=np.array([r.get("rev", 1) for r in reactions]),
                   thirdbody=np.array([r.get("tb", 0) for r in reactions]), eff=list(eff),
-                  falloff=list(falloff))
+                  falloff=list(falloff), plog=list(plog))
     write_mech(str(path), m)
     return m

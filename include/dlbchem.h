@@ -122,9 +122,9 @@ int dlbchem_options_default(dlbchem_options* opt);
 /*
  * Load a mechanism file (the DLBMECH1 binary format written by the seeded
  * generator: species thermo, Arrhenius reactions with third bodies and
- * listed efficiencies, and optional fall-off (Lindemann, Troe) and PLOG
- * sections; synth/mechfile.py documents the layout) on the current CUDA
- * device and create a context: the
+ * listed efficiencies, and optional fall-off (Lindemann, Troe), PLOG and
+ * NASA-7 thermo sections; synth/mechfile.py documents the layout) on the
+ * current CUDA device and create a context: the
  * preprocessing of Sec. 2.2 stage 1 that every cell shares (the kinetics
  * each problem of Sec. 2.2 is integrated with). opt may be
  * NULL (defaults). On success *out owns device copies of the mechanism

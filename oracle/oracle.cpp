@@ -62,6 +62,9 @@ struct Reaction {
 struct Mech {
   int nsp = 0, nrx = 0, nelem = 0;
   std::vector<double> W, a, b, hf, s0;
+  // NASA-7 thermo when present: per species Tlow, Tmid, Thigh, low a1..a7,
+  // high a1..a7 (17 values); then a, b, hf, s0 are not used
+  std::vector<double> nasa;
   std::vector<int> atoms;
   std::vector<Reaction> rx;
 };
@@ -112,52 +115,85 @@ bool load_mech(const char* path, Mech& m, std::string& err) {
     if (jk[0] < 0 || jk[0] >= m.nrx || jk[1] < 0 || jk[1] >= m.nsp || !m.rx[jk[0]].thirdbody) { err = "bad efficiency"; return false; }
     m.rx[jk[0]].eff[jk[1]] = e;
   }
-  // optional fall-off section
-  if (off + 12 <= buf.size() && std::memcmp(buf.data() + off, "FALLOFF1", 8) == 0) {
-    off += 8;
-    int32_t nf = 0;
-    get(buf, off, &nf, 1);
-    for (int i = 0; i < nf; ++i) {
-      int32_t jk[2];
-      double d[7];
-      if (!get(buf, off, jk, 2) || !get(buf, off, d, 7)) { err = "truncated fall-off section"; return false; }
-      if (jk[0] < 0 || jk[0] >= m.nrx || jk[1] < 1 || jk[1] > 3 || !m.rx[jk[0]].thirdbody) { err = "bad fall-off record"; return false; }
-      Reaction& r = m.rx[jk[0]];
-      r.falloff = jk[1];
-      r.lnA0 = d[0]; r.beta0 = d[1]; r.Ea0 = d[2]; r.troe_a = d[3]; r.T3 = d[4]; r.T1 = d[5]; r.T2 = d[6];
+  // optional sections, in any order
+  while (off + 8 <= buf.size()) {
+    char tag[8];
+    get(buf, off, tag, 8);
+    if (std::memcmp(tag, "FALLOFF1", 8) == 0) {
+      int32_t nf = 0;
+      get(buf, off, &nf, 1);
+      for (int i = 0; i < nf; ++i) {
+        int32_t jk[2];
+        double d[7];
+        if (!get(buf, off, jk, 2) || !get(buf, off, d, 7)) { err = "truncated fall-off section"; return false; }
+        if (jk[0] < 0 || jk[0] >= m.nrx || jk[1] < 1 || jk[1] > 3 || !m.rx[jk[0]].thirdbody) { err = "bad fall-off record"; return false; }
+        Reaction& r = m.rx[jk[0]];
+        r.falloff = jk[1];
+        r.lnA0 = d[0]; r.beta0 = d[1]; r.Ea0 = d[2]; r.troe_a = d[3]; r.T3 = d[4]; r.T1 = d[5]; r.T2 = d[6];
+      }
+    } else if (std::memcmp(tag, "PLOG0001", 8) == 0) {
+      int32_t npl = 0;
+      get(buf, off, &npl, 1);
+      for (int i = 0; i < npl; ++i) {
+        int32_t jn[2];
+        if (!get(buf, off, jn, 2)) { err = "truncated PLOG section"; return false; }
+        if (jn[0] < 0 || jn[0] >= m.nrx || jn[1] < 1) { err = "bad PLOG record"; return false; }
+        Reaction& r = m.rx[jn[0]];
+        if (r.thirdbody || r.falloff) { err = "PLOG on a third-body or fall-off reaction"; return false; }
+        r.plog.resize(jn[1]);
+        for (auto& q : r.plog)
+          if (!get(buf, off, q.data(), 4)) { err = "truncated PLOG section"; return false; }
+        for (int k = 0; k < jn[1]; ++k)
+          if (!(r.plog[k][0] > 0) || (k > 0 && !(r.plog[k][0] > r.plog[k - 1][0]))) {
+            err = "PLOG pressures must be positive and increasing";
+            return false;
+          }
+      }
+    } else if (std::memcmp(tag, "NASA7001", 8) == 0) {
+      m.nasa.resize(size_t(17) * m.nsp);
+      if (!get(buf, off, m.nasa.data(), m.nasa.size())) { err = "truncated NASA-7 section"; return false; }
+      for (int k = 0; k < m.nsp; ++k)
+        if (!(m.nasa[17 * k + 1] > 0)) { err = "NASA-7 Tmid must be positive"; return false; }
+    } else {
+      err = "unknown mechanism file section";
+      return false;
     }
   }
-  // optional PLOG section
-  if (off + 12 <= buf.size() && std::memcmp(buf.data() + off, "PLOG0001", 8) == 0) {
-    off += 8;
-    int32_t npl = 0;
-    get(buf, off, &npl, 1);
-    for (int i = 0; i < npl; ++i) {
-      int32_t jn[2];
-      if (!get(buf, off, jn, 2)) { err = "truncated PLOG section"; return false; }
-      if (jn[0] < 0 || jn[0] >= m.nrx || jn[1] < 1) { err = "bad PLOG record"; return false; }
-      Reaction& r = m.rx[jn[0]];
-      if (r.thirdbody || r.falloff) { err = "PLOG on a third-body or fall-off reaction"; return false; }
-      r.plog.resize(jn[1]);
-      for (auto& q : r.plog)
-        if (!get(buf, off, q.data(), 4)) { err = "truncated PLOG section"; return false; }
-      for (int k = 0; k < jn[1]; ++k)
-        if (!(r.plog[k][0] > 0) || (k > 0 && !(r.plog[k][0] > r.plog[k - 1][0]))) {
-          err = "PLOG pressures must be positive and increasing";
-          return false;
-        }
-    }
-  }
+  for (auto& r : m.rx)
+    if (!r.plog.empty() && (r.thirdbody || r.falloff)) { err = "PLOG on a third-body or fall-off reaction"; return false; }
   return true;
 }
 
-// ---- thermodynamics (molar, cp = a + b T) ---------------------------------
-double cp_k(const Mech& m, int k, double T) { return m.a[k] + m.b[k] * T; }
+// ---- thermodynamics (molar) -------------------------------------------------
+// Linear cp = a + b T with h(T0) = hf and s(T0, p0) = s0, or, when the file
+// has them, the two NASA-7 polynomials of each species (low set below Tmid,
+// high set from Tmid up): cp/R = a1 + a2 T + a3 T^2 + a4 T^3 + a5 T^4,
+// h/(R T) = a1 + a2 T/2 + a3 T^2/3 + a4 T^3/4 + a5 T^4/5 + a6/T,
+// s/R = a1 ln T + a2 T + a3 T^2/2 + a4 T^3/3 + a5 T^4/4 + a7.
+const double* nasa_set(const Mech& m, int k, double T) {
+  const double* d = m.nasa.data() + size_t(17) * k;
+  return T < d[1] ? d + 3 : d + 10;
+}
+double cp_k(const Mech& m, int k, double T) {
+  if (m.nasa.empty()) return m.a[k] + m.b[k] * T;
+  const double* c = nasa_set(m, k, T);
+  return kR * (c[0] + c[1] * T + c[2] * T * T + c[3] * T * T * T + c[4] * T * T * T * T);
+}
+double dcp_k(const Mech& m, int k, double T) {   // d cp / dT
+  if (m.nasa.empty()) return m.b[k];
+  const double* c = nasa_set(m, k, T);
+  return kR * (c[1] + 2 * c[2] * T + 3 * c[3] * T * T + 4 * c[4] * T * T * T);
+}
 double h_k(const Mech& m, int k, double T) {
-  return m.hf[k] + m.a[k] * (T - kT0) + 0.5 * m.b[k] * (T * T - kT0 * kT0);
+  if (m.nasa.empty()) return m.hf[k] + m.a[k] * (T - kT0) + 0.5 * m.b[k] * (T * T - kT0 * kT0);
+  const double* c = nasa_set(m, k, T);
+  return kR * T * (c[0] + c[1] * T / 2 + c[2] * T * T / 3 + c[3] * T * T * T / 4 + c[4] * T * T * T * T / 5 + c[5] / T);
 }
 double s_k(const Mech& m, int k, double T) {
-  return m.s0[k] + m.a[k] * std::log(T / kT0) + m.b[k] * (T - kT0);
+  if (m.nasa.empty()) return m.s0[k] + m.a[k] * std::log(T / kT0) + m.b[k] * (T - kT0);
+  const double* c = nasa_set(m, k, T);
+  return kR * (c[0] * std::log(T) + c[1] * T + c[2] * T * T / 2 + c[3] * T * T * T / 3 + c[4] * T * T * T * T / 4 +
+               c[6]);
 }
 double g_k(const Mech& m, int k, double T) { return h_k(m, k, T) - T * s_k(m, k, T); }
 
@@ -419,7 +455,7 @@ void jacobian(const Mech& m, double p, const double* y, double* J, bool isotherm
   double cpm = 0, Q = 0, dcpmdT = 0;
   for (int k = 0; k < ns; ++k) {
     cpm += y[1 + k] * cp_k(m, k, T) / m.W[k];
-    dcpmdT += y[1 + k] * m.b[k] / m.W[k];
+    dcpmdT += y[1 + k] * dcp_k(m, k, T) / m.W[k];
     Q += h_k(m, k, T) * w[k];
   }
   std::vector<double> dQ(N, 0.0), drc(N, 0.0);   // dQ/dy, d(rho cpm)/dy

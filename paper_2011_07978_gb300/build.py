@@ -10,8 +10,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libdlbchem.so")
-SOURCES = ["integrator_w1.cu", "integrator_w2.cu", "integrator_w4.cu", "integrator.cu", "sched.cu", "api.cu", "batch.cu",
-           "mlp.cu", "noalloc.cu"]
+SOURCES = ["integrator_w1.cu", "integrator_w2.cu", "integrator_w4.cu", "integrator_w1p.cu", "integrator_w2p.cu",
+           "integrator_w4p.cu", "integrator.cu", "sched.cu", "api.cu", "batch.cu", "mlp.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--cudart", "shared"]
 

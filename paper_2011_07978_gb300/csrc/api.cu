@@ -94,45 +94,56 @@ bool parse_mech(const char* path, dlb::HostMech& m, std::string& err) {
     m.rx[j].eff.push_back({k, e});
   }
   if (!rd.ok) { err = "truncated mechanism file"; return false; }
-  // optional fall-off section
-  if (rd.pos + 12 <= buf.size() && std::memcmp(buf.data() + rd.pos, "FALLOFF1", 8) == 0) {
+  // optional sections, in any order
+  while (rd.pos + 8 <= buf.size()) {
+    char tag[8];
+    std::memcpy(tag, buf.data() + rd.pos, 8);
     rd.pos += 8;
-    const int nf = rd.get<int32_t>();
-    for (int i = 0; i < nf && rd.ok; ++i) {
-      const int j = rd.get<int32_t>(), kind = rd.get<int32_t>();
-      double d[7];
-      for (auto& x : d) x = rd.get<double>();
-      if (!rd.ok) break;
-      if (j < 0 || j >= m.nrx || kind < 1 || kind > 3 || !m.rx[j].tb) { err = "bad fall-off record"; return false; }
-      if (kind >= 2 && (!(d[4] > 0) || !(d[5] > 0))) { err = "Troe T3 and T1 must be positive"; return false; }
-      HostRxn& r = m.rx[j];
-      r.fall = kind;
-      r.lnA0 = d[0]; r.beta0 = d[1]; r.Ea0 = d[2]; r.troe_a = d[3]; r.T3 = d[4]; r.T1 = d[5]; r.T2 = d[6];
+    if (std::memcmp(tag, "FALLOFF1", 8) == 0) {
+      const int nf = rd.get<int32_t>();
+      for (int i = 0; i < nf && rd.ok; ++i) {
+        const int j = rd.get<int32_t>(), kind = rd.get<int32_t>();
+        double d[7];
+        for (auto& x : d) x = rd.get<double>();
+        if (!rd.ok) break;
+        if (j < 0 || j >= m.nrx || kind < 1 || kind > 3 || !m.rx[j].tb) { err = "bad fall-off record"; return false; }
+        if (kind >= 2 && (!(d[4] > 0) || !(d[5] > 0))) { err = "Troe T3 and T1 must be positive"; return false; }
+        HostRxn& r = m.rx[j];
+        r.fall = kind;
+        r.lnA0 = d[0]; r.beta0 = d[1]; r.Ea0 = d[2]; r.troe_a = d[3]; r.T3 = d[4]; r.T1 = d[5]; r.T2 = d[6];
+      }
+      if (!rd.ok) { err = "truncated fall-off section"; return false; }
+    } else if (std::memcmp(tag, "PLOG0001", 8) == 0) {
+      const int npl = rd.get<int32_t>();
+      for (int i = 0; i < npl && rd.ok; ++i) {
+        const int j = rd.get<int32_t>(), n = rd.get<int32_t>();
+        if (!rd.ok) break;
+        if (j < 0 || j >= m.nrx || n < 1 || n > 64) { err = "bad PLOG record"; return false; }
+        HostRxn& r = m.rx[j];
+        r.plog.resize(n);
+        for (auto& q : r.plog)
+          for (auto& v : q) v = rd.get<double>();
+        if (!rd.ok) break;
+        for (int k = 0; k < n; ++k)
+          if (!(r.plog[k][0] > 0) || (k > 0 && !(r.plog[k][0] > r.plog[k - 1][0]))) {
+            err = "PLOG pressures must be positive and increasing";
+            return false;
+          }
+      }
+      if (!rd.ok) { err = "truncated PLOG section"; return false; }
+    } else if (std::memcmp(tag, "NASA7001", 8) == 0) {
+      m.nasa.resize(size_t(17) * m.nsp);
+      for (auto& v : m.nasa) v = rd.get<double>();
+      if (!rd.ok) { err = "truncated NASA-7 section"; return false; }
+      for (int k = 0; k < m.nsp; ++k)
+        if (!(m.nasa[17 * size_t(k) + 1] > 0)) { err = "NASA-7 Tmid must be positive"; return false; }
+    } else {
+      err = "unknown mechanism file section";
+      return false;
     }
-    if (!rd.ok) { err = "truncated fall-off section"; return false; }
   }
-  // optional PLOG section
-  if (rd.pos + 12 <= buf.size() && std::memcmp(buf.data() + rd.pos, "PLOG0001", 8) == 0) {
-    rd.pos += 8;
-    const int npl = rd.get<int32_t>();
-    for (int i = 0; i < npl && rd.ok; ++i) {
-      const int j = rd.get<int32_t>(), n = rd.get<int32_t>();
-      if (!rd.ok) break;
-      if (j < 0 || j >= m.nrx || n < 1 || n > 64) { err = "bad PLOG record"; return false; }
-      HostRxn& r = m.rx[j];
-      if (r.tb || r.fall) { err = "PLOG on a third-body or fall-off reaction"; return false; }
-      r.plog.resize(n);
-      for (auto& q : r.plog)
-        for (auto& v : q) v = rd.get<double>();
-      if (!rd.ok) break;
-      for (int k = 0; k < n; ++k)
-        if (!(r.plog[k][0] > 0) || (k > 0 && !(r.plog[k][0] > r.plog[k - 1][0]))) {
-          err = "PLOG pressures must be positive and increasing";
-          return false;
-        }
-    }
-    if (!rd.ok) { err = "truncated PLOG section"; return false; }
-  }
+  for (const auto& r : m.rx)
+    if (!r.plog.empty() && (r.tb || r.fall)) { err = "PLOG on a third-body or fall-off reaction"; return false; }
   for (int k = 0; k < m.nsp; ++k)
     if (!(m.W[k] > 0.0)) { err = "non-positive molar mass"; return false; }
   return true;
@@ -558,6 +569,29 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   offs.push_back(put(fall.data(), fall.size() * 8));
   if (plog.empty()) plog.assign(5, 0.0);
   offs.push_back(put(plog.data(), plog.size() * 8));
+  // NASA-7 thermo folded per species and range (kNasaStride doubles each,
+  // low range first): ln E_k = E1 ln T + T (E2 + T (E3 + T (E4 + T E5))) - E6/T + E0
+  // (the standard-state concentration p0/(R_c T) folded in as for the linear
+  // thermo), h = H0 + T (H1 + T (H2 + T (H3 + T (H4 + T H5)))),
+  // cp = C0 + T (C1 + T (C2 + T (C3 + T C4))), dcp/dT = D0 + T (D1 + T (D2 + T D3)); then Tmid
+  std::vector<double> nasa(size_t(2) * kNasaStride * std::max(nsp, 1) + std::max(nsp, 1), 0.0);
+  if (!hm.nasa.empty()) {
+    for (int k = 0; k < nsp; ++k) {
+      const double* d = hm.nasa.data() + size_t(17) * k;
+      for (int rg = 0; rg < 2; ++rg) {
+        const double* c = d + 3 + 7 * rg;
+        double* o = nasa.data() + (size_t(2) * k + rg) * kNasaStride;
+        o[0] = c[6] - c[0] - std::log(kRc); o[1] = c[0] - 1.0; o[2] = c[1] / 2; o[3] = c[2] / 6; o[4] = c[3] / 12;
+        o[5] = c[4] / 20; o[6] = c[5];
+        o[7] = kR * c[5]; o[8] = kR * c[0]; o[9] = kR * c[1] / 2; o[10] = kR * c[2] / 3; o[11] = kR * c[3] / 4;
+        o[12] = kR * c[4] / 5;
+        o[13] = kR * c[0]; o[14] = kR * c[1]; o[15] = kR * c[2]; o[16] = kR * c[3]; o[17] = kR * c[4];
+        o[18] = kR * c[1]; o[19] = 2 * kR * c[2]; o[20] = 3 * kR * c[3]; o[21] = 4 * kR * c[4];
+      }
+      nasa[size_t(2) * kNasaStride * nsp + k] = d[1];
+    }
+  }
+  offs.push_back(put(nasa.data(), nasa.size() * 8));
   // store offsets as fake pointers; relocated after upload
   auto P = [&](int i) { return reinterpret_cast<const double*>(offs[i]); };
   dm.W = P(0); dm.iW = P(1); dm.H0 = P(2); dm.cpa = P(3); dm.hcpb = P(4); dm.cpb = P(5);
@@ -578,6 +612,10 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   dm.kB0 = P(26); dm.kB1 = P(27); dm.kB2 = P(28);
   dm.fall = P(29);
   dm.plog = P(30);
+  dm.nasa = hm.nasa.empty() ? nullptr : P(31);
+  dm.nasa_tmid = hm.nasa.empty() ? nullptr : P(31) + 2 * kNasaStride * nsp;
+  dm.nplog = 0;
+  for (const auto& x : hm.rx) dm.nplog += x.plog.empty() ? 0 : 1;
   return true;
 }
 
@@ -603,6 +641,10 @@ void relocate(DevMech& dm, void* base) {
   dm.kB0 = reloc(dm.kB0, base); dm.kB1 = reloc(dm.kB1, base); dm.kB2 = reloc(dm.kB2, base);
   dm.fall = reloc(dm.fall, base);
   dm.plog = reloc(dm.plog, base);
+  if (dm.nasa) {
+    dm.nasa = reloc(dm.nasa, base);
+    dm.nasa_tmid = reloc(dm.nasa_tmid, base);
+  }
 }
 
 int configure_launch(dlbchem_ctx* c) {
@@ -625,14 +667,14 @@ int configure_launch(dlbchem_ctx* c) {
   if (teams < 1) return fail(c, DLBCHEM_BAD_MECH, "mechanism too large: one cell's workspace exceeds shared memory");
   c->teams = teams;
   c->smem_bytes = int(team_bytes * teams) + 80 * 8;   // + the CTA's exp and nu tables
-  e = cudaFuncSetAttribute(dlb::rosenbrock_kernel_ptr(c->wpc), cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
+  e = cudaFuncSetAttribute(dlb::rosenbrock_kernel_ptr(c->wpc, dlb::general_kernel(c->dm)), cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(dlb::gate_kernel_ptr(c->wpc), cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(dlb::rhs_kernel_ptr(c->wpc), cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaFuncSetAttribute");
   int bps = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, dlb::rosenbrock_kernel_ptr(c->wpc), 32 * c->wpc * teams, c->smem_bytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, dlb::rosenbrock_kernel_ptr(c->wpc, dlb::general_kernel(c->dm)), 32 * c->wpc * teams, c->smem_bytes);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (bps < 1) return fail(c, DLBCHEM_BAD_MECH, "integrator kernel cannot be resident with this workspace");
   c->blocks_per_sm = bps;

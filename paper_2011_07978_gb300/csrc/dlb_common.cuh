@@ -72,6 +72,11 @@ struct DevMech {
   // PLOG points, 5 doubles each: ln p (Pa), ln A, beta, Ea/R, and 1 / (ln p of
   // the next point - ln p) (0 for a reaction's last point)
   const double* plog;
+  int nplog;              // PLOG reactions
+  // NASA-7 thermo (nullptr: cp = a + b T through the tables above): per species
+  // and range (low, high) kNasaStride folded coefficients, and each species' Tmid
+  const double* nasa;
+  const double* nasa_tmid;
   const int32_t* eff_sp;
   const double* eff_dm1;
   // Reactions are processed in chunks of CH = team size; per chunk c and
@@ -94,6 +99,12 @@ struct DevMech {
   const double* exptab;   // 2^(j/64), j = 0..63 (staged into shared memory per CTA)
   const double* aW;       // [4][nsp] atoms of element e per gram of species k (a_ek / W_k)
 };
+
+constexpr int kNasaStride = 24;
+
+// The integrator instantiation with PLOG and NASA-7 support runs for
+// mechanisms that have either; the other one for all the rest.
+__host__ __device__ inline bool general_kernel(const DevMech& m) { return m.nplog > 0 || m.nasa != nullptr; }
 
 struct IntegParams {
   double rtol, atol, hmin_frac, dt;
@@ -255,8 +266,15 @@ cudaError_t launch_rosenbrock_w4(unsigned grid, int threads, int smem, cudaStrea
 const void* rosenbrock_kernel_ptr_w1();
 const void* rosenbrock_kernel_ptr_w2();
 const void* rosenbrock_kernel_ptr_w4();
+cudaError_t launch_rosenbrock_w1p(unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
+cudaError_t launch_rosenbrock_w2p(unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
+cudaError_t launch_rosenbrock_w4p(unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
+const void* rosenbrock_kernel_ptr_w1p();
+const void* rosenbrock_kernel_ptr_w2p();
+const void* rosenbrock_kernel_ptr_w4p();
+// the instantiation for a.m (with or without PLOG reactions)
 cudaError_t launch_rosenbrock(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a);
-const void* rosenbrock_kernel_ptr(int wpc);
+const void* rosenbrock_kernel_ptr(int wpc, bool plog);
 cudaError_t launch_check_math(int64_t n, const double* x, const double* tab, double* out, cudaStream_t s);
 cudaError_t launch_fp64_fma_probe(int64_t iters, double* out, int64_t nout, cudaStream_t s);
 cudaError_t launch_map_classify(int64_t n, int nsp, const double* T, const double* Y, const double* Yref,

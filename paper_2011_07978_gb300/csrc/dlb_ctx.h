@@ -33,6 +33,7 @@ struct HostMech {
   int nsp = 0, nrx = 0, nelem = 0;
   std::vector<double> W, a, b, hf, s0;
   std::vector<int> atoms;      // [nsp][nelem]
+  std::vector<double> nasa;    // NASA-7: per species Tlow, Tmid, Thigh, low a1..a7, high a1..a7 (or empty)
   std::vector<HostRxn> rx;
 };
 

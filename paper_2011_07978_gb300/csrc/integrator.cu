@@ -47,6 +47,11 @@ cudaError_t launch_check_math(int64_t n, const double* x, const double* tab, dou
 }
 
 cudaError_t launch_rosenbrock(int wpc, unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a) {
+  if (general_kernel(a.m)) {
+    if (wpc == 1) return launch_rosenbrock_w1p(grid, threads, smem, s, a);
+    if (wpc == 2) return launch_rosenbrock_w2p(grid, threads, smem, s, a);
+    return launch_rosenbrock_w4p(grid, threads, smem, s, a);
+  }
   if (wpc == 1) return launch_rosenbrock_w1(grid, threads, smem, s, a);
   if (wpc == 2) return launch_rosenbrock_w2(grid, threads, smem, s, a);
   return launch_rosenbrock_w4(grid, threads, smem, s, a);
@@ -72,7 +77,8 @@ const void* gate_kernel_ptr(int wpc) {
   return wpc == 1 ? gate_kernel_ptr_w1() : (wpc == 2 ? gate_kernel_ptr_w2() : gate_kernel_ptr_w4());
 }
 
-const void* rosenbrock_kernel_ptr(int wpc) {
+const void* rosenbrock_kernel_ptr(int wpc, bool plog) {
+  if (plog) return wpc == 1 ? rosenbrock_kernel_ptr_w1p() : (wpc == 2 ? rosenbrock_kernel_ptr_w2p() : rosenbrock_kernel_ptr_w4p());
   return wpc == 1 ? rosenbrock_kernel_ptr_w1() : (wpc == 2 ? rosenbrock_kernel_ptr_w2() : rosenbrock_kernel_ptr_w4());
 }
 

@@ -191,6 +191,30 @@ __device__ __forceinline__ double rcp_nr(double d) {
   return fma(r, fma(e, e, e), r);
 }
 
+// NASA-7 folded coefficients of species k for temperature T (low range below
+// its Tmid, high range from Tmid up): [0..6] ln E_k, [7..12] h, [13..17] cp,
+// [18..21] dcp/dT (see the table builder).
+__device__ __forceinline__ const double* nasa_set(const DevMech& m, int k, double T) {
+  return m.nasa + (2 * size_t(k) + (T < m.nasa_tmid[k] ? 0 : 1)) * kNasaStride;
+}
+// molar cp_k(T) and d cp_k / dT: NASA-7 in the general instantiation, else a + b T
+template <bool GEN>
+__device__ __forceinline__ double cp_of(const DevMech& m, int k, double T) {
+  if (GEN && m.nasa) {
+    const double* a = nasa_set(m, k, T);
+    return fma(T, fma(T, fma(T, fma(T, a[17], a[16]), a[15]), a[14]), a[13]);
+  }
+  return fma(m.cpb[k], T, m.cpa[k]);
+}
+template <bool GEN>
+__device__ __forceinline__ double dcp_of(const DevMech& m, int k, double T) {
+  if (GEN && m.nasa) {
+    const double* a = nasa_set(m, k, T);
+    return fma(T, fma(T, fma(T, a[21], a[20]), a[19]), a[18]);
+  }
+  return m.cpb[k];
+}
+
 // ---------------------------------------------------------------------------
 // Rates. Species pass: concentrations c_k = rho Y_k / W_k, E_k =
 // exp(-g_k/RT) p0/(R_c T) (the standard-state concentration folded in, so
@@ -285,13 +309,22 @@ __device__ __forceinline__ void plog_params(const DevMech& m, const RxnMeta& mt,
   }
 }
 
-template <bool JAC>
+// GEN: the general instantiation (mechanisms with PLOG reactions or NASA-7
+// thermo); in the other one the parameters come straight from the tables.
+template <bool JAC, bool GEN>
 __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mix& mx, int r, int rl, double* qdst) {
   const RxnMeta mt = m.meta[r];
-  double lnA = m.lnA[r], beta = m.beta[r], EaR = m.EaR[r];
-  const bool plog = (mt.flags & RX_PLOG) != 0;
-  if (plog) plog_params(m, mt, mx.lnp, lnA, beta, EaR);
-  double kf = exp_tab(fma(beta, mx.lnT, fma(-EaR, mx.iT, lnA)), w.exptab);
+  double lnA = 0.0, beta = 0.0, EaR = 0.0;
+  bool plog = false;
+  double kf;
+  if (GEN) {
+    lnA = m.lnA[r]; beta = m.beta[r]; EaR = m.EaR[r];
+    plog = (mt.flags & RX_PLOG) != 0;
+    if (plog) plog_params(m, mt, mx.lnp, lnA, beta, EaR);
+    kf = exp_tab(fma(beta, mx.lnT, fma(-EaR, mx.iT, lnA)), w.exptab);
+  } else {
+    kf = exp_tab(fma(m.beta[r], mx.lnT, fma(-m.EaR[r], mx.iT, m.lnA[r])), w.exptab);
+  }
   // expanded slots as fixed registers (unused slots hold 1)
   const double a0 = w.c[mt.sp[0]];
   const double a1 = mt.nr > 1 ? w.c[mt.sp[1]] : 1.0;
@@ -360,15 +393,36 @@ __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mi
   // d q / d T at fixed c: pf d ln k_f / dT - pr d ln k_r / dT, with
   // d ln k_r / dT = d ln k_f / dT - d ln K_c / dT = kB2 / T^2 + kB1 / T + kB0
   // (fall-off adds dfT to both)
+  if (!GEN) {
+    const double dlnkf = fma(m.EaR[r], mx.iT2, m.beta[r] * mx.iT);
+    double dq = pf * dlnkf;
+    if (mt.flags & RX_REV) dq = fma(-pr, fma(m.kB2[r], mx.iT2, fma(m.kB1[r], mx.iT, m.kB0[r])), dq);
+    if (fall) dq = fma(dfT, pf - pr, dq);
+    w.dqdT[rl] = fma(-sig, mx.iT, Mq * dq);
+    w.dlt[rl] = fma(-sig, mx.irS, tb ? stb : 0.0);
+    return;
+  }
   const double dlnkf = fma(EaR, mx.iT2, beta * mx.iT);
   double dq = pf * dlnkf;
   if (mt.flags & RX_REV) {
-    double kB2 = m.kB2[r], kB1 = m.kB1[r];
-    if (plog) {   // the tables' constants hold the reaction record's Ea and beta
-      kB2 += EaR - m.EaR[r];
-      kB1 += beta - m.beta[r];
+    if (m.nasa) {
+      // d ln k_r / dT = d ln k_f / dT - (sum_k nu_k h_k / (R T^2) - dnu / T)
+      // (the expanded slots repeat a species by its coefficient)
+      double dh = w.hk[mt.sp[3]] - w.hk[mt.sp[0]];
+      if (mt.nr > 1) dh -= w.hk[mt.sp[1]];
+      if (mt.nr > 2) dh -= w.hk[mt.sp[2]];
+      if (mt.np > 1) dh += w.hk[mt.sp[4]];
+      if (mt.np > 2) dh += w.hk[mt.sp[5]];
+      const double dlnKc = fma(dh, mx.iT2 * (1.0 / kR), -w.nutab[8 + mt.dnu] * mx.iT);
+      dq = fma(-pr, dlnkf - dlnKc, dq);
+    } else {
+      double kB2 = m.kB2[r], kB1 = m.kB1[r];
+      if (plog) {   // the tables' constants hold the reaction record's Ea and beta
+        kB2 += EaR - m.EaR[r];
+        kB1 += beta - m.beta[r];
+      }
+      dq = fma(-pr, fma(kB2, mx.iT2, fma(kB1, mx.iT, m.kB0[r])), dq);
     }
-    dq = fma(-pr, fma(kB2, mx.iT2, fma(kB1, mx.iT, m.kB0[r])), dq);
   }
   if (fall) dq = fma(dfT, pf - pr, dq);
   // the assembly needs v only inside dwdot/dT - v/T and u - v/(rho S), so the
@@ -377,7 +431,7 @@ __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mi
   w.dlt[rl] = fma(-sig, mx.irS, tb ? stb : 0.0);
 }
 
-template <int WPC, bool JAC>
+template <int WPC, bool JAC, bool GEN>
 __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm, const WS& w, const double* yv,
                                         double P1, double iP1, Mix& mx) {
   constexpr int TS = 32 * WPC;
@@ -402,13 +456,21 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
   mx.T = T; mx.iT = iT; mx.iT2 = iT * iT; mx.lnT = lnT; mx.S = S; mx.rho = rho; mx.irho = irho;
   mx.Ctot = P1 * iT;                          // sum_k c_k (unit efficiencies)
   mx.irS = T * iP1;
-  mx.lnp = w.scal[30];                        // set per cell by the caller
+  if (GEN) mx.lnp = w.scal[30];                // set per cell by the caller
   for (int k = tm.tid; k < nsp; k += TS) {
     w.c[k] = rho * yv[1 + k] * m.iW[k];
-    const double e = exp_tab(fma(m.G2[k], lnT, fma(m.G3[k], T, -fma(m.G0[k], iT, m.G1[k]))), w.exptab);
+    double e;
+    if (GEN && m.nasa) {
+      const double* a = nasa_set(m, k, T);
+      e = exp_tab(fma(a[1], lnT, fma(T, fma(T, fma(T, fma(T, a[5], a[4]), a[3]), a[2]), fma(-a[6], iT, a[0]))),
+                  w.exptab);
+      w.hk[k] = fma(T, fma(T, fma(T, fma(T, fma(T, a[12], a[11]), a[10]), a[9]), a[8]), a[7]);
+    } else {
+      e = exp_tab(fma(m.G2[k], lnT, fma(m.G3[k], T, -fma(m.G0[k], iT, m.G1[k]))), w.exptab);
+      w.hk[k] = fma(T, fma(m.hcpb[k], T, m.cpa[k]), m.H0[k]);
+    }
     w.E[k] = e;
     w.Einv[k] = JAC ? rcp_nr(e) : w.c[k] * rcp_nr(e);   // without the Jacobian: c_k / E_k
-    w.hk[k] = fma(T, fma(m.hcpb[k], T, m.cpa[k]), m.H0[k]);
   }
   if (tm.tid == 0) w.c[nsp] = 0.0;
   if (!JAC) {
@@ -418,7 +480,7 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
     }
     tm.sync();
     double* qa = w.D;
-    for (int r = tm.tid; r < nrx; r += TS) reaction<false>(m, w, mx, r, r, qa);
+    for (int r = tm.tid; r < nrx; r += TS) reaction<false, GEN>(m, w, mx, r, r, qa);
     tm.sync();
     for (int rd = m.incp_all[tm.warp], r1 = m.incp_all[tm.warp + 1]; rd < r1; ++rd) {
       const uint32_t e = m.inc_all[rd * 32 + tm.lane];
@@ -440,7 +502,7 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
   tm.sync();
   for (int c = 0; c < m.nchunks; ++c) {
     const int r = c * m.CH + tm.tid;
-    if (r < nrx) reaction<true>(m, w, mx, r, tm.tid, w.q);
+    if (r < nrx) reaction<true, GEN>(m, w, mx, r, tm.tid, w.q);
     tm.sync();
     const int ci = c * m.wpc + tm.warp;
     for (int rd = m.incp[ci], r1 = m.incp[ci + 1]; rd < r1; ++rd) {
@@ -465,7 +527,7 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
 
 // f = (f_T, f_Y): f_Y_k = W_k wdot_k / rho, f_T = -sum h_k wdot_k / (rho cp_mass).
 // Returns Q = sum h_k wdot_k and cp_mass through the references.
-template <int WPC>
+template <int WPC, bool GEN>
 __device__ __forceinline__ void finish_f(const DevMech& m, const Team<WPC>& tm, const WS& w, const double* yv,
                                          const Mix& mx, bool iso, double* f, double& Q, double& cpm) {
   constexpr int TS = 32 * WPC;
@@ -473,7 +535,7 @@ __device__ __forceinline__ void finish_f(const DevMech& m, const Team<WPC>& tm, 
   for (int k = tm.tid; k < m.nsp; k += TS) {
     f[1 + k] = m.W[k] * w.wdot[k] * mx.irho;
     q = fma(w.hk[k], w.wdot[k], q);
-    cp = fma(yv[1 + k] * m.iW[k], fma(m.cpb[k], mx.T, m.cpa[k]), cp);
+    cp = fma(yv[1 + k] * m.iW[k], cp_of<GEN>(m, k, mx.T), cp);
   }
   tm.sum2(q, cp);
   Q = q;
@@ -482,13 +544,13 @@ __device__ __forceinline__ void finish_f(const DevMech& m, const Team<WPC>& tm, 
   tm.sync();
 }
 
-template <int WPC>
+template <int WPC, bool GEN>
 __device__ __forceinline__ void eval_f(const DevMech& m, const Team<WPC>& tm, const WS& w, const double* yv,
                                        double P1, double iP1, bool iso, double* f) {
   Mix mx;
-  eval_rates<WPC, false>(m, tm, w, yv, P1, iP1, mx);
+  eval_rates<WPC, false, GEN>(m, tm, w, yv, P1, iP1, mx);
   double Q, cpm;
-  finish_f<WPC>(m, tm, w, yv, mx, iso, f, Q, cpm);
+  finish_f<WPC, GEN>(m, tm, w, yv, mx, iso, f, Q, cpm);
 }
 
 // ---------------------------------------------------------------------------
@@ -501,7 +563,7 @@ __device__ __forceinline__ void eval_f(const DevMech& m, const Team<WPC>& tm, co
 // third-body term and v_k = sum_j c_j dwdot_k/dc_j the chain rule through
 // rho(T, Y).
 // ---------------------------------------------------------------------------
-template <int WPC>
+template <int WPC, bool GEN>
 __device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, const WS& w, double P1, double iP1, bool iso,
                                       double ihg) {
   constexpr int TS = 32 * WPC;
@@ -510,16 +572,16 @@ __device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, 
   for (int i = tm.tid; i < ntot; i += TS) w.M[i] = 0.0;   // the Jacobian rounds accumulate into M
   tm.sync();
   Mix mx;
-  eval_rates<WPC, true>(m, tm, w, w.y0, P1, iP1, mx);
+  eval_rates<WPC, true, GEN>(m, tm, w, w.y0, P1, iP1, mx);
   double Q, cpm;
-  finish_f<WPC>(m, tm, w, w.y0, mx, iso, w.f0, Q, cpm);
+  finish_f<WPC, GEN>(m, tm, w, w.y0, mx, iso, w.f0, Q, cpm);
   // scalars for the T row / column
   // dwdT now holds y_k = dwdot_k/dT - v_k/T and uu holds z_k = u_k - v_k/(rho S)
   double hz = 0.0, dc = 0.0, tt = 0.0;
   for (int k = tm.tid; k < nsp; k += TS) {
     hz = fma(w.hk[k], w.uu[k], hz);
-    dc = fma(w.y0[1 + k], m.bW[k], dc);
-    const double cpk = fma(m.cpb[k], mx.T, m.cpa[k]);
+    dc = GEN && m.nasa ? fma(w.y0[1 + k] * m.iW[k], dcp_of<GEN>(m, k, mx.T), dc) : fma(w.y0[1 + k], m.bW[k], dc);
+    const double cpk = cp_of<GEN>(m, k, mx.T);
     tt = fma(cpk, w.wdot[k], fma(w.hk[k], w.dwdT[k], tt));
   }
   tm.sum2(hz, dc);
@@ -540,7 +602,7 @@ __device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, 
   for (int j = tm.tid; j < nsp; j += TS) {
     double hs = 0.0;
     for (int k = 0; k < nsp; ++k) hs = fma(w.Einv[k], w.M[(1 + k) * ld + 1 + j], hs);
-    const double cpj = fma(m.cpb[j], mx.T, m.cpa[j]);
+    const double cpj = cp_of<GEN>(m, j, mx.T);
     const double bracket = fma(Q * cpj, mx.irho * icpm, -fma(Q, irS, Hz));
     const double JT = icpm * fma(m.iW[j], bracket, -hs);
     w.M[1 + j] = iso ? 0.0 : -JT;
@@ -964,7 +1026,7 @@ __device__ __forceinline__ double wrms(const Team<WPC>& tm, const double* v, con
 
 // Starting step (Hairer, Norsett, Wanner, Solving ODEs I, Sec. II.4) with the
 // order-3 error exponent 1/4 and fallbacks scaled by dt. Uses ys, fs, u.
-template <int WPC>
+template <int WPC, bool GEN>
 __device__ double initial_step(const DevMech& m, const Team<WPC>& tm, const WS& w, const IntegParams& P,
                                double P1, double iP1, bool iso) {
   constexpr int TS = 32 * WPC;
@@ -977,7 +1039,7 @@ __device__ double initial_step(const DevMech& m, const Team<WPC>& tm, const WS& 
   h0 = fmin(h0, P.dt);
   for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(h0, w.f0[i], w.y0[i]);
   tm.sync();
-  eval_f<WPC>(m, tm, w, w.ys, P1, iP1, iso, w.fs);
+  eval_f<WPC, GEN>(m, tm, w, w.ys, P1, iP1, iso, w.fs);
   double* df = w.u + N;
   for (int i = tm.tid; i < N; i += TS) df[i] = w.fs[i] - w.f0[i];
   tm.sync();
@@ -989,7 +1051,7 @@ __device__ double initial_step(const DevMech& m, const Team<WPC>& tm, const WS& 
 }
 
 // Integrate one cell over [0, dt] (the oracle's algorithm step for step).
-template <int WPC>
+template <int WPC, bool GEN>
 __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Team<WPC>& tm, const WS& w,
                                int64_t cell, int64_t n, const double* __restrict__ Tin,
                                const double* __restrict__ pin, const double* __restrict__ Yin,
@@ -1000,7 +1062,7 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
   const bool iso = P.isothermal != 0;
   for (int i = tm.tid; i < N; i += TS) w.y0[i] = (i == 0) ? Tin[cell] : Yin[int64_t(i - 1) * n + cell];
   const double p = pin[cell];
-  if (tm.tid == 0) w.scal[30] = log(p);   // ln p for PLOG reactions
+  if (GEN && tm.tid == 0) w.scal[30] = log(p);   // ln p for PLOG reactions
   tm.sync();
   int bad = 0;
   for (int i = tm.tid; i < N; i += TS) bad |= !isfinite(w.y0[i]);
@@ -1010,8 +1072,8 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
   if (!bad) {
     const double P1 = 1e-6 * p / kR;   // p / (R T) = P1 / T in mol/cm^3
     const double iP1 = 1.0 / P1;
-    eval_f<WPC>(m, tm, w, w.y0, P1, iP1, iso, w.f0);
-    double h = initial_step<WPC>(m, tm, w, P, P1, iP1, iso);
+    eval_f<WPC, GEN>(m, tm, w, w.y0, P1, iP1, iso, w.f0);
+    double h = initial_step<WPC, GEN>(m, tm, w, P, P1, iP1, iso);
     const double dt = P.dt;
     double t = 0.0;
     bool rejected_last = false;
@@ -1026,7 +1088,7 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
       if (h < P.hmin_frac * dt) { status = CELL_H_UNDERFLOW; break; }
       ++steps;
       const double ih = rcp_nr(h);
-      assemble<WPC>(m, tm, w, P1, iP1, iso, ih * (1.0 / kGamma));
+      assemble<WPC, GEN>(m, tm, w, P1, iP1, iso, ih * (1.0 / kGamma));
       bool mixed = P.precision == 1 && w.g != nullptr;   // no scratch: FP64
       bool ok;
       const int ld = m.ld;
@@ -1062,14 +1124,14 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
         // stage 2
         for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(kA21, u1[i], w.y0[i]);
         tm.sync();
-        eval_f<WPC>(m, tm, w, w.ys, P1, iP1, iso, w.fs);
+        eval_f<WPC, GEN>(m, tm, w, w.ys, P1, iP1, iso, w.fs);
         for (int i = tm.tid; i < N; i += TS) w.fs[i] = fma(kC21 * ih, u1[i], w.fs[i]);
         tm.sync();
         solve(w.fs, u2);
         // stage 3
         for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(kA31, u1[i], fma(kA32, u2[i], w.y0[i]));
         tm.sync();
-        eval_f<WPC>(m, tm, w, w.ys, P1, iP1, iso, w.fs);
+        eval_f<WPC, GEN>(m, tm, w, w.ys, P1, iP1, iso, w.fs);
         for (int i = tm.tid; i < N; i += TS) w.ys[i] = fma(ih, fma(kC31, u1[i], kC32 * u2[i]), w.fs[i]);
         tm.sync();
         solve(w.ys, u3);
@@ -1125,7 +1187,10 @@ __device__ void integrate_cell(const DevMech& m, const IntegParams& P, const Tea
 }
 
 
-template <int WPC>
+// GEN: the mechanism has PLOG reactions or NASA-7 thermo (a separate
+// instantiation, so that the rate evaluation of every other mechanism is
+// unchanged)
+template <int WPC, bool GEN>
 __global__ void __launch_bounds__(128, WPC == 1 ? 4 : (WPC == 2 ? 3 : 2)) rosenbrock_kernel(const KernelArgs a) {
   extern __shared__ __align__(16) double smem[];
   constexpr int TS = 32 * WPC;
@@ -1161,7 +1226,7 @@ __global__ void __launch_bounds__(128, WPC == 1 ? 4 : (WPC == 2 ? 3 : 2)) rosenb
       md = a.mesh[mi];
       P.dt = md.dt;
     }
-    integrate_cell<WPC>(a.m, P, tm, w, cell, md.n, md.T, md.p, md.Y, md.Tout, md.Yout, md.steps, md.status,
+    integrate_cell<WPC, GEN>(a.m, P, tm, w, cell, md.n, md.T, md.p, md.Y, md.Tout, md.Yout, md.steps, md.status,
                         a.fallbacks);
   };
   // One call site of run() for both schedules: a second inlined copy of the
@@ -1242,7 +1307,7 @@ __global__ void __launch_bounds__(128) gate_kernel(const GateArgs a) {
     if (tm.any(bad)) continue;
     const double P1 = 1e-6 * p / kR;
     const double iP1 = 1.0 / P1;
-    eval_f<WPC>(m, tm, w, w.y0, P1, iP1, a.P.isothermal != 0, w.f0);
+    eval_f<WPC, true>(m, tm, w, w.y0, P1, iP1, a.P.isothermal != 0, w.f0);
     // candidates: the network's proposal; with residual, the explicit Euler
     // step plus the network's correction, then the Euler step alone, then
     // the zero increment (a nearly inert cell)
@@ -1259,7 +1324,7 @@ __global__ void __launch_bounds__(128) gate_kernel(const GateArgs a) {
       for (int i = tm.tid; i < N; i += TS) bad |= !isfinite(w.ys[i]);
       bad |= !(w.ys[0] > 0.0);
       if (tm.any(bad)) continue;
-      eval_f<WPC>(m, tm, w, w.ys, P1, iP1, a.P.isothermal != 0, w.fs);
+      eval_f<WPC, true>(m, tm, w, w.ys, P1, iP1, a.P.isothermal != 0, w.fs);
       const double hdt = 0.5 * a.P.dt;
       // trapezoid defect, realizability (no mass fraction below -gate) and a
       // stiffness guard: dt |f(y') - f(y)| may not exceed |y' - y| + 2 gate
@@ -1363,7 +1428,7 @@ __global__ void __launch_bounds__(128) rhs_kernel(const RhsArgs a) {
       continue;
     }
     const double P1 = 1e-6 * p / kR;
-    eval_f<WPC>(a.m, tm, w, w.y0, P1, 1.0 / P1, a.isothermal != 0, w.f0);
+    eval_f<WPC, true>(a.m, tm, w, w.y0, P1, 1.0 / P1, a.isothermal != 0, w.f0);
     for (int i = tm.tid; i < N; i += TS) {
       if (i == 0) a.fT[cell] = w.f0[0];
       else a.fY[int64_t(i - 1) * n + cell] = w.f0[i];

@@ -4,11 +4,11 @@
 namespace dlb {
 
 cudaError_t launch_rosenbrock_w1(unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a) {
-  rosenbrock_kernel<1><<<grid, threads, smem, s>>>(a);
+  rosenbrock_kernel<1, false><<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-const void* rosenbrock_kernel_ptr_w1() { return reinterpret_cast<const void*>(&rosenbrock_kernel<1>); }
+const void* rosenbrock_kernel_ptr_w1() { return reinterpret_cast<const void*>(&rosenbrock_kernel<1, false>); }
 
 const void* gate_kernel_ptr_w1() { return reinterpret_cast<const void*>(&gate_kernel<1>); }
 

@@ -4,11 +4,11 @@
 namespace dlb {
 
 cudaError_t launch_rosenbrock_w4(unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a) {
-  rosenbrock_kernel<4><<<grid, threads, smem, s>>>(a);
+  rosenbrock_kernel<4, false><<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-const void* rosenbrock_kernel_ptr_w4() { return reinterpret_cast<const void*>(&rosenbrock_kernel<4>); }
+const void* rosenbrock_kernel_ptr_w4() { return reinterpret_cast<const void*>(&rosenbrock_kernel<4, false>); }
 
 const void* gate_kernel_ptr_w4() { return reinterpret_cast<const void*>(&gate_kernel<4>); }
 

@@ -1,0 +1,14 @@
+// The batched Rosenbrock integrator with 4 warps per cell for mechanisms with PLOG
+// reactions or NASA-7 thermo (see integrator_impl.cuh).
+#include "integrator_impl.cuh"
+
+namespace dlb {
+
+cudaError_t launch_rosenbrock_w4p(unsigned grid, int threads, int smem, cudaStream_t s, const KernelArgs& a) {
+  rosenbrock_kernel<4, true><<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+const void* rosenbrock_kernel_ptr_w4p() { return reinterpret_cast<const void*>(&rosenbrock_kernel<4, true>); }
+
+}  // namespace dlb

@@ -36,6 +36,16 @@ The layout is little-endian:
         linear in ln p; below the first or above the last listed pressure it
         is that point's Arrhenius form. The reaction record's own lnA, beta,
         Ea are not used. A PLOG reaction is neither third-body nor fall-off.
+    optional NASA-7 thermo section (then the cp_a, cp_b, hf, s0 arrays
+    above are not used):
+        char[8] "NASA7001", then per species 17 f64: Tlow, Tmid, Thigh, the
+        low-range coefficients a1..a7 (T < Tmid) and the high-range ones
+        (T >= Tmid), with cp/R = a1 + a2 T + a3 T^2 + a4 T^3 + a5 T^4,
+        h/(R T) = a1 + a2 T/2 + a3 T^2/3 + a4 T^3/4 + a5 T^4/5 + a6/T,
+        s/R = a1 ln T + a2 T + a3 T^2/2 + a4 T^3/3 + a5 T^4/4 + a7
+        (s at p0 = 1 atm, T in K). Outside [Tlow, Thigh] the nearer range's
+        polynomials are used as they are.
+    The optional sections may appear in any order, each at most once.
 
 Each species appears at most once per side; its integer coefficient is in
 rnu / pnu.
@@ -70,6 +80,7 @@ class Mechanism:
     eff: list = dataclasses.field(default_factory=list)  # (rxn, species, eff)
     falloff: list = dataclasses.field(default_factory=list)  # (rxn, kind, lnA0, beta0, Ea0, a, T3, T1, T2)
     plog: list = dataclasses.field(default_factory=list)     # (rxn, [(p_Pa, lnA, beta, Ea), ...])
+    nasa: np.ndarray = None      # [nsp, 17] Tlow, Tmid, Thigh, low a1..a7, high a1..a7, or None
 
     @property
     def nsp(self) -> int:
@@ -134,6 +145,12 @@ def write_mech(path: str, m: Mechanism) -> None:
                 f.write(struct.pack("<2i", j, len(pts)))
                 for q in pts:
                     f.write(struct.pack("<4d", *[float(x) for x in q]))
+        if m.nasa is not None:
+            nasa = np.asarray(m.nasa, dtype="<f8")
+            if nasa.shape != (nsp, 17) or not (nasa[:, 1] > 0).all():
+                raise ValueError("NASA-7 data: [nsp, 17] with positive Tmid")
+            f.write(b"NASA7001")
+            f.write(nasa.tobytes())
 
 
 def read_mech(path: str) -> Mechanism:
@@ -165,23 +182,30 @@ def read_mech(path: str) -> Mechanism:
         j, k, e = struct.unpack_from("<2id", buf, off)
         off += 16
         eff.append((j, k, e))
-    falloff, plog = [], []
-    if len(buf) >= off + 12 and buf[off:off + 8] == b"FALLOFF1":
-        (nf,) = struct.unpack_from("<i", buf, off + 8)
-        off += 12
-        for _ in range(nf):
-            rec = struct.unpack_from("<2i7d", buf, off)
-            off += 64
-            falloff.append(tuple(rec))
-    if len(buf) >= off + 12 and buf[off:off + 8] == b"PLOG0001":
-        (npl,) = struct.unpack_from("<i", buf, off + 8)
-        off += 12
-        for _ in range(npl):
-            j, n = struct.unpack_from("<2i", buf, off)
-            off += 8
-            pts = [struct.unpack_from("<4d", buf, off + 32 * i) for i in range(n)]
-            off += 32 * n
-            plog.append((j, [tuple(q) for q in pts]))
+    falloff, plog, nasa = [], [], None
+    while len(buf) >= off + 8:
+        tag = buf[off:off + 8]
+        off += 8
+        if tag == b"FALLOFF1":
+            (nf,) = struct.unpack_from("<i", buf, off)
+            off += 4
+            for _ in range(nf):
+                falloff.append(tuple(struct.unpack_from("<2i7d", buf, off)))
+                off += 64
+        elif tag == b"PLOG0001":
+            (npl,) = struct.unpack_from("<i", buf, off)
+            off += 4
+            for _ in range(npl):
+                j, n = struct.unpack_from("<2i", buf, off)
+                off += 8
+                pts = [struct.unpack_from("<4d", buf, off + 32 * i) for i in range(n)]
+                off += 32 * n
+                plog.append((j, [tuple(q) for q in pts]))
+        elif tag == b"NASA7001":
+            nasa = np.frombuffer(buf, dtype="<f8", count=17 * nsp, offset=off).reshape(nsp, 17).copy()
+            off += 8 * 17 * nsp
+        else:
+            raise ValueError(f"{path}: unknown section {tag!r}")
     return Mechanism(W=arrs[0], cp_a=arrs[1], cp_b=arrs[2], hf=arrs[3], s0=arrs[4], atoms=atoms,
                      lnA=np.array(lnA), beta=np.array(beta), Ea=np.array(Ea), reac=reac, prod=prod,
-                     reversible=np.array(rev), thirdbody=np.array(tb), eff=eff, falloff=falloff, plog=plog)
+                     reversible=np.array(rev), thirdbody=np.array(tb), eff=eff, falloff=falloff, plog=plog, nasa=nasa)

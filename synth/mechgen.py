@@ -203,3 +203,55 @@ def with_plog(m: Mechanism, seed: int, frac: float = 0.15) -> Mechanism:
     out.plog = plog
     return out
 
+
+
+def nasa7_of_linear(m: Mechanism, Tmid: float = 1000.0) -> np.ndarray:
+    """NASA-7 data [nsp, 17] that reproduce m's linear thermo exactly
+    (cp = a + b T, h(T0) = hf, s(T0) = s0; both ranges the same)."""
+    R, T0 = 8.314462618, 298.15
+    out = np.zeros((m.nsp, 17))
+    for k in range(m.nsp):
+        a1, a2 = m.cp_a[k] / R, m.cp_b[k] / R
+        a6 = T0 * (m.hf[k] / (R * T0) - a1 - a2 * T0 / 2)
+        a7 = m.s0[k] / R - a1 * np.log(T0) - a2 * T0
+        c = [a1, a2, 0.0, 0.0, 0.0, a6, a7]
+        out[k] = [200.0, Tmid, 6000.0, *c, *c]
+    return out
+
+
+def with_nasa7(m: Mechanism, seed: int) -> Mechanism:
+    """A copy of m with NASA-7 thermo: each species keeps h(T0) = hf and
+    s(T0) = s0 and its linear cp plus curvature, cp/R += a3 T^2 + a4 T^3 +
+    a5 T^4 with a3 ~ U[-2e-7, 2e-7], a4 ~ U[-5e-11, 5e-11], a5 ~ U[-5e-15, 5e-15]
+    below Tmid (a few tenths of cp/R at 3000 K); above Tmid a3 changes by U[-1e-7, 1e-7] and a1 so that cp
+    is continuous at Tmid, and a6, a7 so that h and s are. Tmid is 1000 K for
+    most species and 1200 K for every fifth. (Stand-in for real
+    mechanisms' NASA-7 data, which is not available here.)"""
+    import copy
+    R, T0 = 8.314462618, 298.15
+    rng = np.random.default_rng(seed + 9090)
+    out = copy.deepcopy(m)
+    nasa = np.zeros((m.nsp, 17))
+
+    def poly_h(c, T):   # h/(R T) without the a6 term
+        return c[0] + c[1] * T / 2 + c[2] * T ** 2 / 3 + c[3] * T ** 3 / 4 + c[4] * T ** 4 / 5
+
+    def poly_s(c, T):   # s/R without a7
+        return c[0] * np.log(T) + c[1] * T + c[2] * T ** 2 / 2 + c[3] * T ** 3 / 3 + c[4] * T ** 4 / 4
+
+    for k in range(m.nsp):
+        Tmid = 1200.0 if k % 5 == 4 else 1000.0
+        lo = np.zeros(7)
+        lo[0], lo[1] = m.cp_a[k] / R, m.cp_b[k] / R
+        lo[2:5] = rng.uniform(-2e-7, 2e-7), rng.uniform(-5e-11, 5e-11), rng.uniform(-5e-15, 5e-15)
+        lo[5] = T0 * (m.hf[k] / (R * T0) - poly_h(lo, T0))
+        lo[6] = m.s0[k] / R - poly_s(lo, T0)
+        hi = lo.copy()
+        g = rng.uniform(-1e-7, 1e-7)
+        hi[2] += g
+        hi[0] -= g * Tmid ** 2
+        hi[5] = lo[5] + Tmid * (poly_h(lo, Tmid) - poly_h(hi, Tmid))
+        hi[6] = lo[6] + poly_s(lo, Tmid) - poly_s(hi, Tmid)
+        nasa[k] = [200.0, Tmid, 6000.0, *lo, *hi]
+    out.nasa = nasa
+    return out

@@ -296,15 +296,16 @@ def test_gate_accept_branch_with_a_host_built_network():
 
 def test_rhs_matches_oracle():
     """dlbchem_rhs against the oracle's right-hand side, cell by cell, on the
-    10- and the 53-species mechanisms and fall-off and PLOG variants of the
-    10-species one at 0.01 to 300 bar. The two sides evaluate rates, thermo
+    10- and the 53-species mechanisms, fall-off and PLOG variants of the
+    10-species one at 0.01 to 300 bar, and a NASA-7 variant of the 53-species
+    one. The two sides evaluate rates, thermo
     and f in different orders, so they agree to rounding of the terms that
     make up each component: for f_Y_k the scale is W_k / rho times the sum of
     |nu_kr| [M]_r (forward_r + reverse_r) over the reactions (near
     equilibrium those cancel), for f_T that scale times |h_k| / cp."""
     d = lib()
     import tempfile
-    from synth import with_falloff, with_plog, write_mech
+    from synth import with_falloff, with_nasa7, with_plog, write_mech
     fall = tempfile.NamedTemporaryFile(suffix=".bin", delete=False).name
     write_mech(fall, with_falloff(read_mech(states.mech_path(10, 20, 0)), 0))
     plog = tempfile.NamedTemporaryFile(suffix=".bin", delete=False).name
@@ -313,8 +314,11 @@ def test_rhs_matches_oracle():
     pf = np.geomspace(1e3, 1e7, 300)
     Tp, pp, Yp = states.uniform_states(10, 300, 7)
     pp = np.geomspace(3e3, 3e7, 300)
+    nasa = tempfile.NamedTemporaryFile(suffix=".bin", delete=False).name
+    write_mech(nasa, with_nasa7(read_mech(states.mech_path(53, 325, 0)), 0))
     for mech, (T, p, Y) in ((states.mech_path(10, 20, 0), states.uniform_states(10, 500, 3)),
                             (fall, (Tf, pf, Yf)), (plog, (Tp, pp, Yp)),
+                            (nasa, states.bimodal_states(53, 325, 400, 5)[:3]),
                             (states.mech_path(53, 325, 0), states.bimodal_states(53, 325, 600, 4)[:3])):
         ctx = d.Context(mech)
         dd = lambda a: torch.tensor(np.ascontiguousarray(a), device=DEV)

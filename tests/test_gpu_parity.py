@@ -605,3 +605,36 @@ def test_plog_mechanism_parity(tmp_path, which):
     assert (g[3] == 0).all()
     dT, dY, frac = assert_parity(g, o, min_tight=0.99, tight_ref=tight[:2])
     print(f"PLOG {which}: max dT/T {dT:.2e}, max dY {dY:.2e}, within 1e-9 {frac:.4f}")
+
+
+@pytest.mark.parametrize("which", ["c1", "c2", "c1_all"])
+def test_nasa7_mechanism_parity(tmp_path, which):
+    """NASA-7 thermo (two ranges, Tmid 1000 K and 1200 K, curvature up to
+    T^4) on the 10- and 53-species mechanisms, and on the 10-species one with
+    fall-off and PLOG reactions as well: GPU against the oracle, bar and
+    rounding-sensitive criterion as in the fall-off test."""
+    from synth import read_mech, with_falloff, with_nasa7, with_plog, write_mech
+    nsp, nrx = (53, 325) if which == "c2" else (10, 20)
+    m = with_nasa7(read_mech(states.mech_path(nsp, nrx, 0)), 0)
+    if which == "c1_all":
+        m = with_plog(with_falloff(m, 0), 0, frac=0.5)
+        assert m.falloff and m.plog
+    path = str(tmp_path / f"{which}_nasa.bin")
+    write_mech(path, m)
+    if which == "c2":
+        T, p, Y, cls = states.bimodal_states(53, 325, 400, 10)
+        dt, rtol, atol = 1e-5, 1e-5, 1e-8
+    else:
+        T, p, Y = states.uniform_states(10, 400, 10)
+        dt, rtol, atol = 1e-6, 1e-8, 1e-12
+        if which == "c1_all":
+            p = np.geomspace(3e3, 3e7, T.size)[np.random.default_rng(3).permutation(T.size)]
+    ctx = dlb().Context(path, rtol=rtol, atol=atol, schedule=dlb().SCHED_QUEUE)
+    g = run_gpu(ctx, T, p, Y, dt)
+    orc = oracle.Oracle(path)
+    o = orc.integrate(T, p, Y, dt, rtol=rtol, atol=atol)
+    tight = orc.integrate(T, p, Y, dt, rtol=rtol * 1e-3, atol=atol * 1e-4)
+    assert (g[3] == 0).all()
+    assert (np.abs(o[0] - T) > 1.0).mean() > 0.1          # heat release exercises h(T) and cp(T)
+    dT, dY, frac = assert_parity(g, o, min_tight=0.99, tight_ref=tight[:2])
+    print(f"NASA-7 {which}: max dT/T {dT:.2e}, max dY {dY:.2e}, within 1e-9 {frac:.4f}")

@@ -575,9 +575,30 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   // thermo), h = H0 + T (H1 + T (H2 + T (H3 + T (H4 + T H5)))),
   // cp = C0 + T (C1 + T (C2 + T (C3 + T C4))), dcp/dT = D0 + T (D1 + T (D2 + T D3)); then Tmid
   std::vector<double> nasa(size_t(2) * kNasaStride * std::max(nsp, 1) + std::max(nsp, 1), 0.0);
-  if (!hm.nasa.empty()) {
+  int nplog = 0;
+  for (const auto& x : hm.rx) nplog += x.plog.empty() ? 0 : 1;
+  // the general instantiation (PLOG or NASA-7) and the gate and right-hand-side
+  // kernels always read NASA-7 tables: a linear-cp mechanism gets its exact
+  // NASA-7 form (a1 = a/R, a2 = b/R, a6 and a7 from hf and s0 at T0, both
+  // ranges alike)
+  std::vector<double> lin_nasa;
+  const std::vector<double>* src = &hm.nasa;
+  if (hm.nasa.empty()) {
+    lin_nasa.assign(size_t(17) * nsp, 0.0);
     for (int k = 0; k < nsp; ++k) {
-      const double* d = hm.nasa.data() + size_t(17) * k;
+      double* d = lin_nasa.data() + size_t(17) * k;
+      const double a1 = hm.a[k] / kR, a2 = hm.b[k] / kR;
+      const double a6 = kT0 * (hm.hf[k] / (kR * kT0) - a1 - a2 * kT0 / 2);
+      const double a7 = hm.s0[k] / kR - a1 * std::log(kT0) - a2 * kT0;
+      const double c[7] = {a1, a2, 0.0, 0.0, 0.0, a6, a7};
+      d[0] = 200.0; d[1] = 1000.0; d[2] = 6000.0;
+      for (int i = 0; i < 7; ++i) d[3 + i] = d[10 + i] = c[i];
+    }
+    src = &lin_nasa;
+  }
+  {
+    for (int k = 0; k < nsp; ++k) {
+      const double* d = src->data() + size_t(17) * k;
       for (int rg = 0; rg < 2; ++rg) {
         const double* c = d + 3 + 7 * rg;
         double* o = nasa.data() + (size_t(2) * k + rg) * kNasaStride;
@@ -612,10 +633,10 @@ bool build_tables(const dlb::HostMech& hm, int wpc, std::vector<unsigned char>& 
   dm.kB0 = P(26); dm.kB1 = P(27); dm.kB2 = P(28);
   dm.fall = P(29);
   dm.plog = P(30);
-  dm.nasa = hm.nasa.empty() ? nullptr : P(31);
-  dm.nasa_tmid = hm.nasa.empty() ? nullptr : P(31) + 2 * kNasaStride * nsp;
-  dm.nplog = 0;
-  for (const auto& x : hm.rx) dm.nplog += x.plog.empty() ? 0 : 1;
+  dm.nplog = nplog;
+  dm.nasa_file = hm.nasa.empty() ? 0 : 1;
+  dm.nasa = P(31);
+  dm.nasa_tmid = P(31) + 2 * kNasaStride * nsp;
   return true;
 }
 
@@ -641,10 +662,8 @@ void relocate(DevMech& dm, void* base) {
   dm.kB0 = reloc(dm.kB0, base); dm.kB1 = reloc(dm.kB1, base); dm.kB2 = reloc(dm.kB2, base);
   dm.fall = reloc(dm.fall, base);
   dm.plog = reloc(dm.plog, base);
-  if (dm.nasa) {
-    dm.nasa = reloc(dm.nasa, base);
-    dm.nasa_tmid = reloc(dm.nasa_tmid, base);
-  }
+  dm.nasa = reloc(dm.nasa, base);
+  dm.nasa_tmid = reloc(dm.nasa_tmid, base);
 }
 
 int configure_launch(dlbchem_ctx* c) {

@@ -73,8 +73,11 @@ struct DevMech {
   // the next point - ln p) (0 for a reaction's last point)
   const double* plog;
   int nplog;              // PLOG reactions
-  // NASA-7 thermo (nullptr: cp = a + b T through the tables above): per species
-  // and range (low, high) kNasaStride folded coefficients, and each species' Tmid
+  int nasa_file;          // the mechanism's thermo is NASA-7 (else cp = a + b T)
+  // NASA-7 thermo for every mechanism (a linear-cp one in its exact NASA-7
+  // form), read by the general instantiation and the gate and right-hand-side
+  // kernels: per species and range (low, high) kNasaStride folded coefficients,
+  // then each species' Tmid
   const double* nasa;
   const double* nasa_tmid;
   const int32_t* eff_sp;
@@ -104,7 +107,7 @@ constexpr int kNasaStride = 24;
 
 // The integrator instantiation with PLOG and NASA-7 support runs for
 // mechanisms that have either; the other one for all the rest.
-__host__ __device__ inline bool general_kernel(const DevMech& m) { return m.nplog > 0 || m.nasa != nullptr; }
+__host__ __device__ inline bool general_kernel(const DevMech& m) { return m.nplog > 0 || m.nasa_file != 0; }
 
 struct IntegParams {
   double rtol, atol, hmin_frac, dt;

@@ -193,14 +193,14 @@ __device__ __forceinline__ double rcp_nr(double d) {
 
 // NASA-7 folded coefficients of species k for temperature T (low range below
 // its Tmid, high range from Tmid up): [0..6] ln E_k, [7..12] h, [13..17] cp,
-// [18..21] dcp/dT (see the table builder).
+// [18..21] dcp/dT (see the table builder). Present for every mechanism.
 __device__ __forceinline__ const double* nasa_set(const DevMech& m, int k, double T) {
   return m.nasa + (2 * size_t(k) + (T < m.nasa_tmid[k] ? 0 : 1)) * kNasaStride;
 }
 // molar cp_k(T) and d cp_k / dT: NASA-7 in the general instantiation, else a + b T
 template <bool GEN>
 __device__ __forceinline__ double cp_of(const DevMech& m, int k, double T) {
-  if (GEN && m.nasa) {
+  if (GEN) {
     const double* a = nasa_set(m, k, T);
     return fma(T, fma(T, fma(T, fma(T, a[17], a[16]), a[15]), a[14]), a[13]);
   }
@@ -208,7 +208,7 @@ __device__ __forceinline__ double cp_of(const DevMech& m, int k, double T) {
 }
 template <bool GEN>
 __device__ __forceinline__ double dcp_of(const DevMech& m, int k, double T) {
-  if (GEN && m.nasa) {
+  if (GEN) {
     const double* a = nasa_set(m, k, T);
     return fma(T, fma(T, fma(T, a[21], a[20]), a[19]), a[18]);
   }
@@ -405,24 +405,17 @@ __device__ __forceinline__ void reaction(const DevMech& m, const WS& w, const Mi
   const double dlnkf = fma(EaR, mx.iT2, beta * mx.iT);
   double dq = pf * dlnkf;
   if (mt.flags & RX_REV) {
-    if (m.nasa) {
-      // d ln k_r / dT = d ln k_f / dT - (sum_k nu_k h_k / (R T^2) - dnu / T)
-      // (the expanded slots repeat a species by its coefficient)
-      double dh = w.hk[mt.sp[3]] - w.hk[mt.sp[0]];
-      if (mt.nr > 1) dh -= w.hk[mt.sp[1]];
-      if (mt.nr > 2) dh -= w.hk[mt.sp[2]];
-      if (mt.np > 1) dh += w.hk[mt.sp[4]];
-      if (mt.np > 2) dh += w.hk[mt.sp[5]];
-      const double dlnKc = fma(dh, mx.iT2 * (1.0 / kR), -w.nutab[8 + mt.dnu] * mx.iT);
-      dq = fma(-pr, dlnkf - dlnKc, dq);
-    } else {
-      double kB2 = m.kB2[r], kB1 = m.kB1[r];
-      if (plog) {   // the tables' constants hold the reaction record's Ea and beta
-        kB2 += EaR - m.EaR[r];
-        kB1 += beta - m.beta[r];
-      }
-      dq = fma(-pr, fma(kB2, mx.iT2, fma(kB1, mx.iT, m.kB0[r])), dq);
-    }
+    // d ln k_r / dT = d ln k_f / dT - (sum_k nu_k h_k / (R T^2) - dnu / T)
+    // (the expanded slots repeat a species by its coefficient); with the
+    // participants' h_k instead of per-reaction constants, since species
+    // can switch NASA-7 range at different temperatures
+    double dh = w.hk[mt.sp[3]] - w.hk[mt.sp[0]];
+    if (mt.nr > 1) dh -= w.hk[mt.sp[1]];
+    if (mt.nr > 2) dh -= w.hk[mt.sp[2]];
+    if (mt.np > 1) dh += w.hk[mt.sp[4]];
+    if (mt.np > 2) dh += w.hk[mt.sp[5]];
+    const double dlnKc = fma(dh, mx.iT2 * (1.0 / kR), -w.nutab[8 + mt.dnu] * mx.iT);
+    dq = fma(-pr, dlnkf - dlnKc, dq);
   }
   if (fall) dq = fma(dfT, pf - pr, dq);
   // the assembly needs v only inside dwdot/dT - v/T and u - v/(rho S), so the
@@ -459,16 +452,18 @@ __device__ __forceinline__ void eval_rates(const DevMech& m, const Team<WPC>& tm
   if (GEN) mx.lnp = w.scal[30];                // set per cell by the caller
   for (int k = tm.tid; k < nsp; k += TS) {
     w.c[k] = rho * yv[1 + k] * m.iW[k];
-    double e;
-    if (GEN && m.nasa) {
+    // the general instantiation always has NASA-7 tables (a linear-cp
+    // mechanism's are its exact NASA-7 form); one call site of exp_tab
+    double arg;
+    if (GEN) {
       const double* a = nasa_set(m, k, T);
-      e = exp_tab(fma(a[1], lnT, fma(T, fma(T, fma(T, fma(T, a[5], a[4]), a[3]), a[2]), fma(-a[6], iT, a[0]))),
-                  w.exptab);
+      arg = fma(a[1], lnT, fma(T, fma(T, fma(T, fma(T, a[5], a[4]), a[3]), a[2]), fma(-a[6], iT, a[0])));
       w.hk[k] = fma(T, fma(T, fma(T, fma(T, fma(T, a[12], a[11]), a[10]), a[9]), a[8]), a[7]);
     } else {
-      e = exp_tab(fma(m.G2[k], lnT, fma(m.G3[k], T, -fma(m.G0[k], iT, m.G1[k]))), w.exptab);
+      arg = fma(m.G2[k], lnT, fma(m.G3[k], T, -fma(m.G0[k], iT, m.G1[k])));
       w.hk[k] = fma(T, fma(m.hcpb[k], T, m.cpa[k]), m.H0[k]);
     }
+    const double e = exp_tab(arg, w.exptab);
     w.E[k] = e;
     w.Einv[k] = JAC ? rcp_nr(e) : w.c[k] * rcp_nr(e);   // without the Jacobian: c_k / E_k
   }
@@ -580,7 +575,7 @@ __device__ __forceinline__ void assemble(const DevMech& m, const Team<WPC>& tm, 
   double hz = 0.0, dc = 0.0, tt = 0.0;
   for (int k = tm.tid; k < nsp; k += TS) {
     hz = fma(w.hk[k], w.uu[k], hz);
-    dc = GEN && m.nasa ? fma(w.y0[1 + k] * m.iW[k], dcp_of<GEN>(m, k, mx.T), dc) : fma(w.y0[1 + k], m.bW[k], dc);
+    dc = GEN ? fma(w.y0[1 + k] * m.iW[k], dcp_of<GEN>(m, k, mx.T), dc) : fma(w.y0[1 + k], m.bW[k], dc);
     const double cpk = cp_of<GEN>(m, k, mx.T);
     tt = fma(cpk, w.wdot[k], fma(w.hk[k], w.dwdT[k], tt));
   }

@@ -46,11 +46,11 @@ METRIC = "chemistry cells/s per dt at stated T/Y error vs FP64 oracle; frac of F
 # FMA lanes per clock per SM x 2 flop (= the 1.25 TFLOP/s nominal figure).
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one FP64 integrator launch
-# from ncu per integrated cell (3,852,544 B read, 0 written, 912 cells
-# integrated on the 8,192-cell bimodal field with bucket mapping), scaled by
-# the cells the benchmark's launch integrates; None whenever the kernel has
-# changed since the capture.
-INTEGRATOR_TRAFFIC_BYTES_PER_CELL = 3852544 / 912
+# (rosenbrock_kernel<2, false>) from ncu per integrated cell (4,040,960 B
+# read, 0 written, 912 cells integrated on the 8,192-cell bimodal field with
+# bucket mapping), scaled by the cells the benchmark's launch integrates; None
+# whenever the kernel has changed since the capture.
+INTEGRATOR_TRAFFIC_BYTES_PER_CELL = 4040960 / 912
 N_F = 3   # function evaluations per Rosenbrock step (stage 4 reuses stage 3's)
 PAPER_CONTEXT = ("paper (DLBFoam, arXiv 2011.07978): load balancing + reference mapping speed the CPU "
                  "chemistry step up by about 10x (Spray A, 256 MPI ranks on 2x64-core AMD EPYC Rome nodes, "

@@ -390,6 +390,25 @@ void dlbchem_destroy(dlbchem_ctx* ctx);
  */
 int dlbchem_table_stats(const char* mech_path, int32_t team_warps, int64_t* out);
 
+/*
+ * Host only, no GPU needed: a symbolic analysis of a sparse LU of the
+ * iteration matrix I/(h gamma) - J (the problem-tailored linear algebra of
+ * Sec. 5, future work), against the dense LU the integrator runs. The sparse
+ * part of the species block is the pattern of d wdot_k / d c_j through the
+ * reactions' own concentrations (participants, listed efficiencies) plus the
+ * diagonal; the temperature row and column are dense, and the dense rank-1
+ * term (the chain rule through rho and unit third-body efficiencies) is
+ * taken by Sherman-Morrison. Species are eliminated by minimum degree on the
+ * symmetrised pattern (ties to the lower index, no pivoting), temperature
+ * last. On success out[0..9] = unknowns N, species-block nonzeros, L + U
+ * nonzeros after fill (species pivots), dense LU multiply-adds, sparse LU
+ * multiply-adds, dense and sparse multiply-adds of one pair of triangular
+ * solves, the rank-1 extra per step, and the per-step totals (LU + four
+ * solves) dense and sparse. Returns OK, BAD_ARG (NULL, more than 1024
+ * species) or BAD_MECH.
+ */
+int dlbchem_lu_stats(const char* mech_path, int64_t* out);
+
 #ifdef __cplusplus
 }
 #endif

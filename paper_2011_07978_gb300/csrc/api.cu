@@ -1282,6 +1282,81 @@ int dlbchem_table_stats(const char* mech_path, int32_t team_warps, int64_t* out)
   return DLBCHEM_OK;
 }
 
+int dlbchem_lu_stats(const char* mech_path, int64_t* out) {
+  g_create_err.clear();
+  if (!mech_path || !out) return fail(nullptr, DLBCHEM_BAD_ARG, "NULL argument");
+  dlb::HostMech hm;
+  std::string why;
+  if (!parse_mech(mech_path, hm, why)) return fail(nullptr, DLBCHEM_BAD_MECH, why);
+  const int nsp = hm.nsp, N = nsp + 1;
+  if (nsp > 1024) return fail(nullptr, DLBCHEM_BAD_ARG, "symbolic analysis is limited to 1024 species");
+  // species-block pattern of the sparse part of the Jacobian: row k (a species
+  // with net coefficient != 0 in reaction r) against every species r's rate
+  // depends on through its own concentrations (reactants, products if
+  // reversible, listed third-body efficiencies), and the diagonal;
+  // symmetrised for the elimination graph
+  std::vector<std::vector<char>> adj(nsp, std::vector<char>(nsp, 0));
+  int64_t nnz = 0;
+  for (const auto& x : hm.rx) {
+    std::map<int, int> nu;
+    for (int k : x.r) nu[k] -= 1;
+    for (int k : x.p) nu[k] += 1;
+    std::vector<int> dep(x.r.begin(), x.r.end());
+    if (x.rev) dep.insert(dep.end(), x.p.begin(), x.p.end());
+    if (x.tb)
+      for (const auto& e : x.eff) dep.push_back(e.first);
+    for (const auto& kv : nu)
+      if (kv.second != 0)
+        for (int j : dep) adj[kv.first][j] = adj[j][kv.first] = 1;
+  }
+  for (int k = 0; k < nsp; ++k) adj[k][k] = 1;
+  for (int k = 0; k < nsp; ++k)
+    for (int j = 0; j < nsp; ++j) nnz += adj[k][j];
+  // minimum-degree elimination of the species (ties to the lower index), the
+  // temperature (coupled to every species) last; d_k = the pivot's remaining
+  // neighbours, so the pivot's update takes d_k^2 multiply-adds and its L and U
+  // parts hold d_k entries each
+  std::vector<char> done(nsp, 0);
+  int64_t lu_sparse = 0, tri_sparse = 0, filled = 0;
+  for (int step = 0; step < nsp; ++step) {
+    int best = -1, bdeg = 1 << 30;
+    for (int v = 0; v < nsp; ++v) {
+      if (done[v]) continue;
+      int d = 0;
+      for (int u = 0; u < nsp; ++u) d += (u != v && !done[u] && adj[v][u]) ? 1 : 0;
+      if (d < bdeg) { bdeg = d; best = v; }
+    }
+    std::vector<int> nb;
+    for (int u = 0; u < nsp; ++u)
+      if (u != best && !done[u] && adj[best][u]) nb.push_back(u);
+    for (int a : nb)
+      for (int b : nb) adj[a][b] = 1;
+    const int64_t d = int64_t(nb.size()) + 1;   // + the temperature
+    lu_sparse += d * d;
+    tri_sparse += 2 * d;
+    filled += 2 * int64_t(nb.size()) + 1;
+    done[best] = 1;
+  }
+  int64_t lu_dense = 0;
+  for (int k = 0; k < N; ++k) lu_dense += int64_t(N - 1 - k) * (N - 1 - k);
+  const int64_t tri_dense = int64_t(N) * (N - 1);
+  // the dense rank-1 part (the chain rule through rho and unit-efficiency
+  // third bodies) by Sherman-Morrison: one more solve per step, a dot product,
+  // and a dot product and an axpy per stage solve
+  const int64_t rank1 = tri_sparse + N + 4 * 2 * int64_t(N);
+  out[0] = N;
+  out[1] = nnz;
+  out[2] = filled;
+  out[3] = lu_dense;
+  out[4] = lu_sparse;
+  out[5] = tri_dense;
+  out[6] = tri_sparse;
+  out[7] = rank1;
+  out[8] = lu_dense + 4 * tri_dense;
+  out[9] = lu_sparse + 4 * tri_sparse + rank1;
+  return DLBCHEM_OK;
+}
+
 void dlbchem_destroy(dlbchem_ctx* c) {
   if (!c) return;
   if (c->d_blob || c->d_ws || c->d_stage) cudaStreamSynchronize(c->last_stream);

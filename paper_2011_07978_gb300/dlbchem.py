@@ -49,6 +49,7 @@ def load() -> ctypes.CDLL:
     lib.dlbchem_integrate_static.argtypes = sig[:-2] + [_vp]
     lib.dlbchem_nspecies.argtypes = [_vp]
     lib.dlbchem_table_stats.argtypes = [ctypes.c_char_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+    lib.dlbchem_lu_stats.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64)]
     lib.dlbchem_nreactions.argtypes = [_vp]
     lib.dlbchem_last_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
     lib.dlbchem_last_timing.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
@@ -400,3 +401,15 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+
+def lu_stats(mech_path: str) -> dict:
+    """dlbchem_lu_stats: symbolic sparse-LU analysis of a mechanism (host only)."""
+    out = (ctypes.c_int64 * 10)()
+    rc = load().dlbchem_lu_stats(mech_path.encode(), out)
+    if rc != OK:
+        raise DlbchemError(rc, load().dlbchem_last_error(None).decode())
+    keys = ("N", "block_nnz", "factor_nnz", "lu_dense", "lu_sparse", "solve_dense", "solve_sparse", "rank1",
+            "step_dense", "step_sparse")
+    return dict(zip(keys, (int(v) for v in out)))
+

@@ -13,7 +13,7 @@ REACTIONS line: CAL/MOLE (default), KCAL/MOLE, JOULES/MOLE, KJOULES/MOLE,
 KELVINS for Ea; MOLES (default) for A. Comments start at '!'.
 
 Not read (ValueError): other elements, fractional coefficients, more than
-three molecules on a side, explicit reverse parameters (REV), SRI and
+three molecules on a side, reactions whose elements do not balance, explicit reverse parameters (REV), SRI and
 Chebyshev forms, third bodies that are a named species ((+H2O)), several
 Arrhenius terms at one PLOG pressure, MOLECULES units.
 
@@ -241,6 +241,9 @@ def read_chemkin(mech_text: str, thermo_text: str | None = None) -> Mechanism:
         for side in (r["reac"], r["prod"]):
             if sum(nu for _, nu in side) > 3 or len(side) > 3:
                 raise ValueError(f"reaction {j}: more than three molecules on a side")
+        bal = sum(nu * atoms[k] for k, nu in r["reac"]) - sum(nu * atoms[k] for k, nu in r["prod"])
+        if np.any(bal != 0):
+            raise ValueError(f"reaction {j}: elements not balanced")
         if r["eff"] and not r["tb"]:
             raise ValueError(f"reaction {j}: efficiencies without a third body")
         for k, e in r["eff"]:

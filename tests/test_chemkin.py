@@ -74,7 +74,7 @@ CZ
 END
 REACTIONS KCAL/MOLE
 AX + BY <=> CZ        1.0E13  0.0   10.0   ! plain, reversible
-2AX+M=>CZ+AX+M        2.0E15 -1.0   0.0
+AX+BY+M=>CZ+M         2.0E15 -1.0   0.0
    BY/2.5/ CZ/0.0/
 AX+BY(+M) = CZ(+M)    3.0E12  0.5   5.0
    LOW / 4.0E18 -1.5 1.0 /
@@ -95,7 +95,7 @@ def test_hand_written_text_reads_to_its_values():
     cal = 4184.0
     assert m.reac[0] == [(0, 1), (1, 1)] and m.prod[0] == [(2, 1)] and m.reversible[0] == 1
     assert m.lnA[0] == pytest.approx(math.log(1e13)) and m.Ea[0] == pytest.approx(10.0 * cal)
-    assert m.reac[1] == [(0, 2)] and m.prod[1] == [(0, 1), (2, 1)] and m.reversible[1] == 0 and m.thirdbody[1] == 1
+    assert m.reac[1] == [(0, 1), (1, 1)] and m.prod[1] == [(2, 1)] and m.reversible[1] == 0 and m.thirdbody[1] == 1
     assert sorted(e for e in m.eff if e[0] == 1) == [(1, 1, 2.5), (1, 2, 0.0)]
     assert m.thirdbody[2] == 1 and m.reversible[2] == 1
     (j, kind, lnA0, b0, E0, a, T3, T1, T2), = m.falloff
@@ -115,7 +115,9 @@ def test_hand_written_text_reads_to_its_values():
 
 @pytest.mark.parametrize("bad", [
     MECH.replace("C H O", "C H O AR"),
-    MECH.replace("2AX+M=>CZ+AX+M", "2AX+M=>CZ+AX"),
+    MECH.replace("AX+BY+M=>CZ+M", "AX+BY+M=>CZ"),
+    MECH.replace("AX+BY+M=>CZ+M", "3AX+BY+M=>CZ+M"),
+    MECH.replace("AX+BY+M=>CZ+M", "2AX+M=>CZ+AX+M"),
     MECH.replace("   DUPLICATE", "   REV / 1.0E9 0.0 5.0 /"),
     MECH.replace("AX + BY <=> CZ", "0.5AX + BY <=> CZ"),
     MECH.replace("AX+BY(+M) = CZ(+M)", "AX+BY(+BY) = CZ(+BY)"),

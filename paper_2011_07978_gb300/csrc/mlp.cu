@@ -187,29 +187,30 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, const
 // ---------------------------------------------------------------------------
 // Whole-network forward pass for inference: one persistent CTA per SM, three
 // roles in warps of their own. The weights, packed once into BF16 k-tiles of
-// 32 in exactly the shared-memory layout the MMA reads, stream through a ring
-// of kFusedStages buffers filled by bulk copies (cp.async.bulk, the TMA
-// engine, completing on mbarriers) from a producer warp. An MMA warp issues
-// tcgen05.mma (kind::f16, BF16 operands, FP32 accumulator in tensor memory)
-// and commits each k-tile to free its buffer. Four epilogue warps (one per
-// tensor-memory lane quarter, 32 rows each) read the accumulator, add the
-// bias, apply SiLU and write the activations back to shared memory as BF16:
-// the next layer's A operand. Activations never leave shared memory; only
-// the network input and output cross HBM. The CTA keeps two 128-row tiles in
-// flight, each with its own activation tile and accumulator, and alternates
-// them layer by layer, so the epilogue of one tile runs while the tensor
-// cores work on the other. Arithmetic per element is that of the layered
-// path above: BF16 operands, FP32 accumulation, FP32 bias and SiLU,
+// 64 (four MMAs of K = 16 each) in exactly the shared-memory layout the MMA
+// reads, stream through a two-deep ring of 32 KB buffers filled by bulk
+// copies (cp.async.bulk, the TMA engine, completing on mbarriers) from a
+// producer warp. An MMA warp issues tcgen05.mma (kind::f16, BF16 operands,
+// FP32 accumulator in tensor memory) and commits each k-tile to free its
+// buffer. Eight epilogue warps (two per tensor-memory lane quarter, 32 rows
+// each, alternate 16-column chunks) read the accumulator, add the bias, apply
+// SiLU and write the activations back to shared memory as BF16: the next
+// layer's A operand. Activations never leave shared memory; only the network
+// input and output cross HBM. The CTA keeps two 128-row tiles in flight, each
+// with its own activation tile and accumulator, and alternates them layer by
+// layer, so the epilogue of one tile runs while the tensor cores work on the
+// other. Arithmetic per element is that of the layered path above: BF16
+// operands, FP32 accumulation over k-tiles of 64, FP32 bias and SiLU,
 // activations rounded to BF16 as the next layer's operand. Supported shapes:
 // hidden widths multiples of 64 up to 256, n_in and n_out up to 256, at most
 // kFusedMaxLayers layers.
 // ---------------------------------------------------------------------------
 constexpr int kFusedMaxLayers = 8;
 constexpr int kFusedMaxN = 256;
-constexpr int kFK = 32;                                       // k-tile of the weight stream
-constexpr int kFusedStages = 5;                               // weight ring depth
+constexpr int kFK = 64;                                       // k-tile of the weight stream
+constexpr int kFusedStages = 2;                               // weight ring depth
 constexpr int kFusedSmemH = kTM * kFusedMaxN * 2;             // 64 KB per activation tile
-constexpr int kFusedSmemW = kFusedMaxN * kFK * 2;             // 16 KB per weight buffer
+constexpr int kFusedSmemW = kFusedMaxN * kFK * 2;             // 32 KB per weight buffer
 constexpr int kFusedBias = kFusedMaxLayers * kFusedMaxN * 4;  // every layer's bias
 constexpr int kFusedSmem = 2 * kFusedSmemH + kFusedStages * kFusedSmemW + kFusedBias + 1024;   // + alignment
 constexpr int kFusedEpiWarps = 8;                             // two per tensor-memory lane quarter

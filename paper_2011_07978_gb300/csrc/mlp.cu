@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(128) gemm_tc_kernel(int M, int N, int K, const
 // 64 (four MMAs of K = 16 each) in exactly the shared-memory layout the MMA
 // reads, stream through a two-deep ring of 32 KB buffers filled by bulk
 // copies (cp.async.bulk, the TMA engine, completing on mbarriers) from a
-// producer warp. An MMA warp issues tcgen05.mma (kind::f16, BF16 operands,
+// producer warp; an output layer of at most 16 KB is copied once and stays. An MMA warp issues tcgen05.mma (kind::f16, BF16 operands,
 // FP32 accumulator in tensor memory) and commits each k-tile to free its
 // buffer. Eight epilogue warps (two per tensor-memory lane quarter, 32 rows
 // each, alternate 16-column chunks) read the accumulator, add the bias, apply
@@ -212,7 +212,10 @@ constexpr int kFusedStages = 2;                               // weight ring dep
 constexpr int kFusedSmemH = kTM * kFusedMaxN * 2;             // 64 KB per activation tile
 constexpr int kFusedSmemW = kFusedMaxN * kFK * 2;             // 32 KB per weight buffer
 constexpr int kFusedBias = kFusedMaxLayers * kFusedMaxN * 4;  // every layer's bias
-constexpr int kFusedSmem = 2 * kFusedSmemH + kFusedStages * kFusedSmemW + kFusedBias + 1024;   // + alignment
+// the output layer's packed weights stay in shared memory when they fit here
+// (a narrow output: they then skip the ring and its per-k-tile round trips)
+constexpr int kFusedResident = 16 * 1024;
+constexpr int kFusedSmem = 2 * kFusedSmemH + kFusedStages * kFusedSmemW + kFusedBias + kFusedResident + 1024;
 constexpr int kFusedEpiWarps = 8;                             // two per tensor-memory lane quarter
 constexpr int kFusedThreads = 32 * (kFusedEpiWarps + 2);      // + producer warp + MMA warp
 
@@ -223,6 +226,7 @@ struct FusedNet {
   int64_t woff[kFusedMaxLayers];                // byte offset of the layer's packed weights
   const float* bias[kFusedMaxLayers];
   const unsigned char* wpk;
+  uint32_t res_bytes;                           // output layer resident in shared memory (0: streamed)
 };
 
 // byte offset of (row, k) in a tile of rows x kext BF16 values (kext a multiple of 8)
@@ -295,7 +299,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_forward_kernel(int
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(fused_smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* sW = sH0 + 2 * kFusedSmemH;                               // kFusedStages buffers
   float* sbias = reinterpret_cast<float*>(sW + kFusedStages * kFusedSmemW);  // [layer][kFusedMaxN]
-  __shared__ __align__(8) unsigned long long full[kFusedStages], empty[kFusedStages], acc_full[2], h_ready[2];
+  unsigned char* sR = reinterpret_cast<unsigned char*>(sbias) + kFusedBias;    // resident output layer
+  __shared__ __align__(8) unsigned long long full[kFusedStages], empty[kFusedStages], acc_full[2], h_ready[2], res_bar, drain_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -311,6 +316,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_forward_kernel(int
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[b])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[b])) : "memory");
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&res_bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&drain_bar)) : "memory");
     for (int j = 0; j < 2; ++j) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_full[j])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&h_ready[j])), "r"(kFusedEpiWarps)
@@ -345,6 +352,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_forward_kernel(int
         int64_t lt;
         int l;
         ord.unit(u, lt, l);
+        if (l + 1 == net.nl && net.res_bytes) continue;   // resident: not streamed
         const uint32_t bytes = uint32_t(net.np[l]) * kFK * 2;
         for (int kt = 0; kt < net.kp[l] / kFK; ++kt, ++g) {
           const int st = int(g % kFusedStages);
@@ -364,7 +372,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_forward_kernel(int
     // MMA issuer
     if (lane == 0) {
       int64_t g = 0, done_units[2] = {0, 0};
-      bool issued = false;
+      bool res_ready = false;
+      if (net.res_bytes && nunits > 0) {   // the output layer's weights, once
+        const uint32_t bar = smem_u32(&res_bar);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(net.res_bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(sR)),
+                     "l"(net.wpk + net.woff[net.nl - 1]), "r"(net.res_bytes), "r"(bar)
+                     : "memory");
+      }
       for (int64_t u = 0; u < nunits && !abort_flag; ++u) {
         int64_t lt;
         int l;
@@ -379,6 +395,31 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_forward_kernel(int
         const uint32_t hbase = smem_u32(sH0 + slot * kFusedSmemH);
         const uint32_t dtm = tmem + uint32_t(slot * kFusedMaxN);
         bool ok = true;
+        if (l + 1 == net.nl && net.res_bytes) {
+          // resident output layer: no ring, one commit for the whole unit
+          if (!res_ready) {
+            if (!wait(&res_bar, 0u)) break;
+            res_ready = true;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          for (int kt = 0; kt < kp / kFK; ++kt) {
+#pragma unroll
+            for (int kk = 0; kk < kFK / 16; ++kk) {
+              const uint64_t ad = umma_desc(hbase + uint32_t(kt * (kFK / 8) + kk * 2) * 128u, 128, uint32_t(kp) * 16u);
+              const uint64_t bd = umma_desc(smem_u32(sR) + uint32_t(kt) * uint32_t(np) * (kFK * 2) + uint32_t(kk) * 256u,
+                                            128, (kFK / 8) * 128);
+              const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+              asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                           "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtm),
+                           "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&acc_full[slot]))
+                       : "memory");
+          ++done_units[slot];
+          continue;
+        }
         for (int kt = 0; kt < kp / kFK; ++kt, ++g) {
           const int st = int(g % kFusedStages);
           if (!wait(&full[st], uint32_t(g / kFusedStages) & 1u)) { ok = false; break; }
@@ -396,7 +437,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_forward_kernel(int
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            smem_u32(&empty[st]))
                        : "memory");
-          issued = true;
         }
         if (!ok) break;
         // the unit's accumulator is complete when its MMAs are
@@ -405,8 +445,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_forward_kernel(int
                      : "memory");
         ++done_units[slot];
       }
-      // on a give-up, let the MMAs in flight finish before tensor memory is freed
-      if (abort_flag && issued) mbar_wait(smem_u32(&empty[(g - 1) % kFusedStages]), uint32_t((g - 1) / kFusedStages) & 1u);
+      // on a give-up, let the copy and the MMAs in flight finish before tensor
+      // memory is freed: one more commit covers every MMA issued so far
+      if (abort_flag) {
+        if (net.res_bytes && nunits > 0 && !res_ready) mbar_wait(smem_u32(&res_bar), 0u);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&drain_bar))
+                     : "memory");
+        mbar_wait(smem_u32(&drain_bar), 0u);
+      }
     }
   } else {
     // epilogue warps: warp w reads tensor-memory lane quarter w % 4 (rows
@@ -695,6 +742,8 @@ bool plan_fused(dlbchem_mlp* m) {
   }
   f.wpk = m->d_wpk;
   for (int l = 0; l < f.nl; ++l) f.bias[l] = m->d_params + L[l].b;
+  const int64_t last_bytes = int64_t(f.kp[f.nl - 1]) * f.np[f.nl - 1] * 2;
+  f.res_bytes = last_bytes <= dlb::kFusedResident ? uint32_t(last_bytes) : 0u;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

@@ -19,12 +19,14 @@
 //    mapped to the others).
 // Plain loops, row-major dense matrices, partial pivoting, no blocking or SIMD.
 //
-// Pinned (tests/test_oracle_pins.py, test_oracle_mapping.py) by the method's
-// order conditions and stability function, closed-form decays and
-// relaxations, equilibrium constants, detailed balance, linear invariants,
-// an independent stiff solver, finite-difference Jacobians and a library
-// linear solve. The end-to-end result of a multi-species mechanism has no
-// published value to compare with: parity unpinned beyond those pins.
+// Pinned (tests/test_oracle_*.py) by the method's order conditions and
+// stability function, closed-form decays and relaxations, equilibrium
+// constants, detailed balance, linear invariants, an independent stiff
+// solver, finite-difference Jacobians and a library linear solve; the
+// end-to-end result on the full 10- and 53-species mechanisms by the
+// right-hand side written out again in numpy and integrated by scipy's
+// Radau (tests/test_oracle_endtoend.py). No published value of a
+// multi-species result exists to compare with.
 #include <algorithm>
 #include <array>
 #include <atomic>

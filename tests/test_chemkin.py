@@ -127,3 +127,24 @@ def test_hand_written_text_reads_to_its_values():
 def test_refuses_what_it_does_not_read(bad):
     with pytest.raises(ValueError):
         read_chemkin(bad, THERMO)
+
+
+def test_command_line_writes_a_mechanism_file(tmp_path):
+    """python -m synth.chemkin mech.inp thermo.dat out.bin: the file the
+    oracle then loads and integrates (element totals kept)."""
+    import subprocess
+    import sys
+    mech, thermo, out = tmp_path / "m.inp", tmp_path / "t.dat", tmp_path / "m.bin"
+    mech.write_text(MECH)
+    thermo.write_text(THERMO)
+    r = subprocess.run([sys.executable, "-m", "synth.chemkin", str(mech), str(thermo), str(out)],
+                       capture_output=True, text=True, cwd=str(__import__("pathlib").Path(__file__).parents[1]))
+    assert r.returncode == 0, r.stderr
+    assert "3 species, 5 reactions, 1 fall-off, 1 PLOG" in r.stdout
+    m = read_mech(str(out))
+    T = np.array([1200.0, 1500.0])
+    Y = np.array([[0.5, 0.2], [0.3, 0.5], [0.2, 0.3]])
+    To, Yo, _, st = oracle.Oracle(str(out)).integrate(T, np.array([1e5, 2e6]), Y, 1e-5, rtol=1e-8, atol=1e-12)
+    assert (st == 0).all()
+    aW = m.atoms.T / m.W[None, :]
+    np.testing.assert_allclose(aW @ Yo, aW @ Y, rtol=1e-10, atol=1e-14)
